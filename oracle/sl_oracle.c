@@ -1,0 +1,683 @@
+/*
+ * sl_oracle.c -- plain FP64 CPU oracle for the Seven-League (7L) scheme.
+ *
+ * TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only the test suite, the smoke
+ * check and the CPU-baseline leg of the benchmark load this file.  It shares
+ * no code, header, table or constant generator with the CUDA library: every
+ * routine here is written from the paper's definitions (or the published
+ * definition of the random number generator) and kept deliberately simple:
+ * one path at a time, one loop per sum, FP64 throughout.
+ *
+ * Paper: S. Liu, G. Colonna, L. Grzelak, C. Oosterlee, "GPU acceleration of
+ * the Seven-League scheme for large time step simulations of SDEs"
+ * (arXiv:2302.05170).  Citations below name its equations and Algorithm I.
+ *
+ * Pinned against (tests/test_oracle_*.py): Gauss-Hermite closed forms and
+ * moment exactness, Philox published known-answer vectors, Lagrange
+ * interpolation identities, closed-form moments of the exact-collocation GBM
+ * chain, pathwise exactness of the exact-collocation OU chain, exact moment
+ * recursions of Euler-Maruyama, brute-force order statistics, central finite
+ * differences for every derivative, and closed-form Black-Scholes values.
+ * No function in this file is "parity unpinned".
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Model / SDE / activation codes (the same integers the library uses, chosen
+ * independently here and checked by the tests). */
+enum { ORC_MODEL_MLP = 0, ORC_MODEL_GBM_EXACT = 1, ORC_MODEL_OU_EXACT = 2 };
+enum { ORC_SDE_GBM = 0, ORC_SDE_OU = 1, ORC_SDE_CIR = 2 };
+enum { ORC_ACT_RELU = 0, ORC_ACT_SOFTPLUS = 1 };
+enum { ORC_TAG_7L = 0, ORC_TAG_EM = 1 };
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+static void set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+/* ------------------------------------------------------------------------
+ * Philox4x32-10, from its published definition (Salmon, Moraes, Dror, Shaw,
+ * "Parallel random numbers: as easy as 1, 2, 3", SC'11): ten rounds of
+ *   (c0,c1,c2,c3) -> (hi(M1*c2)^c1^k0, lo(M1*c2), hi(M0*c0)^c3^k1, lo(M0*c0))
+ * with the key bumped by the Weyl constants between rounds.
+ * The paper only requires X ~ N(0,1) (Eq. 6.2, Algorithm I step 6); the
+ * generator is the library's choice and is reproduced here independently.
+ * ---------------------------------------------------------------------- */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Uniform on (0,1) from the top 24 bits of a word: ((w >> 8) + 1/2) / 2^24. */
+static double word_to_uniform(uint32_t w) {
+    return ((double)(w >> 8) + 0.5) * (1.0 / 16777216.0);
+}
+
+/* Standard normal number `step` of the stream (seed, tag, set, path).
+ * Counter = (step / 4, path, set, tag), key = (seed low word, seed high word).
+ * Box-Muller on the word pairs (0,1) and (2,3): radius from the first word
+ * of the pair, angle from the second; cosine for even `step`, sine for odd. */
+double orc_normal(uint64_t seed, uint32_t tag, uint32_t set, uint32_t path, uint32_t step) {
+    uint32_t ctr[4] = {step >> 2, path, set, tag};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    uint32_t pair = (step & 3u) >> 1;      /* 0 -> words (0,1), 1 -> words (2,3) */
+    double u_r = word_to_uniform(w[2 * pair]);
+    double u_a = word_to_uniform(w[2 * pair + 1]);
+    double radius = sqrt(-2.0 * log(u_r));
+    double angle = 2.0 * M_PI * u_a;
+    return (step & 1u) ? radius * sin(angle) : radius * cos(angle);
+}
+
+void orc_normals(uint64_t seed, uint32_t tag, uint32_t set, uint32_t path,
+                 uint32_t first_step, int n, double* out) {
+    for (int i = 0; i < n; ++i) out[i] = orc_normal(seed, tag, set, path, first_step + (uint32_t)i);
+}
+
+/* ------------------------------------------------------------------------
+ * Gauss-Hermite points of the standard normal (the x_j of the 7L map g_m,
+ * Section "Methodology": x_j are Gauss-Hermite points of X ~ N(0,1)).
+ * Probabilists' Hermite polynomials He_0 = 1, He_1 = x,
+ * He_{k+1} = x He_k - k He_{k-1}; the nodes are the m roots of He_m and the
+ * probability weights are m! / (m^2 He_{m-1}(x_j)^2), which sum to one.
+ * Roots are bracketed on a fine grid and refined by bisection (no eigen
+ * solver: the library uses Golub-Welsch, the oracle deliberately does not).
+ * ---------------------------------------------------------------------- */
+static double hermite_e(int n, double x) {
+    if (n == 0) return 1.0;
+    double prev = 1.0, cur = x;
+    for (int k = 1; k < n; ++k) {
+        double next = x * cur - (double)k * prev;
+        prev = cur;
+        cur = next;
+    }
+    return cur;
+}
+
+int orc_gauss_hermite(int m, double* x, double* w) {
+    if (m < 1 || m > 64) return 1;
+    double R = sqrt(4.0 * m + 2.0) + 1.0;     /* all roots lie in (-R, R) */
+    const int n_grid = 20001;                  /* odd count of intervals: 0 is never a grid point */
+    int found = 0;
+    double a = -R, fa = hermite_e(m, a);
+    for (int g = 1; g <= n_grid && found < m; ++g) {
+        double b = -R + 2.0 * R * (double)g / (double)n_grid;
+        double fb = hermite_e(m, b);
+        if ((fa < 0.0 && fb > 0.0) || (fa > 0.0 && fb < 0.0)) {
+            double lo = a, hi = b, flo = fa;
+            for (int it = 0; it < 200; ++it) {
+                double mid = 0.5 * (lo + hi);
+                if (mid <= lo || mid >= hi) break;
+                double fm = hermite_e(m, mid);
+                if (fm == 0.0) { lo = hi = mid; break; }
+                if ((fm < 0.0) == (flo < 0.0)) { lo = mid; flo = fm; } else { hi = mid; }
+            }
+            x[found++] = 0.5 * (lo + hi);
+        }
+        a = b;
+        fa = fb;
+    }
+    if (found != m) return 2;
+    /* The roots are symmetric about 0: average each pair, centre exactly 0. */
+    for (int j = 0; j < m / 2; ++j) {
+        double s = 0.5 * (x[m - 1 - j] - x[j]);
+        x[j] = -s;
+        x[m - 1 - j] = s;
+    }
+    if (m % 2 == 1) x[m / 2] = 0.0;
+    double mfact = 1.0;
+    for (int k = 2; k <= m; ++k) mfact *= (double)k;
+    for (int j = 0; j < m; ++j) {
+        double h = hermite_e(m - 1, x[j]);
+        w[j] = mfact / ((double)m * (double)m * h * h);
+    }
+    return 0;
+}
+
+/* Standard normal CDF. */
+static double std_normal_cdf(double x) { return 0.5 * erfc(-x / sqrt(2.0)); }
+
+/* 0-based rank of the empirical quantile at level Phi(x_j) among n samples:
+ * the inverse empirical CDF, ceil(n * Phi(x_j)) - 1, clamped to [0, n-1]. */
+int orc_quantile_ranks(int m, int64_t n, int64_t* ranks) {
+    double x[64], w[64];
+    if (orc_gauss_hermite(m, x, w) != 0) return 1;
+    for (int j = 0; j < m; ++j) {
+        double level = std_normal_cdf(x[j]);
+        int64_t k = (int64_t)ceil((double)n * level) - 1;
+        if (k < 0) k = 0;
+        if (k > n - 1) k = n - 1;
+        ranks[j] = k;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Lagrange interpolation through (x_j, y_j), j = 0..m-1: the map g_m of the
+ * 7L scheme (Section "Methodology", Algorithm I step 5).  Written as the
+ * plain definition sum_j y_j prod_{k != j} (X - x_k) / (x_j - x_k); the
+ * barycentric rearrangement the paper uses is the same polynomial.
+ * ---------------------------------------------------------------------- */
+double orc_lagrange(int m, const double* xn, const double* y, double X) {
+    double g = 0.0;
+    for (int j = 0; j < m; ++j) {
+        double l = 1.0;
+        for (int k = 0; k < m; ++k)
+            if (k != j) l *= (X - xn[k]) / (xn[j] - xn[k]);
+        g += y[j] * l;
+    }
+    return g;
+}
+
+/* d g_m / d y_j at X: the Lagrange basis polynomial l_j(X). */
+static void lagrange_basis(int m, const double* xn, double X, double* l) {
+    for (int j = 0; j < m; ++j) {
+        double v = 1.0;
+        for (int k = 0; k < m; ++k)
+            if (k != j) v *= (X - xn[k]) / (xn[j] - xn[k]);
+        l[j] = v;
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * The network H of Eq. (6.3)/(6.4): d_in -> width (x n_hidden) -> m, fully
+ * connected.  Parameters are one flat array, layer by layer: W_l (row-major
+ * [out][in]) followed by b_l.  Hidden layers apply the activation (ReLU or
+ * Softplus), the output layer is linear.
+ * ---------------------------------------------------------------------- */
+#define ORC_MAX_W 128
+
+int64_t orc_n_params(int d_in, int width, int n_hidden, int m) {
+    int64_t n = (int64_t)width * d_in + width;
+    n += (int64_t)(n_hidden - 1) * ((int64_t)width * width + width);
+    n += (int64_t)m * width + m;
+    return n;
+}
+
+static double act_f(int act, double z) {
+    if (act == ORC_ACT_SOFTPLUS) return z > 0.0 ? z + log1p(exp(-z)) : log1p(exp(z));
+    return z > 0.0 ? z : 0.0;
+}
+
+static double act_df(int act, double z) {
+    if (act == ORC_ACT_SOFTPLUS) return 1.0 / (1.0 + exp(-z));
+    return z > 0.0 ? 1.0 : 0.0;
+}
+
+/* Forward pass; if zs/hs are given, store pre-activations and activations of
+ * every hidden layer (n_hidden x width each). */
+static void mlp_forward(const double* P, int d_in, int width, int n_hidden, int m, int act,
+                        const double* f, double* out, double* zs, double* hs) {
+    double hin[ORC_MAX_W], h[ORC_MAX_W], z[ORC_MAX_W];
+    const double* in = f;
+    int n_in = d_in;
+    for (int l = 0; l < n_hidden; ++l) {
+        const double* W = P;
+        const double* b = P + (int64_t)width * n_in;
+        for (int o = 0; o < width; ++o) {
+            double s = b[o];
+            for (int i = 0; i < n_in; ++i) s += W[(int64_t)o * n_in + i] * in[i];
+            z[o] = s;
+        }
+        for (int o = 0; o < width; ++o) h[o] = act_f(act, z[o]);
+        if (zs) memcpy(zs + (int64_t)l * width, z, sizeof(double) * width);
+        if (hs) memcpy(hs + (int64_t)l * width, h, sizeof(double) * width);
+        P += (int64_t)width * n_in + width;
+        memcpy(hin, h, sizeof(double) * width);   /* this layer's output is the next one's input */
+        in = hin;
+        n_in = width;
+    }
+    const double* W = P;
+    const double* b = P + (int64_t)m * n_in;
+    for (int o = 0; o < m; ++o) {
+        double s = b[o];
+        for (int i = 0; i < n_in; ++i) s += W[(int64_t)o * n_in + i] * in[i];
+        out[o] = s;
+    }
+}
+
+void orc_mlp_forward(const double* P, int d_in, int width, int n_hidden, int m, int act,
+                     const double* feats, int64_t n_rows, double* out) {
+    for (int64_t r = 0; r < n_rows; ++r)
+        mlp_forward(P, d_in, width, n_hidden, m, act, feats + r * d_in, out + r * m, NULL, NULL);
+}
+
+/* Reverse mode (back-propagation) for one row: given dL/dout (m values),
+ * ADD dL/dparams into gP (if non-NULL) and write dL/dfeatures into gf
+ * (if non-NULL). */
+static void mlp_backward_row(const double* P, int d_in, int width, int n_hidden, int m, int act,
+                             const double* f, const double* gout, double* gP, double* gf) {
+    double zs[8 * ORC_MAX_W], hs[8 * ORC_MAX_W], out[ORC_MAX_W];
+    mlp_forward(P, d_in, width, n_hidden, m, act, f, out, zs, hs);
+    /* offsets of each layer's parameters */
+    int64_t off[16];
+    int64_t o = 0;
+    int n_in = d_in;
+    for (int l = 0; l < n_hidden; ++l) {
+        off[l] = o;
+        o += (int64_t)width * n_in + width;
+        n_in = width;
+    }
+    off[n_hidden] = o;
+    /* output layer */
+    double gh[ORC_MAX_W], gz[ORC_MAX_W];
+    {
+        const double* W = P + off[n_hidden];
+        const double* hin = hs + (int64_t)(n_hidden - 1) * width;
+        for (int i = 0; i < width; ++i) {
+            double s = 0.0;
+            for (int k = 0; k < m; ++k) s += W[(int64_t)k * width + i] * gout[k];
+            gh[i] = s;
+        }
+        if (gP) {
+            double* gW = gP + off[n_hidden];
+            double* gb = gW + (int64_t)m * width;
+            for (int k = 0; k < m; ++k) {
+                for (int i = 0; i < width; ++i) gW[(int64_t)k * width + i] += gout[k] * hin[i];
+                gb[k] += gout[k];
+            }
+        }
+    }
+    for (int l = n_hidden - 1; l >= 0; --l) {
+        int nin = (l == 0) ? d_in : width;
+        const double* in = (l == 0) ? f : hs + (int64_t)(l - 1) * width;
+        const double* z = zs + (int64_t)l * width;
+        for (int k = 0; k < width; ++k) gz[k] = gh[k] * act_df(act, z[k]);
+        const double* W = P + off[l];
+        if (gP) {
+            double* gW = gP + off[l];
+            double* gb = gW + (int64_t)width * nin;
+            for (int k = 0; k < width; ++k) {
+                for (int i = 0; i < nin; ++i) gW[(int64_t)k * nin + i] += gz[k] * in[i];
+                gb[k] += gz[k];
+            }
+        }
+        double gin[ORC_MAX_W];
+        for (int i = 0; i < nin; ++i) {
+            double s = 0.0;
+            for (int k = 0; k < width; ++k) s += W[(int64_t)k * nin + i] * gz[k];
+            gin[i] = s;
+        }
+        if (l == 0) {
+            if (gf) memcpy(gf, gin, sizeof(double) * d_in);
+        } else {
+            memcpy(gh, gin, sizeof(double) * width);
+        }
+    }
+}
+
+/* Mean-squared error over a batch of rows and all m outputs,
+ * L = 1/(n_rows*m) sum_r sum_j (H_j(f_r) - y_rj)^2, and its gradient with
+ * respect to the parameters (written to gP, overwritten). */
+double orc_mse_grad(const double* P, int d_in, int width, int n_hidden, int m, int act,
+                    const double* feats, const double* labels, const int32_t* rows, int64_t n_rows,
+                    double* gP) {
+    int64_t np = orc_n_params(d_in, width, n_hidden, m);
+    if (gP) memset(gP, 0, sizeof(double) * np);
+    double loss = 0.0;
+    double scale = 1.0 / ((double)n_rows * (double)m);
+    for (int64_t r = 0; r < n_rows; ++r) {
+        int64_t row = rows ? rows[r] : r;
+        const double* f = feats + row * d_in;
+        const double* y = labels + row * m;
+        double out[ORC_MAX_W], gout[ORC_MAX_W];
+        mlp_forward(P, d_in, width, n_hidden, m, act, f, out, NULL, NULL);
+        for (int j = 0; j < m; ++j) {
+            double e = out[j] - y[j];
+            loss += e * e * scale;
+            gout[j] = 2.0 * e * scale;
+        }
+        if (gP) mlp_backward_row(P, d_in, width, n_hidden, m, act, f, gout, gP, NULL);
+    }
+    return loss;
+}
+
+/* Input gradient of sum_j c_j H_j(f) for each row (a vector-Jacobian product). */
+void orc_mlp_vjp_input(const double* P, int d_in, int width, int n_hidden, int m, int act,
+                       const double* feats, const double* c, int64_t n_rows, double* gfeats) {
+    for (int64_t r = 0; r < n_rows; ++r)
+        mlp_backward_row(P, d_in, width, n_hidden, m, act, feats + r * d_in, c + r * m, NULL,
+                         gfeats + r * d_in);
+}
+
+/* ------------------------------------------------------------------------
+ * Adam (Kingma & Ba 2015), the optimiser named in the experiments section:
+ *   m <- b1 m + (1-b1) g,  v <- b2 v + (1-b2) g^2,
+ *   P <- P - lr * (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps).
+ * Runs n_batches steps, step counter t = t0+1 .. t0+n_batches; batch b uses
+ * rows batch_rows[b*batch .. b*batch+batch-1].  Loss of each batch (before
+ * its update) goes to losses[b].
+ * ---------------------------------------------------------------------- */
+void orc_train_adam(double* P, double* am, double* av, int64_t t0, int d_in, int width,
+                    int n_hidden, int m, int act, const double* feats, const double* labels,
+                    const int32_t* batch_rows, int n_batches, int batch, double lr, double b1,
+                    double b2, double eps, double* losses) {
+    int64_t np = orc_n_params(d_in, width, n_hidden, m);
+    double* g = (double*)malloc(sizeof(double) * np);
+    for (int b = 0; b < n_batches; ++b) {
+        double loss = orc_mse_grad(P, d_in, width, n_hidden, m, act, feats, labels,
+                                   batch_rows + (int64_t)b * batch, batch, g);
+        if (losses) losses[b] = loss;
+        double t = (double)(t0 + b + 1);
+        double c1 = 1.0 - pow(b1, t), c2 = 1.0 - pow(b2, t);
+        for (int64_t i = 0; i < np; ++i) {
+            am[i] = b1 * am[i] + (1.0 - b1) * g[i];
+            av[i] = b2 * av[i] + (1.0 - b2) * g[i] * g[i];
+            P[i] -= lr * (am[i] / c1) / (sqrt(av[i] / c2) + eps);
+        }
+    }
+    free(g);
+}
+
+/* ------------------------------------------------------------------------
+ * Conditional collocation points y_j | Y_i  (Eq. 6.3 / 6.4).
+ *  - MLP: the network with features [Y_i, dt, theta_0..theta_{p-1}].
+ *  - GBM_EXACT, theta = (mu, sigma): the exact lognormal quantile map,
+ *      y_j = Y_i exp((mu - sigma^2/2) dt + sigma sqrt(dt) x_j).
+ *  - OU_EXACT, theta = (Ybar, sigma, lambda), Eq. (6.5)/(6.6) restarted at Y_i:
+ *      y_j = e^{-lambda dt} Y_i + Ybar (1 - e^{-lambda dt})
+ *            + sigma sqrt((1 - e^{-2 lambda dt}) / (2 lambda)) x_j.
+ * With tangents: dy[j*(1+p) + q] = d y_j / d(Y_i, theta)_q (q = 0 is Y_i).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int model, d_in, width, n_hidden, act, m, p;
+    const double* P;
+    const double* xn;
+} orc_net;
+
+static void collocation(const orc_net* N, double Y, double dt, const double* th, double* y,
+                        double* dy) {
+    int m = N->m, p = N->p, q1 = 1 + p;
+    if (N->model == ORC_MODEL_GBM_EXACT) {
+        double mu = th[0], sg = th[1], sdt = sqrt(dt);
+        for (int j = 0; j < m; ++j) {
+            double e = exp((mu - 0.5 * sg * sg) * dt + sg * sdt * N->xn[j]);
+            y[j] = Y * e;
+            if (dy) {
+                dy[j * q1 + 0] = e;
+                dy[j * q1 + 1] = y[j] * dt;
+                dy[j * q1 + 2] = y[j] * (-sg * dt + sdt * N->xn[j]);
+            }
+        }
+        return;
+    }
+    if (N->model == ORC_MODEL_OU_EXACT) {
+        double yb = th[0], sg = th[1], lam = th[2];
+        double e1 = exp(-lam * dt), e2 = exp(-2.0 * lam * dt);
+        double s2 = (1.0 - e2) / (2.0 * lam), s = sqrt(s2);
+        double ds2 = dt * e2 / lam - (1.0 - e2) / (2.0 * lam * lam);
+        double ds = ds2 / (2.0 * s);
+        for (int j = 0; j < m; ++j) {
+            y[j] = e1 * Y + yb * (1.0 - e1) + sg * s * N->xn[j];
+            if (dy) {
+                dy[j * q1 + 0] = e1;
+                dy[j * q1 + 1] = 1.0 - e1;
+                dy[j * q1 + 2] = s * N->xn[j];
+                dy[j * q1 + 3] = -dt * e1 * Y + yb * dt * e1 + sg * ds * N->xn[j];
+            }
+        }
+        return;
+    }
+    double f[64];
+    f[0] = Y;
+    f[1] = dt;
+    for (int k = 0; k < p; ++k) f[2 + k] = th[k];
+    mlp_forward(N->P, N->d_in, N->width, N->n_hidden, m, N->act, f, y, NULL, NULL);
+    if (dy) {
+        /* Jacobian row by row: reverse mode with unit output cotangents. */
+        for (int j = 0; j < m; ++j) {
+            double c[ORC_MAX_W] = {0}, gf[64];
+            c[j] = 1.0;
+            mlp_backward_row(N->P, N->d_in, N->width, N->n_hidden, m, N->act, f, c, NULL, gf);
+            dy[j * q1 + 0] = gf[0];
+            for (int k = 0; k < p; ++k) dy[j * q1 + 1 + k] = gf[2 + k];
+        }
+    }
+}
+
+/* Largest s with offsets[s] <= g (the set owning flat path g; empty sets skipped). */
+static int owning_set(const int64_t* offsets, int n_sets, int64_t g) {
+    int lo = 0, hi = n_sets - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) / 2;
+        if (offsets[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+/* ------------------------------------------------------------------------
+ * Algorithm I, online stage (steps 2-8) for one path of set s:
+ *   Y_0 given; for i = 0..n_steps-1: y = H(Y_i, dt, theta_s) (step 3),
+ *   draw X_{i+1} (step 6), Y_{i+1} = g_m(X_{i+1}) (steps 5-6).
+ * The normal for step i is orc_normal(seed, tag 0, s, path-in-set, i).
+ * If tangent is non-NULL it receives dY_T / d(Y0, theta) (1+p values),
+ * propagated forward step by step (forward-mode chain rule).
+ * ---------------------------------------------------------------------- */
+static double path_7l(const orc_net* N, const double* th, double Y0, double T, int n_steps,
+                      uint64_t seed, uint32_t set, uint32_t path, double* grid, double* tangent) {
+    int m = N->m, p = N->p, q1 = 1 + p;
+    double dt = T / (double)n_steps;
+    double Y = Y0;
+    double tg[16] = {0};
+    tg[0] = 1.0;
+    if (grid) grid[0] = Y;
+    for (int i = 0; i < n_steps; ++i) {
+        double y[ORC_MAX_W], dy[ORC_MAX_W * 16], l[ORC_MAX_W];
+        collocation(N, Y, dt, th, y, tangent ? dy : NULL);
+        double X = orc_normal(seed, ORC_TAG_7L, set, path, (uint32_t)i);
+        double Ynew = orc_lagrange(m, N->xn, y, X);
+        if (tangent) {
+            lagrange_basis(m, N->xn, X, l);
+            double ntg[16] = {0};
+            for (int q = 0; q < q1; ++q) {
+                double s = 0.0;
+                for (int j = 0; j < m; ++j) {
+                    /* chain rule through Y_i, plus the direct theta dependence */
+                    double dyq = dy[j * q1 + 0] * tg[q];
+                    if (q >= 1) dyq += dy[j * q1 + q];
+                    s += l[j] * dyq;
+                }
+                ntg[q] = s;
+            }
+            memcpy(tg, ntg, sizeof(double) * q1);
+        }
+        Y = Ynew;
+        if (grid) grid[i + 1] = Y;
+    }
+    if (tangent) memcpy(tangent, tg, sizeof(double) * q1);
+    return Y;
+}
+
+/* Evaluate selected flat paths (idx == NULL: all of them) of a batched call.
+ * theta is [n_sets][p]; Y0 is [n_sets]; offsets is the exclusive prefix of
+ * per-set path counts ([n_sets+1]).  out_YT[k] is Y_T of path idx[k]; the
+ * optional out_grid[k*(n_steps+1) + i] is Y_i. */
+int orc_7l_paths(int model, const double* P, int d_in, int width, int n_hidden, int act,
+                 const double* theta, int p, const double* Y0, const int64_t* offsets, int n_sets,
+                 double T, int n_steps, int m, uint64_t seed, const int64_t* idx, int64_t n_idx,
+                 double* out_YT, double* out_grid, int n_threads) {
+    double xn[64], wn[64];
+    if (orc_gauss_hermite(m, xn, wn) != 0) return 1;
+    orc_net N = {model, d_in, width, n_hidden, act, m, p, P, xn};
+    set_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < n_idx; ++k) {
+        int64_t g = idx ? idx[k] : k;
+        int s = owning_set(offsets, n_sets, g);
+        uint32_t q = (uint32_t)(g - offsets[s]);
+        out_YT[k] = path_7l(&N, theta + (int64_t)s * p, Y0[s], T, n_steps, seed, (uint32_t)s, q,
+                            out_grid ? out_grid + k * (int64_t)(n_steps + 1) : NULL, NULL);
+    }
+    return 0;
+}
+
+/* Per-set mean and unbiased sample variance of Y_T over ALL paths of every
+ * set (variance 0 when a set has fewer than two paths). */
+int orc_7l_moments(int model, const double* P, int d_in, int width, int n_hidden, int act,
+                   const double* theta, int p, const double* Y0, const int64_t* offsets,
+                   int n_sets, double T, int n_steps, int m, uint64_t seed, double* out_mean,
+                   double* out_var, int n_threads) {
+    int64_t total = offsets[n_sets];
+    double* yt = (double*)malloc(sizeof(double) * (total > 0 ? total : 1));
+    int rc = orc_7l_paths(model, P, d_in, width, n_hidden, act, theta, p, Y0, offsets, n_sets, T,
+                          n_steps, m, seed, NULL, total, yt, NULL, n_threads);
+    if (rc) { free(yt); return rc; }
+    for (int s = 0; s < n_sets; ++s) {
+        int64_t a = offsets[s], b = offsets[s + 1], n = b - a;
+        double mean = 0.0;
+        for (int64_t g = a; g < b; ++g) mean += yt[g];
+        mean = n > 0 ? mean / (double)n : 0.0;
+        double ss = 0.0;
+        for (int64_t g = a; g < b; ++g) ss += (yt[g] - mean) * (yt[g] - mean);
+        out_mean[s] = mean;
+        if (out_var) out_var[s] = n > 1 ? ss / (double)(n - 1) : 0.0;
+    }
+    free(yt);
+    return 0;
+}
+
+/* Pathwise sensitivities of the call payoff f = max(Y_T - K, 0):
+ * per selected path, value[k] = f(Y_T) and grad[k*(1+p) + q] =
+ * 1{Y_T > K} dY_T/d(Y0, theta)_q, by forward-mode propagation of dY/d(Y0, theta). */
+int orc_7l_payoff_grad(int model, const double* P, int d_in, int width, int n_hidden, int act,
+                       const double* theta, int p, const double* Y0, const int64_t* offsets,
+                       int n_sets, double T, int n_steps, int m, uint64_t seed, double K,
+                       const int64_t* idx, int64_t n_idx, double* out_YT, double* value,
+                       double* grad, int n_threads) {
+    double xn[64], wn[64];
+    if (orc_gauss_hermite(m, xn, wn) != 0) return 1;
+    orc_net N = {model, d_in, width, n_hidden, act, m, p, P, xn};
+    set_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < n_idx; ++k) {
+        int64_t g = idx ? idx[k] : k;
+        int s = owning_set(offsets, n_sets, g);
+        uint32_t q = (uint32_t)(g - offsets[s]);
+        double tg[16];
+        double YT = path_7l(&N, theta + (int64_t)s * p, Y0[s], T, n_steps, seed, (uint32_t)s, q,
+                            NULL, tg);
+        if (out_YT) out_YT[k] = YT;
+        value[k] = YT > K ? YT - K : 0.0;
+        for (int c = 0; c < 1 + p; ++c) grad[k * (1 + p) + c] = YT > K ? tg[c] : 0.0;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Offline stage (Algorithm I step 1): Euler-Maruyama, Eq. (6.2), with
+ * n_fine steps of d_tau = dt / n_fine from Y_i, normals from stream
+ * (seed, tag 1, row, path), fine step k using normal number k.
+ *   GBM (mu, sigma):          a = mu Y,             b = sigma Y
+ *   OU  (Ybar, sigma, lambda): a = -lambda (Y - Ybar), b = sigma        (Eq. 6.5)
+ *   CIR (kappa, ybar, gamma):  full truncation, a = kappa (ybar - Y+),
+ *                              b = gamma sqrt(Y+), Y+ = max(Y, 0);
+ *                              the returned sample is Y+ at the end.
+ * ---------------------------------------------------------------------- */
+static double em_path(int sde, const double* th, double Y, double dt, int n_fine, uint64_t seed,
+                      uint32_t row, uint32_t path) {
+    double dtau = dt / (double)n_fine, sq = sqrt(dtau);
+    for (int k = 0; k < n_fine; ++k) {
+        double X = orc_normal(seed, ORC_TAG_EM, row, path, (uint32_t)k);
+        double a, b;
+        if (sde == ORC_SDE_GBM) {
+            a = th[0] * Y;
+            b = th[1] * Y;
+        } else if (sde == ORC_SDE_OU) {
+            a = -th[2] * (Y - th[0]);
+            b = th[1];
+        } else {
+            double yp = Y > 0.0 ? Y : 0.0;
+            a = th[0] * (th[1] - yp);
+            b = th[2] * sqrt(yp);
+        }
+        Y = Y + a * dtau + b * sq * X;
+    }
+    if (sde == ORC_SDE_CIR && Y < 0.0) Y = 0.0;
+    return Y;
+}
+
+static int sde_p(int sde) { return sde == ORC_SDE_GBM ? 2 : 3; }
+
+/* Terminal EM samples: out[r*n_paths + q] for rows r in [row0, row0+n_rows). */
+int orc_em_terminal(int sde, const double* theta, const double* Yi, const double* dt, int row0,
+                    int n_rows, int64_t n_paths, int n_fine, uint64_t seed, double* out,
+                    int n_threads) {
+    int p = sde_p(sde);
+    set_threads(n_threads);
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int r = 0; r < n_rows; ++r)
+        for (int64_t q = 0; q < n_paths; ++q) {
+            int row = row0 + r;
+            out[(int64_t)r * n_paths + q] = em_path(sde, theta + (int64_t)row * p, Yi[row], dt[row],
+                                                    n_fine, seed, (uint32_t)row, (uint32_t)q);
+        }
+    return 0;
+}
+
+static int cmp_double(const void* a, const void* b) {
+    double x = *(const double*)a, y = *(const double*)b;
+    return (x > y) - (x < y);
+}
+
+/* k-th smallest (0-based) of each segment by sorting it: out[s*n_k + j] =
+ * sorted(values[off[s]..off[s+1]))[ranks[j]]. */
+int orc_order_statistics(const double* values, const int64_t* seg_off, int n_seg,
+                         const int64_t* ranks, int n_k, double* out) {
+    for (int s = 0; s < n_seg; ++s) {
+        int64_t n = seg_off[s + 1] - seg_off[s];
+        double* tmp = (double*)malloc(sizeof(double) * (n > 0 ? n : 1));
+        memcpy(tmp, values + seg_off[s], sizeof(double) * n);
+        qsort(tmp, (size_t)n, sizeof(double), cmp_double);
+        for (int j = 0; j < n_k; ++j) out[(int64_t)s * n_k + j] = (ranks[j] < n) ? tmp[ranks[j]] : NAN;
+        free(tmp);
+    }
+    return 0;
+}
+
+/* Collocation labels y_j | (theta, Y_i, dt) (Algorithm I step 1): the
+ * empirical quantiles of n_paths EM terminal samples at levels Phi(x_j). */
+int orc_em_labels(int sde, const double* theta, const double* Yi, const double* dt, int row0,
+                  int n_rows, int64_t n_paths, int n_fine, int m, uint64_t seed, double* labels,
+                  int n_threads) {
+    int64_t ranks[64];
+    if (orc_quantile_ranks(m, n_paths, ranks) != 0) return 1;
+    double* buf = (double*)malloc(sizeof(double) * n_paths);
+    for (int r = 0; r < n_rows; ++r) {
+        orc_em_terminal(sde, theta, Yi, dt, row0 + r, 1, n_paths, n_fine, seed, buf, n_threads);
+        int64_t off[2] = {0, n_paths};
+        orc_order_statistics(buf, off, 1, ranks, m, labels + (int64_t)r * m);
+    }
+    free(buf);
+    return 0;
+}
