@@ -78,9 +78,11 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* Uniform on (0,1) from the top 24 bits of a word: ((w >> 8) + 1/2) / 2^24. */
+/* Uniform on (0,1) from the top 23 bits of a word: ((w >> 9) + 1/2) / 2^23.
+ * 23 bits keep the value exactly representable in FP32 as well as FP64, so
+ * a single-precision implementation starts from the identical number. */
 static double word_to_uniform(uint32_t w) {
-    return ((double)(w >> 8) + 0.5) * (1.0 / 16777216.0);
+    return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0);
 }
 
 /* Standard normal number `step` of the stream (seed, tag, set, path).

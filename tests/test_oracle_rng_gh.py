@@ -45,10 +45,10 @@ def test_box_muller_wiring(orc):
         w = orc.philox4x32_10([blk, q, s, tag], [seed & 0xFFFFFFFF, seed >> 32])
         z = orc.normals(seed, tag, s, q, 4 * blk, 4)
         for pair in range(2):
-            u = ((int(w[2 * pair]) >> 8) + 0.5) / 2.0 ** 24
+            u = ((int(w[2 * pair]) >> 9) + 0.5) / 2.0 ** 23
             r2 = -2.0 * math.log(u)
             assert z[2 * pair] ** 2 + z[2 * pair + 1] ** 2 == pytest.approx(r2, rel=1e-13)
-            ua = ((int(w[2 * pair + 1]) >> 8) + 0.5) / 2.0 ** 24
+            ua = ((int(w[2 * pair + 1]) >> 9) + 0.5) / 2.0 ** 23
             ang = math.atan2(z[2 * pair + 1], z[2 * pair]) % (2 * math.pi)
             assert ang == pytest.approx(2 * math.pi * ua, abs=1e-12)
 
