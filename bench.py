@@ -1,0 +1,367 @@
+"""Benchmark of the 7L online sampler on B300.
+
+One step = one batched call of the online sampler (Algorithm I steps 2-8:
+network, Philox normal, g_m, state update, FP64 per-set moments) over the
+GBM workload: 16 parameter sets theta=(mu,sigma) ~ U([0,0.2]x[0.1,0.5]),
+10^6 paths each, Y0=1, T=2, 16 coarse steps, m=7, network 4->50x4->7 ReLU.
+Metric: path-steps/s (whole job, all ranks).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16|fp32]
+                  [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own copy of
+the workload (independent parameter-set batches, seed offset by rank): weak
+scaling, no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "path-steps/s (7L online, BF16-TC vs FP32) at <=2e-3 rel err; EM label samples/s"
+UNIT = "path-steps/s"
+WORKLOAD = "GBM 7L online: 16 theta x 1e6 paths x 16 coarse steps, m=7, MLP 4->50x4->7 ReLU"
+ALG_FLOPS_PER_PATH_STEP = 2 * (4 * 50 + 3 * 50 * 50 + 50 * 7)   # 16,100 (biases excluded)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0,
+                "sm_max_mhz": 2032.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.rows, self.proc, self.bus_id = [], None, bus_id
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.bus_id:
+            cmd[1:1] = ["-i", self.bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=5)
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 9 for i in range(4)
+                          if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the FP64 oracle on the host cores (bounded sample per step)
+# ---------------------------------------------------------------------------
+def oracle_sample(params, n_per_set, threads=0):
+    import oracle
+    from paper_2302_05170_b300 import workloads as W
+    w = W.gbm_online(n_paths_per_set=n_per_set, params=params)
+    t0 = time.perf_counter()
+    yt = oracle.seven_league_paths(oracle.MODEL_MLP, np.asarray(w["params"], np.float64), w["theta"],
+                                   w["Y0"], w["offsets"], w["T"], w["n_steps"], w["m"], w["seed"],
+                                   d_in=4, threads=threads)
+    dt = time.perf_counter() - t0
+    path_steps = int(w["offsets"][-1]) * w["n_steps"]
+    return yt, w["offsets"], path_steps, dt
+
+
+def run_reference(args):
+    import oracle
+    from paper_2302_05170_b300 import workloads as W
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    oracle.build()
+    params = W.xavier_params(4, 7, seed=0)
+    n_per_set = args.ref_paths
+    cores = oracle.num_threads()
+    for _ in range(args.warmup):
+        oracle_sample(params, max(n_per_set // 10, 10))
+    total_ps, total_t = 0, 0.0
+    for _ in range(args.steps):
+        _, _, ps, dt = oracle_sample(params, n_per_set)
+        total_ps += ps
+        total_t += dt
+    v = total_ps / total_t
+    sample = "16 theta x %d paths x 16 steps per step (of 16 x 1e6)" % n_per_set
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n_sets": 16,
+                                            "paths_per_set": 10 ** 6, "n_steps": 16, "m": 7},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--paths", type=int, default=10 ** 6, help="paths per theta set")
+    ap.add_argument("--ref-paths", type=int, default=2000, help="oracle paths per set per reference step")
+    ap.add_argument("--cpu-paths", type=int, default=20000, help="oracle paths per set for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2302_05170_b300 as sl
+    from paper_2302_05170_b300 import workloads as W
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    sl.load()
+    dev = torch.device("cuda", local)
+    f32, i64 = torch.float32, torch.int64
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    params_np = W.xavier_params(4, 7, seed=0)
+    weights_kind = "Xavier-uniform seed 0 (untrained)"
+    w = W.gbm_online(n_paths_per_set=args.paths, params=params_np)
+    seed = w["seed"] + rank
+    total = int(w["offsets"][-1])
+    n_steps, m, T = w["n_steps"], w["m"], w["T"]
+    theta = torch.as_tensor(w["theta"], device=dev)
+    Y0 = torch.as_tensor(w["Y0"], device=dev)
+    off = torch.as_tensor(w["offsets"], device=dev)
+    P = torch.as_tensor(w["params"], device=dev)
+    prec = sl.PREC_BF16 if args.prec == "bf16" else sl.PREC_FP32
+    net = sl.make_net(P, 4, 7, prec=prec)
+    yt = torch.empty(total, dtype=f32, device=dev)
+    mean = torch.empty(16, dtype=torch.float64, device=dev)
+    var = torch.empty_like(mean)
+    ws = torch.empty(sl.simulate_workspace_size(total, 16), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)   # > 126 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step(out_yt=yt, out_mean=mean, out_var=var, net_=net):
+        sl.seven_league_simulate_batched(sl.MODEL_MLP, net_, theta, Y0, off, T, n_steps, m, seed,
+                                         out_YT=out_yt, out_mean=out_mean, out_var=out_var, ws=ws,
+                                         total_paths=total)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    assert sl.workspace_status(ws) == 0, "device status set during warm-up"
+    # --- timed region: K steps, L2 flushed between steps (outside the events)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(dev).pci_bus_id
+    except Exception:
+        pass
+    barrier()
+    with ClockSampler(bus) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        barrier()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    t_local = sum(ms) / 1e3
+    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    t_max = float(t.item())
+    path_steps = total * n_steps
+    value = world * path_steps * args.steps / t_max
+    launches_per_step = 3          # 7L kernel + 2 moment kernels
+
+    # --- dominant kernel alone (Y_T only: status clear + the 7L kernel)
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for a, b in kev:
+        flush.zero_()
+        a.record(stream)
+        step(out_mean=None, out_var=None)
+        b.record(stream)
+    torch.cuda.synchronize()
+    k_ms = float(np.mean([a.elapsed_time(b) for a, b in kev]))
+    peaks, peak_src = _peaks()
+    if prec == sl.PREC_BF16:
+        achieved = ALG_FLOPS_PER_PATH_STEP * path_steps / (k_ms * 1e-3) / 1e12
+        peak = peaks["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_kind": "bf16 sustained, " + peak_src}
+    else:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = sms * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+        achieved = ALG_FLOPS_PER_PATH_STEP * path_steps / (k_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_kind": "FP32 FMA: %d SMs x 128 lanes x 2 flop x %.0f MHz" % (sms, peaks["sm_max_mhz"])}
+
+    secondary = {}
+    if not args.no_secondary and rank == 0:
+        # the other form on the same paths
+        other = sl.PREC_FP32 if prec == sl.PREC_BF16 else sl.PREC_BF16
+        try:
+            net_o = sl.make_net(P, 4, 7, prec=other)
+            yt_o = torch.empty_like(yt)
+            step(out_yt=yt_o, net_=net_o)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                step(out_yt=yt_o, net_=net_o)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            o_ms = e0.elapsed_time(e1) / 3
+            key = "fp32_simt" if other == sl.PREC_FP32 else "bf16_tc"
+            secondary[key + "_path_steps_per_s"] = path_steps / (o_ms * 1e-3)
+            secondary["bf16_over_fp32"] = (value / (path_steps / (o_ms * 1e-3))) if other == sl.PREC_FP32 else \
+                (path_steps / (o_ms * 1e-3)) / value
+            a64, b64 = yt.double(), yt_o.double()
+            secondary["bf16_vs_fp32_max_rel_diff"] = float(((a64 - b64).abs() / (b64.abs() + 1.0)).max())
+        except sl.SLError as e:
+            secondary["other_form_error"] = str(e)
+        # offline stage: EM label samples/s on the CIR labels workload
+        th, yi, dtr = W.cir_label_rows(1024)
+        thd, yid, dtd = (torch.as_tensor(a, device=dev) for a in (th, yi, dtr))
+        lab = torch.empty((1024, 7), dtype=f32, device=dev)
+        wsl = torch.empty(sl.em_labels_workspace_size(1024, 10 ** 5, 7), dtype=torch.uint8, device=dev)
+        sl.em_collocation_labels(2, thd, yid, dtd, 10 ** 5, 100, 7, 1, labels=lab, ws=wsl)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            sl.em_collocation_labels(2, thd, yid, dtd, 10 ** 5, 100, 7, 1, labels=lab, ws=wsl)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        l_ms = e0.elapsed_time(e1) / 3
+        secondary["em_label_samples_per_s"] = 1024 * 10 ** 5 / (l_ms * 1e-3)
+        secondary["em_fine_steps_per_s"] = 1024 * 10 ** 5 * 100 / (l_ms * 1e-3)
+        secondary["em_labels_workload"] = "CIR 1024 rows x 1e5 paths x 100 fine steps, 7 quantiles"
+        del wsl
+
+    # --- end to end through the C ABI with host buffers (pinned), copies timed
+    h_theta = torch.as_tensor(w["theta"]).pin_memory()
+    h_y0 = torch.as_tensor(w["Y0"]).pin_memory()
+    h_off = torch.as_tensor(w["offsets"]).pin_memory()
+    h_P = torch.as_tensor(w["params"]).pin_memory()
+    h_yt = torch.empty(total, dtype=f32).pin_memory()
+    h_mom = torch.empty(32, dtype=torch.float64).pin_memory()
+    mom = torch.empty(32, dtype=torch.float64, device=dev)
+    h2d = sum(t.numel() * t.element_size() for t in (h_theta, h_y0, h_off, h_P))
+    d2h = h_yt.numel() * 4 + h_mom.numel() * 8
+    e2e_ms = []
+    for k in range(max(3, args.steps // 4) + 1):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        theta.copy_(h_theta, non_blocking=True)
+        Y0.copy_(h_y0, non_blocking=True)
+        off.copy_(h_off, non_blocking=True)
+        P.copy_(h_P, non_blocking=True)
+        sl.seven_league_simulate_batched(sl.MODEL_MLP, net, theta, Y0, off, T, n_steps, m, seed,
+                                         out_YT=yt, out_mean=mom[:16], out_var=mom[16:], ws=ws,
+                                         total_paths=total)
+        h_yt.copy_(yt, non_blocking=True)
+        h_mom.copy_(mom, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        if k:
+            e2e_ms.append(a.elapsed_time(b))
+    e2e_t = torch.tensor([float(np.mean(e2e_ms))], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
+    e2e_value = world * path_steps / (float(e2e_t.item()) * 1e-3)
+
+    cpu = None
+    accuracy = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        n_s = min(args.cpu_paths, args.paths)
+        # the oracle runs with the weights the form uses (BF16-valued for the tensor-core form)
+        Pw = W.bf16_round(params_np) if prec == sl.PREC_BF16 else params_np
+        yo, offs_o, ps, dt = oracle_sample(Pw, n_s)
+        cpu = {"value": ps / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": "first %d paths of each of the 16 theta sets, 16 steps (%d path-steps, %.1f s)"
+                         % (n_s, ps, dt)}
+        # accuracy of this run's Y_T on the sampled paths (same seed and weights)
+        idx = np.concatenate([np.arange(s * args.paths, s * args.paths + n_s) for s in range(16)])
+        g = yt.cpu().numpy()[idx].astype(np.float64)
+        err = np.abs(g - yo) / (np.abs(yo) + 1.0)
+        accuracy = {"max_rel_err": float(err.max()), "p9999_rel_err": float(np.percentile(err, 99.99)),
+                    "n_paths_checked": int(len(idx)), "metric": "|a-b|/(|b|+Y0) vs FP64 oracle"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16" if prec == sl.PREC_BF16 else "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n_sets": 16, "paths_per_set": args.paths,
+                           "n_steps": 16, "m": 7, "T": T, "weights": weights_kind,
+                           "l2": "flushed between timed steps (256 MB write, outside the events)",
+                           "parallelism": "dp%d" % world},
+                "roofline": roof, "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "cpu_baseline": cpu, "accuracy": accuracy, "kernel_ms": k_ms, "secondary": secondary}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

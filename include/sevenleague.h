@@ -1,0 +1,213 @@
+/*
+ * sevenleague.h -- C ABI of the B300 (sm_103a) Seven-League (7L) library.
+ *
+ * The 7L scheme (Liu, Colonna, Grzelak, Oosterlee, arXiv:2302.05170) samples
+ * an Ito SDE dY = a dt + b dW (Eq. 6.1) with large time steps: for every
+ * Monte Carlo path and coarse step a small network H maps (Y_i, dt, theta) to
+ * m conditional collocation points y_j (Eq. 6.3/6.4), a standard normal X is
+ * drawn and Y_{i+1} = g_m(X) is the Lagrange interpolant through
+ * (x_j, y_j) at the Gauss-Hermite points x_j (Algorithm I, steps 2-8).  The
+ * offline stage (Algorithm I step 1) produces the training labels from
+ * fine-step Euler-Maruyama paths (Eq. 6.2).
+ *
+ * Conventions (every entry point):
+ *  - Array arguments are caller-owned DEVICE pointers (e.g. a torch tensor's
+ *    data_ptr()) unless the comment says HOST.  The library never frees or
+ *    keeps them after the call.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on that stream; host-side argument
+ *    checks happen before anything is enqueued.
+ *  - Scratch memory comes from a caller buffer `ws` of `ws_bytes` bytes,
+ *    sized by the matching *_workspace_size() query, 256-byte aligned.  The
+ *    library allocates no device memory.
+ *  - Every function returns an sl_status; on failure nothing was enqueued
+ *    (SL_ERR_CUDA: a launch failed) and sl_last_error_string() says why.
+ *  - Kernels that meet non-finite state or out-of-range indices set bits of a
+ *    device status word in the first 256 bytes of `ws`; sl_workspace_status()
+ *    synchronises the stream and reports them as SL_ERR_DEVICE.
+ *  - Random numbers: X for (seed, tag, set s, path q, step i) is normal
+ *    number i of the Philox4x32-10 stream with key (seed low, seed high) and
+ *    counter (i/4, q, s, tag); Box-Muller on word pairs (0,1)/(2,3) of the
+ *    block, uniforms ((w>>9)+1/2)/2^23.  Tags: 0 = 7L online, 1 = EM fine
+ *    steps.  Results are therefore independent of launch shape and batching.
+ */
+#ifndef SEVENLEAGUE_H
+#define SEVENLEAGUE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Network shape (Section "Numerical Results": 4 hidden layers of 50). */
+#define SL_WIDTH 50
+#define SL_N_HIDDEN 4
+#define SL_MIN_M 2         /* supported collocation counts m */
+#define SL_MAX_M 8
+#define SL_MAX_DIN 8       /* FP32 form: d_in = 2 + p <= 8 */
+#define SL_MAX_DIN_TC 7    /* BF16 tensor-core form: 2*d_in + 1 <= 16 */
+#define SL_MAX_SETS (1 << 24)
+
+typedef enum {
+    SL_OK = 0,
+    SL_ERR_ARG = 1,          /* NULL pointer, negative size, inconsistent arguments */
+    SL_ERR_UNSUPPORTED = 2,  /* m outside [2,8], d_in too large, n_steps < 1, ... */
+    SL_ERR_WORKSPACE = 3,    /* ws_bytes below the *_workspace_size() requirement */
+    SL_ERR_CUDA = 4,         /* a CUDA runtime call or launch failed */
+    SL_ERR_DEVICE = 5,       /* the device status word is set (NaN/Inf state, bad index) */
+    SL_ERR_TIMEOUT = 6       /* a bounded device-side wait gave up */
+} sl_status;
+
+/* Device status word bits (read with sl_workspace_status). */
+#define SL_DEV_NONFINITE 0x1u   /* a path produced a non-finite state */
+#define SL_DEV_OFFSETS 0x2u     /* path_offsets not non-decreasing or total mismatch */
+#define SL_DEV_TIMEOUT 0x4u     /* a bounded mbarrier wait expired */
+
+/* Collocation maps H (Eq. 6.3) */
+enum { SL_MODEL_MLP = 0,        /* the network; theta = its parameter inputs (p = d_in - 2) */
+       SL_MODEL_GBM_EXACT = 1,  /* exact lognormal quantile map, theta = (mu, sigma) */
+       SL_MODEL_OU_EXACT = 2 }; /* exact OU map (Eq. 6.6), theta = (Ybar, sigma, lambda) */
+/* SDEs for the offline Euler-Maruyama stage (Eq. 6.2) */
+enum { SL_SDE_GBM = 0,          /* theta = (mu, sigma):        a = mu Y, b = sigma Y */
+       SL_SDE_OU = 1,           /* theta = (Ybar, sigma, lambda), Eq. 6.5 */
+       SL_SDE_CIR = 2 };        /* theta = (kappa, ybar, gamma), full truncation */
+enum { SL_ACT_RELU = 0, SL_ACT_SOFTPLUS = 1 };
+/* Arithmetic of the network in the online sampler */
+enum { SL_PREC_FP32 = 0,        /* FP32 CUDA-core form */
+       SL_PREC_BF16 = 1 };      /* tcgen05 BF16 tensor cores, FP32 accumulate, BF16 weights,
+                                   activations split hi+lo in BF16 (ReLU only) */
+enum { SL_PAYOFF_CALL = 0 };    /* f(Y_T) = max(Y_T - K, 0) */
+
+/*
+ * The network H of Eq. (6.3)/(6.4): d_in -> 50 -> 50 -> 50 -> 50 -> m, hidden
+ * activation `act`, linear output.  `params` (device, FP32) holds, layer by
+ * layer, W_l row-major [out][in] followed by b_l; sl_n_params() gives its
+ * length.  Input features are [Y_i, dt, theta_0 .. theta_{d_in-3}].
+ * Output j is the collocation point at the j-th Gauss-Hermite node in
+ * ascending order.  With prec = SL_PREC_BF16 the weights are rounded to BF16
+ * (nearest, ties to even) when they are staged on chip.
+ */
+typedef struct sl_net {
+    const float* params;
+    int d_in;
+    int m;
+    int act;
+    int prec;
+} sl_net;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int sl_version(void);
+/* Text for the last failing call on this host thread. */
+const char* sl_last_error_string(void);
+/* Number of parameters of the network for (d_in, m). */
+int64_t sl_n_params(int d_in, int m);
+
+/*
+ * HOST, FP64.  Gauss-Hermite points of the standard normal (probabilists'
+ * Hermite polynomial He_m), ascending, by Golub-Welsch (eigenvalues of the
+ * Jacobi matrix with off-diagonal sqrt(k)); w: probability weights
+ * (sum 1); bary: first-form barycentric weights 1/prod_{k!=j}(x_j - x_k).
+ * Any output pointer may be NULL.  Section "Methodology" (x_j are
+ * Gauss-Hermite points of X ~ N(0,1)) and Section "Parallelization"
+ * (barycentric Lagrange).  Errors: SL_ERR_UNSUPPORTED for m outside [2,8].
+ */
+int sl_gauss_hermite(int m, double* x, double* w, double* bary);
+
+/*
+ * HOST.  0-based ranks of the empirical quantiles at levels Phi(x_j) among n
+ * samples: ceil(n Phi(x_j)) - 1 clamped to [0, n-1] (Algorithm I step 1,
+ * labels y_j as quantiles of the fine-step samples).  ranks: HOST [m].
+ */
+int sl_quantile_ranks(int m, int64_t n, int64_t* ranks);
+
+/* Synchronises `stream`, then reports the device status word of `ws`
+ * (SL_OK or SL_ERR_DEVICE / SL_ERR_TIMEOUT).  *bits (HOST, may be NULL)
+ * receives the raw SL_DEV_* bits. */
+int sl_workspace_status(const void* ws, void* stream, uint32_t* bits);
+
+/* ------------------------------------------------------------------------
+ * Online stage (Algorithm I, steps 2-8).
+ * ---------------------------------------------------------------------- */
+
+/* Bytes of workspace seven_league_simulate_batched needs. */
+size_t sl_simulate_workspace_size(int64_t total_paths, int n_sets);
+
+/*
+ * Batched 7L sampler.  n_sets parameter sets; set s owns flat paths
+ * [path_offsets[s], path_offsets[s+1]) (device int64 [n_sets+1],
+ * non-decreasing, path_offsets[0] = 0, path_offsets[n_sets] = total_paths).
+ * For every path: Y_0 = Y0[s]; for i < n_steps, y = H(Y_i, dt, theta_s) with
+ * dt = T / n_steps, X = normal (seed, tag 0, s, q, i), Y_{i+1} = g_m(X) where
+ * q is the path's index within its set.
+ *   model      SL_MODEL_*; `net` is required for SL_MODEL_MLP (net->m == m,
+ *              p == net->d_in - 2) and ignored otherwise (p = 2 or 3).
+ *   theta      device FP32 [n_sets][p];  Y0: device FP32 [n_sets].
+ *   out_YT     device FP32 [total_paths] terminal values, or NULL.
+ *   out_grid   device FP32 [(n_steps+1)][total_paths] (step-major: all paths
+ *              at t_i contiguous, Algorithm I step 7), or NULL.
+ *   out_mean   device FP64 [n_sets] path means of Y_T, or NULL.
+ *   out_var    device FP64 [n_sets] unbiased sample variances, or NULL.
+ * The FP64 per-set reduction is deterministic (fixed order).
+ */
+int seven_league_simulate_batched(int model, const sl_net* net, const float* theta, int p,
+                                  const float* Y0, const int64_t* path_offsets, int n_sets,
+                                  int64_t total_paths, float T, int n_steps, int m, uint64_t seed,
+                                  float* out_YT, float* out_grid, double* out_mean,
+                                  double* out_var, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * Single parameter set, in the order (model, theta, Y0, T, n_steps, m,
+ * weights, n_paths, seed, out): theta device FP32 [p], Y0 a HOST value, out
+ * device FP32 [n_paths] terminal values.  Needs no workspace.
+ */
+int seven_league_simulate(int model, const float* theta, int p, float Y0, float T, int n_steps,
+                          int m, const sl_net* weights, int64_t n_paths, uint64_t seed,
+                          float* out, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Offline stage (Algorithm I, step 1).
+ * ---------------------------------------------------------------------- */
+
+/*
+ * Euler-Maruyama terminal samples (Eq. 6.2): row r starts at Yi[r] and takes
+ * n_fine steps of dt[r]/n_fine with normals (seed, tag 1, r, q, k); CIR uses
+ * full truncation and returns max(Y,0).  theta device FP32 [n_rows][p]
+ * (p = 2 for GBM, 3 for OU/CIR); Yi, dt device FP32 [n_rows];
+ * out device FP32 [n_rows][n_paths].
+ */
+int sl_em_terminal(int sde, const float* theta, const float* Yi, const float* dt, int n_rows,
+                   int64_t n_paths, int n_fine, uint64_t seed, float* out, void* stream);
+
+/* Bytes of workspace sl_segmented_select needs. */
+size_t sl_select_workspace_size(int n_seg, int n_k);
+
+/*
+ * Order statistics of ragged segments: out[s*n_k + j] = the ranks[j]-th
+ * smallest (0-based) value of values[seg_offsets[s] .. seg_offsets[s+1]),
+ * NaN where ranks[j] >= the segment's length.  Values must not be NaN.
+ * seg_offsets device int64 [n_seg+1]; ranks HOST int64 [n_k], n_k <= 16.
+ * Exact (radix select on the order-preserving 32-bit keys).
+ */
+int sl_segmented_select(const float* values, const int64_t* seg_offsets, int n_seg,
+                        const int64_t* ranks, int n_k, float* out, void* ws, size_t ws_bytes,
+                        void* stream);
+
+/* Bytes of workspace em_collocation_labels needs. */
+size_t sl_em_labels_workspace_size(int n_rows, int64_t n_paths, int m);
+
+/*
+ * Collocation labels y_j | (theta_r, Yi_r, dt_r): the empirical quantiles at
+ * levels Phi(x_j) (ranks from sl_quantile_ranks) of n_paths Euler-Maruyama
+ * terminal samples per row (sl_em_terminal), labels device FP32 [n_rows][m].
+ */
+int em_collocation_labels(int sde, const float* theta, const float* Yi, const float* dt,
+                          int n_rows, int64_t n_paths, int n_fine, int m, uint64_t seed,
+                          float* labels, void* ws, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEVENLEAGUE_H */

@@ -1,0 +1,269 @@
+"""B300-native Seven-League (7L) library: Python binding of libsevenleague.so.
+
+The functions below have the names of the C ABI entry points in
+``include/sevenleague.h`` and only marshal arguments: torch CUDA tensors are
+passed as device pointers together with the current CUDA stream, and scratch
+buffers are allocated with torch (PyTorch is used for device memory and
+streams only).  Every step of the computation runs in the library's kernels;
+there is no CPU fallback -- if the shared library is missing or no GPU is
+present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import workloads  # noqa: F401  (seeded synthetic inputs)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsevenleague.so")
+
+# Codes of include/sevenleague.h
+SL_OK, SL_ERR_ARG, SL_ERR_UNSUPPORTED, SL_ERR_WORKSPACE, SL_ERR_CUDA, SL_ERR_DEVICE, SL_ERR_TIMEOUT = range(7)
+MODEL_MLP, MODEL_GBM_EXACT, MODEL_OU_EXACT = 0, 1, 2
+SDE_GBM, SDE_OU, SDE_CIR = 0, 1, 2
+ACT_RELU, ACT_SOFTPLUS = 0, 1
+PREC_FP32, PREC_BF16 = 0, 1
+PAYOFF_CALL = 0
+WIDTH, N_HIDDEN, MIN_M, MAX_M = 50, 4, 2, 8
+_STATUS_NAMES = {1: "SL_ERR_ARG", 2: "SL_ERR_UNSUPPORTED", 3: "SL_ERR_WORKSPACE",
+                 4: "SL_ERR_CUDA", 5: "SL_ERR_DEVICE", 6: "SL_ERR_TIMEOUT"}
+
+# Every symbol the header declares (checked by the test suite without a GPU).
+EXPORTED = [
+    "sl_version", "sl_last_error_string", "sl_n_params", "sl_gauss_hermite",
+    "sl_quantile_ranks", "sl_workspace_status", "sl_simulate_workspace_size",
+    "seven_league_simulate_batched", "seven_league_simulate", "sl_em_terminal",
+    "sl_select_workspace_size", "sl_segmented_select", "sl_em_labels_workspace_size",
+    "em_collocation_labels",
+]
+
+
+class SLError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class sl_net(ctypes.Structure):
+    _fields_ = [("params", ctypes.c_void_p), ("d_in", ctypes.c_int), ("m", ctypes.c_int),
+                ("act", ctypes.c_int), ("prec", ctypes.c_int)]
+
+
+_lib = None
+_vp, _i, _i64, _u64, _f, _sz = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
+                                 ctypes.c_float, ctypes.c_size_t)
+
+
+def build(verbose: bool = False) -> str:
+    """Compile the CUDA sources for sm_103a (nvcc) into the in-tree library."""
+    from .build import build as _b
+    return _b(verbose=verbose)
+
+
+def load(path: str = LIB_PATH):
+    """Load libsevenleague.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libsevenleague.so not built (%s); run paper_2302_05170_b300.build()" % path)
+    L = ctypes.CDLL(path)
+    L.sl_version.restype = _i
+    L.sl_last_error_string.restype = ctypes.c_char_p
+    L.sl_n_params.argtypes = [_i, _i]
+    L.sl_n_params.restype = _i64
+    L.sl_gauss_hermite.argtypes = [_i, _vp, _vp, _vp]
+    L.sl_quantile_ranks.argtypes = [_i, _i64, _vp]
+    L.sl_workspace_status.argtypes = [_vp, _vp, _vp]
+    L.sl_simulate_workspace_size.argtypes = [_i64, _i]
+    L.sl_simulate_workspace_size.restype = _sz
+    L.seven_league_simulate_batched.argtypes = [
+        _i, ctypes.POINTER(sl_net), _vp, _i, _vp, _vp, _i, _i64, _f, _i, _i, _u64,
+        _vp, _vp, _vp, _vp, _vp, _sz, _vp]
+    L.seven_league_simulate.argtypes = [_i, _vp, _i, _f, _f, _i, _i, ctypes.POINTER(sl_net), _i64,
+                                        _u64, _vp, _vp]
+    L.sl_em_terminal.argtypes = [_i, _vp, _vp, _vp, _i, _i64, _i, _u64, _vp, _vp]
+    L.sl_select_workspace_size.argtypes = [_i, _i]
+    L.sl_select_workspace_size.restype = _sz
+    L.sl_segmented_select.argtypes = [_vp, _vp, _i, _vp, _i, _vp, _vp, _sz, _vp]
+    L.sl_em_labels_workspace_size.argtypes = [_i, _i64, _i]
+    L.sl_em_labels_workspace_size.restype = _sz
+    L.em_collocation_labels.argtypes = [_i, _vp, _vp, _vp, _i, _i64, _i, _i, _u64, _vp, _vp, _sz, _vp]
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != SL_OK:
+        raise SLError(rc, _lib.sl_last_error_string().decode())
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("a CUDA device is required (no CPU fallback)")
+    return torch
+
+
+def _ptr(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _workspace(nbytes, device):
+    torch = _torch()
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def make_net(params, d_in, m, act=ACT_RELU, prec=PREC_FP32):
+    """sl_net descriptor for a device FP32 parameter tensor (kept alive by the caller)."""
+    torch = _torch()
+    _ptr(params, torch.float32, "params")
+    if params.numel() != n_params(d_in, m):
+        raise ValueError("params has %d values, the network needs %d" % (params.numel(), n_params(d_in, m)))
+    return sl_net(params.data_ptr(), d_in, m, act, prec)
+
+
+# ---------------------------------------------------------------------------
+# Host helpers
+# ---------------------------------------------------------------------------
+def version():
+    return load().sl_version()
+
+
+def n_params(d_in, m):
+    return int(load().sl_n_params(d_in, m))
+
+
+def gauss_hermite(m):
+    L = load()
+    x, w, b = np.zeros(m), np.zeros(m), np.zeros(m)
+    _check(L.sl_gauss_hermite(m, x.ctypes.data, w.ctypes.data, b.ctypes.data))
+    return x, w, b
+
+
+def quantile_ranks(m, n):
+    L = load()
+    r = np.zeros(m, dtype=np.int64)
+    _check(L.sl_quantile_ranks(m, n, r.ctypes.data))
+    return r
+
+
+def workspace_status(ws, stream=None):
+    """Synchronises and returns the device status bits of a workspace."""
+    L = load()
+    bits = ctypes.c_uint32(0)
+    rc = L.sl_workspace_status(_ptr(ws), _stream(stream), ctypes.byref(bits))
+    if rc not in (SL_OK, SL_ERR_DEVICE, SL_ERR_TIMEOUT):
+        _check(rc)
+    return int(bits.value)
+
+
+# ---------------------------------------------------------------------------
+# Online stage
+# ---------------------------------------------------------------------------
+def simulate_workspace_size(total_paths, n_sets):
+    return int(load().sl_simulate_workspace_size(total_paths, n_sets))
+
+
+def seven_league_simulate_batched(model, net, theta, Y0, path_offsets, T, n_steps, m, seed,
+                                  out_YT=None, out_grid=None, out_mean=None, out_var=None,
+                                  ws=None, total_paths=None, stream=None):
+    """Batched 7L sampler (see include/sevenleague.h).  Tensors on the GPU.
+    Returns the workspace used (its first word is the device status)."""
+    torch = _torch()
+    L = load()
+    n_sets = path_offsets.numel() - 1
+    p = theta.shape[1] if theta.dim() == 2 else theta.numel() // max(n_sets, 1)
+    if total_paths is None:
+        total_paths = int(path_offsets[-1].item())
+    if ws is None:
+        ws = _workspace(L.sl_simulate_workspace_size(total_paths, n_sets), theta.device)
+    netp = ctypes.byref(net) if net is not None else None
+    _check(L.seven_league_simulate_batched(
+        model, netp, _ptr(theta, torch.float32, "theta"), p, _ptr(Y0, torch.float32, "Y0"),
+        _ptr(path_offsets, torch.int64, "path_offsets"), n_sets, int(total_paths), float(T),
+        n_steps, m, seed, _ptr(out_YT, torch.float32, "out_YT"),
+        _ptr(out_grid, torch.float32, "out_grid"), _ptr(out_mean, torch.float64, "out_mean"),
+        _ptr(out_var, torch.float64, "out_var"), _ptr(ws), ws.numel(), _stream(stream)))
+    return ws
+
+
+def seven_league_simulate(model, theta, Y0, T, n_steps, m, weights, n_paths, seed, out,
+                          stream=None):
+    """Single parameter set: theta device FP32 [p], Y0 a Python float, out [n_paths]."""
+    torch = _torch()
+    L = load()
+    netp = ctypes.byref(weights) if weights is not None else None
+    _check(L.seven_league_simulate(model, _ptr(theta, torch.float32, "theta"), theta.numel(),
+                                   float(Y0), float(T), n_steps, m, netp, int(n_paths), seed,
+                                   _ptr(out, torch.float32, "out"), _stream(stream)))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Offline stage
+# ---------------------------------------------------------------------------
+def em_terminal(sde, theta, Yi, dt, n_paths, n_fine, seed, out=None, stream=None):
+    torch = _torch()
+    L = load()
+    n_rows = Yi.numel()
+    if out is None:
+        out = torch.empty((n_rows, n_paths), dtype=torch.float32, device=Yi.device)
+    _check(L.sl_em_terminal(sde, _ptr(theta, torch.float32, "theta"), _ptr(Yi, torch.float32, "Yi"),
+                            _ptr(dt, torch.float32, "dt"), n_rows, int(n_paths), n_fine, seed,
+                            _ptr(out, torch.float32, "out"), _stream(stream)))
+    return out
+
+
+def segmented_select(values, seg_offsets, ranks, out=None, ws=None, stream=None):
+    torch = _torch()
+    L = load()
+    n_seg = seg_offsets.numel() - 1
+    r = np.ascontiguousarray(np.asarray(ranks, dtype=np.int64))
+    if out is None:
+        out = torch.empty((n_seg, r.size), dtype=torch.float32, device=values.device)
+    if ws is None:
+        ws = _workspace(L.sl_select_workspace_size(n_seg, r.size), values.device)
+    _check(L.sl_segmented_select(_ptr(values, torch.float32, "values"),
+                                 _ptr(seg_offsets, torch.int64, "seg_offsets"), n_seg,
+                                 r.ctypes.data, r.size, _ptr(out, torch.float32, "out"), _ptr(ws),
+                                 ws.numel(), _stream(stream)))
+    return out
+
+
+def em_labels_workspace_size(n_rows, n_paths, m):
+    return int(load().sl_em_labels_workspace_size(n_rows, n_paths, m))
+
+
+def em_collocation_labels(sde, theta, Yi, dt, n_paths, n_fine, m, seed, labels=None, ws=None,
+                          stream=None):
+    torch = _torch()
+    L = load()
+    n_rows = Yi.numel()
+    if labels is None:
+        labels = torch.empty((n_rows, m), dtype=torch.float32, device=Yi.device)
+    if ws is None:
+        ws = _workspace(L.sl_em_labels_workspace_size(n_rows, n_paths, m), Yi.device)
+    _check(L.em_collocation_labels(sde, _ptr(theta, torch.float32, "theta"),
+                                   _ptr(Yi, torch.float32, "Yi"), _ptr(dt, torch.float32, "dt"),
+                                   n_rows, int(n_paths), n_fine, m, seed,
+                                   _ptr(labels, torch.float32, "labels"), _ptr(ws), ws.numel(),
+                                   _stream(stream)))
+    return labels

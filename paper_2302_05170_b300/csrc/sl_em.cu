@@ -1,0 +1,275 @@
+// sl_em.cu -- offline stage of the 7L scheme (Algorithm I, step 1):
+// fine-step Euler-Maruyama terminal samples (Eq. 6.2) and their empirical
+// quantiles at levels Phi(x_j), the collocation labels y_j | (theta, Y_i, dt).
+//
+// EM: one thread per path, the whole fine-step loop in registers; the only
+// memory traffic is the 4-byte terminal sample.  Select: one CTA per segment,
+// exact radix select over the order-preserving 32-bit keys (4 passes of 8
+// bits, all requested ranks at once, one histogram per distinct prefix),
+// with warp-aggregated shared-memory histogram updates (__match_any_sync).
+#include <math.h>
+
+#include "sl_internal.cuh"
+
+namespace sl {
+namespace {
+
+constexpr int kEmThreads = 256;
+constexpr int kSelThreads = 512;
+constexpr int kMaxK = 16;
+
+template <int SDE>
+__global__ void __launch_bounds__(kEmThreads)
+em_terminal_kernel(const float* __restrict__ theta, const float* __restrict__ Yi,
+                   const float* __restrict__ dt, int64_t n_paths, int n_fine, uint64_t seed,
+                   float* __restrict__ out) {
+    const int r = blockIdx.y;
+    const int64_t q = static_cast<int64_t>(blockIdx.x) * kEmThreads + threadIdx.x;
+    if (q >= n_paths) return;
+    constexpr int P = (SDE == SL_SDE_GBM) ? 2 : 3;
+    const float t0 = __ldg(theta + r * P), t1 = __ldg(theta + r * P + 1);
+    const float t2 = (P == 3) ? __ldg(theta + r * P + 2) : 0.0f;
+    float Y = __ldg(Yi + r);
+    const float dtau = __ldg(dt + r) / static_cast<float>(n_fine);
+    const float sq = sqrtf(dtau);
+    for (int k = 0; k < n_fine; k += 4) {
+        const float4 z = normal4(seed, 1u, static_cast<uint32_t>(r), static_cast<uint32_t>(q),
+                                 static_cast<uint32_t>(k >> 2));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (k + u < n_fine) {
+                const float X = pick4(z, u);
+                float a, b;
+                if (SDE == SL_SDE_GBM) {            // (mu, sigma)
+                    a = t0 * Y;
+                    b = t1 * Y;
+                } else if (SDE == SL_SDE_OU) {      // (Ybar, sigma, lambda), Eq. 6.5
+                    a = -t2 * (Y - t0);
+                    b = t1;
+                } else {                            // CIR (kappa, ybar, gamma), full truncation
+                    const float yp = fmaxf(Y, 0.0f);
+                    a = t0 * (t1 - yp);
+                    b = t2 * sqrtf(yp);
+                }
+                Y = fmaf(b * sq, X, fmaf(a, dtau, Y));
+            }
+        }
+    }
+    if (SDE == SL_SDE_CIR) Y = fmaxf(Y, 0.0f);
+    out[static_cast<int64_t>(r) * n_paths + q] = Y;
+}
+
+struct RankList {
+    int64_t r[kMaxK];
+    int n;
+};
+
+// Order-preserving map float -> uint32 (-0 folded onto +0).
+__device__ __forceinline__ uint32_t float_key(float f) {
+    const uint32_t b = __float_as_uint(f + 0.0f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float key_float(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+__global__ void __launch_bounds__(kSelThreads)
+segmented_select_kernel(const float* __restrict__ values, const int64_t* __restrict__ seg_off,
+                        int64_t uniform_len, RankList ranks, float* __restrict__ out,
+                        unsigned* status) {
+    __shared__ uint32_t hist[kMaxK][256];
+    __shared__ uint32_t prefix[kMaxK], gprefix[kMaxK];
+    __shared__ int64_t rem[kMaxK];
+    __shared__ int group_of[kMaxK];
+    __shared__ int n_groups;
+    const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t a = seg_off ? seg_off[s] : static_cast<int64_t>(s) * uniform_len;
+    const int64_t n = (seg_off ? seg_off[s + 1] : a + uniform_len) - a;
+    const int nk = ranks.n;
+    if (n < 0 || n >= (int64_t(1) << 31)) {
+        if (tid == 0) raise_status(status, SL_DEV_OFFSETS);
+        if (tid < nk) out[static_cast<int64_t>(s) * nk + tid] = __int_as_float(0x7fc00000);
+        return;
+    }
+    if (tid < nk) {
+        prefix[tid] = 0u;
+        rem[tid] = ranks.r[tid];
+    }
+    __syncthreads();
+    for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 24 - 8 * pass;
+        const uint32_t hi_mask = pass == 0 ? 0u : ~((1u << (shift + 8)) - 1u);
+        if (tid == 0) {   // one histogram per distinct prefix of the still-valid ranks
+            int ng = 0;
+            for (int j = 0; j < nk; ++j) {
+                group_of[j] = -1;
+                if (rem[j] >= n) continue;
+                int g = 0;
+                while (g < ng && gprefix[g] != prefix[j]) ++g;
+                if (g == ng) gprefix[ng++] = prefix[j];
+                group_of[j] = g;
+            }
+            n_groups = ng;
+        }
+        __syncthreads();
+        const int ng = n_groups;
+        for (int i = tid; i < ng * 256; i += kSelThreads) hist[i >> 8][i & 255] = 0u;
+        __syncthreads();
+        for (int64_t base = 0; base < n; base += kSelThreads) {
+            const int64_t idx = base + tid;
+            const bool in = idx < n;
+            const uint32_t key = in ? float_key(__ldg(values + a + idx)) : 0u;
+            const uint32_t digit = (key >> shift) & 255u;
+            for (int g = 0; g < ng; ++g) {
+                const bool hit = in && ((key & hi_mask) == gprefix[g]);
+                const unsigned act = __ballot_sync(0xffffffffu, hit);
+                if (hit) {
+                    const unsigned peers = __match_any_sync(act, digit);
+                    if (lane == __ffs(peers) - 1) atomicAdd(&hist[g][digit], __popc(peers));
+                }
+            }
+        }
+        __syncthreads();
+        if (warp < nk && group_of[warp] >= 0) {   // warp j resolves rank j's digit
+            const uint32_t* h = hist[group_of[warp]];
+            uint32_t c[8], local = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                c[i] = h[lane * 8 + i];
+                local += c[i];
+            }
+            uint32_t incl = local;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int64_t rk = rem[warp];
+            const unsigned hit = __ballot_sync(0xffffffffu, rk < static_cast<int64_t>(incl));
+            const int src = __ffs(hit) - 1;
+            if (lane == src) {
+                int64_t cum = static_cast<int64_t>(incl - local);
+                int bin = 8 * lane;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    if (rk < cum + c[i]) { bin = 8 * lane + i; break; }
+                    cum += c[i];
+                }
+                rem[warp] = rk - cum;
+                prefix[warp] |= static_cast<uint32_t>(bin) << shift;
+            }
+        }
+        __syncthreads();
+    }
+    if (tid < nk)
+        out[static_cast<int64_t>(s) * nk + tid] =
+            (ranks.r[tid] < n) ? key_float(prefix[tid]) : __int_as_float(0x7fc00000);
+}
+
+int launch_em(int sde, const float* theta, const float* Yi, const float* dt, int n_rows,
+              int64_t n_paths, int n_fine, uint64_t seed, float* out, cudaStream_t st) {
+    const dim3 grid(static_cast<unsigned>((n_paths + kEmThreads - 1) / kEmThreads), n_rows);
+    if (sde == SL_SDE_GBM)
+        em_terminal_kernel<SL_SDE_GBM><<<grid, kEmThreads, 0, st>>>(theta, Yi, dt, n_paths, n_fine, seed, out);
+    else if (sde == SL_SDE_OU)
+        em_terminal_kernel<SL_SDE_OU><<<grid, kEmThreads, 0, st>>>(theta, Yi, dt, n_paths, n_fine, seed, out);
+    else
+        em_terminal_kernel<SL_SDE_CIR><<<grid, kEmThreads, 0, st>>>(theta, Yi, dt, n_paths, n_fine, seed, out);
+    return cuda_error(cudaGetLastError(), "em_terminal launch");
+}
+
+int check_em_args(int sde, const float* theta, const float* Yi, const float* dt, int n_rows,
+                  int64_t n_paths, int n_fine) {
+    if (sde != SL_SDE_GBM && sde != SL_SDE_OU && sde != SL_SDE_CIR)
+        return set_error(SL_ERR_ARG, "sde=%d", sde);
+    if (!theta || !Yi || !dt) return set_error(SL_ERR_ARG, "theta / Yi / dt == NULL");
+    if (n_rows < 0 || n_rows > 65535) return set_error(SL_ERR_UNSUPPORTED, "n_rows=%d outside [0,65535]", n_rows);
+    if (n_paths < 0 || n_paths > (int64_t(1) << 31) - 1)
+        return set_error(SL_ERR_UNSUPPORTED, "n_paths=%lld outside [0,2^31)", (long long)n_paths);
+    if (n_fine < 1) return set_error(SL_ERR_UNSUPPORTED, "n_fine=%d < 1", n_fine);
+    return SL_OK;
+}
+
+int launch_select(const float* values, const int64_t* seg_off, int64_t uniform_len, int n_seg,
+                  const int64_t* ranks, int n_k, float* out, unsigned* status, cudaStream_t st) {
+    RankList rl{};
+    rl.n = n_k;
+    for (int j = 0; j < n_k; ++j) rl.r[j] = ranks[j];
+    segmented_select_kernel<<<n_seg, kSelThreads, 0, st>>>(values, seg_off, uniform_len, rl, out, status);
+    return cuda_error(cudaGetLastError(), "segmented_select launch");
+}
+
+}  // namespace
+}  // namespace sl
+
+using namespace sl;
+
+extern "C" {
+
+int sl_em_terminal(int sde, const float* theta, const float* Yi, const float* dt, int n_rows,
+                   int64_t n_paths, int n_fine, uint64_t seed, float* out, void* stream) {
+    int rc = check_em_args(sde, theta, Yi, dt, n_rows, n_paths, n_fine);
+    if (rc) return rc;
+    if (!out) return set_error(SL_ERR_ARG, "out == NULL");
+    if (n_rows == 0 || n_paths == 0) return SL_OK;
+    return launch_em(sde, theta, Yi, dt, n_rows, n_paths, n_fine, seed, out,
+                     static_cast<cudaStream_t>(stream));
+}
+
+size_t sl_select_workspace_size(int n_seg, int n_k) {
+    (void)n_seg;
+    (void)n_k;
+    return kStatusBytes;
+}
+
+int sl_segmented_select(const float* values, const int64_t* seg_offsets, int n_seg,
+                        const int64_t* ranks, int n_k, float* out, void* ws, size_t ws_bytes,
+                        void* stream) {
+    if (n_seg < 0) return set_error(SL_ERR_ARG, "n_seg < 0");
+    if (n_k < 1 || n_k > kMaxK) return set_error(SL_ERR_UNSUPPORTED, "n_k=%d outside [1,%d]", n_k, kMaxK);
+    if (!ranks || !out || !seg_offsets) return set_error(SL_ERR_ARG, "NULL argument");
+    for (int j = 0; j < n_k; ++j)
+        if (ranks[j] < 0) return set_error(SL_ERR_ARG, "ranks[%d] < 0", j);
+    if (!ws || ws_bytes < kStatusBytes) return set_error(SL_ERR_WORKSPACE, "workspace too small");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned* status = static_cast<unsigned*>(ws);
+    int rc = cuda_error(cudaMemsetAsync(status, 0, kStatusBytes, st), "status clear");
+    if (rc) return rc;
+    if (n_seg == 0) return SL_OK;
+    if (!values) return set_error(SL_ERR_ARG, "values == NULL");
+    return launch_select(values, seg_offsets, 0, n_seg, ranks, n_k, out, status, st);
+}
+
+size_t sl_em_labels_workspace_size(int n_rows, int64_t n_paths, int m) {
+    (void)m;
+    if (n_rows < 0) n_rows = 0;
+    if (n_paths < 0) n_paths = 0;
+    return kStatusBytes + align256(static_cast<size_t>(n_rows) * static_cast<size_t>(n_paths) * 4);
+}
+
+int em_collocation_labels(int sde, const float* theta, const float* Yi, const float* dt,
+                          int n_rows, int64_t n_paths, int n_fine, int m, uint64_t seed,
+                          float* labels, void* ws, size_t ws_bytes, void* stream) {
+    int rc = check_em_args(sde, theta, Yi, dt, n_rows, n_paths, n_fine);
+    if (rc) return rc;
+    if (!labels) return set_error(SL_ERR_ARG, "labels == NULL");
+    if (n_paths < 1) return set_error(SL_ERR_ARG, "n_paths < 1");
+    int64_t ranks[SL_MAX_M];
+    rc = sl_quantile_ranks(m, n_paths, ranks);
+    if (rc) return rc;
+    const size_t need = sl_em_labels_workspace_size(n_rows, n_paths, m);
+    if (!ws || ws_bytes < need)
+        return set_error(SL_ERR_WORKSPACE, "workspace %zu bytes < %zu required", ws_bytes, need);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned char* w = static_cast<unsigned char*>(ws);
+    unsigned* status = reinterpret_cast<unsigned*>(w);
+    float* samples = reinterpret_cast<float*>(w + kStatusBytes);
+    rc = cuda_error(cudaMemsetAsync(status, 0, kStatusBytes, st), "status clear");
+    if (rc) return rc;
+    if (n_rows == 0) return SL_OK;
+    rc = launch_em(sde, theta, Yi, dt, n_rows, n_paths, n_fine, seed, samples, st);
+    if (rc) return rc;
+    return launch_select(samples, nullptr, n_paths, n_rows, ranks, m, labels, status, st);
+}
+
+}  // extern "C"

@@ -1,0 +1,299 @@
+// sl_simt.cu -- FP32 CUDA-core form of the 7L online sampler (Algorithm I,
+// steps 2-8) and the deterministic FP64 per-set moments.
+//
+// One thread owns one path for the whole time loop; the state, the network's
+// activations, the normals and the collocation vector stay in registers.  The
+// network (Eq. 6.4) is evaluated with FP32 FMAs against weights staged once per
+// CTA in shared memory (every lane of a warp reads the same weight, a
+// broadcast).  The exact-collocation models (GBM lognormal map, OU map of
+// Eq. 6.6) replace the network by their closed form.
+#include <math.h>
+
+#include "sl_internal.cuh"
+
+namespace sl {
+namespace {
+
+constexpr int W = SL_WIDTH;   // 50
+constexpr int WS = 52;        // padded row stride (16-byte aligned rows)
+constexpr int DS = 8;         // padded input width of layer 1
+
+// Shared-memory image of the network (floats).
+struct SmemNet {
+    float W1[W * DS];
+    float b1[WS];
+    float Wh[3][W * WS];
+    float bh[3][WS];
+    float W5[SL_MAX_M * WS];
+    float b5[SL_MAX_M];
+};
+
+__device__ void stage_net(SmemNet& s, const float* __restrict__ P, int d_in, int m) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const float* p = P;
+    for (int i = tid; i < W * DS; i += nt) {
+        const int o = i / DS, k = i % DS;
+        s.W1[i] = (k < d_in) ? p[o * d_in + k] : 0.0f;
+    }
+    p += W * d_in;
+    for (int i = tid; i < WS; i += nt) s.b1[i] = (i < W) ? p[i] : 0.0f;
+    p += W;
+    for (int l = 0; l < 3; ++l) {
+        for (int i = tid; i < W * WS; i += nt) {
+            const int o = i / WS, k = i % WS;
+            s.Wh[l][i] = (k < W) ? p[o * W + k] : 0.0f;
+        }
+        p += W * W;
+        for (int i = tid; i < WS; i += nt) s.bh[l][i] = (i < W) ? p[i] : 0.0f;
+        p += W;
+    }
+    for (int i = tid; i < SL_MAX_M * WS; i += nt) {
+        const int o = i / WS, k = i % WS;
+        s.W5[i] = (o < m && k < W) ? p[o * W + k] : 0.0f;
+    }
+    p += m * W;
+    for (int i = tid; i < SL_MAX_M; i += nt) s.b5[i] = (i < m) ? p[i] : 0.0f;
+}
+
+template <int ACT>
+__device__ __forceinline__ float activation(float z) {
+    if (ACT == SL_ACT_SOFTPLUS) return z > 0.0f ? z + log1pf(expf(-z)) : log1pf(expf(z));
+    return fmaxf(z, 0.0f);
+}
+
+// sum_k row[k] * in[k] over the 50 inputs (row: 16-byte aligned, stride WS).
+__device__ __forceinline__ float dot50(const float* __restrict__ row, const float (&in)[W], float acc) {
+#pragma unroll
+    for (int k = 0; k < 48; k += 4) {
+        const float4 w4 = *reinterpret_cast<const float4*>(row + k);
+        acc = fmaf(w4.x, in[k], acc);
+        acc = fmaf(w4.y, in[k + 1], acc);
+        acc = fmaf(w4.z, in[k + 2], acc);
+        acc = fmaf(w4.w, in[k + 3], acc);
+    }
+    const float2 w2 = *reinterpret_cast<const float2*>(row + 48);
+    acc = fmaf(w2.x, in[48], acc);
+    return fmaf(w2.y, in[49], acc);
+}
+
+// The network H: features f -> collocation points y (Eq. 6.4).  The inputs of
+// a layer live in registers; its outputs go to the thread's column of `act`
+// (element k at act[k * nt], conflict-free across a warp) and are reloaded as
+// the next layer's inputs.
+template <int ACT>
+__device__ __forceinline__ void mlp_forward(const SmemNet& s, float* act, int nt,
+                                            const float (&f)[DS], float (&y)[SL_MAX_M]) {
+#pragma unroll 2
+    for (int o = 0; o < W; ++o) {
+        const float4 a = *reinterpret_cast<const float4*>(s.W1 + o * DS);
+        const float4 b = *reinterpret_cast<const float4*>(s.W1 + o * DS + 4);
+        float acc = s.b1[o];
+        acc = fmaf(a.x, f[0], acc);
+        acc = fmaf(a.y, f[1], acc);
+        acc = fmaf(a.z, f[2], acc);
+        acc = fmaf(a.w, f[3], acc);
+        acc = fmaf(b.x, f[4], acc);
+        acc = fmaf(b.y, f[5], acc);
+        acc = fmaf(b.z, f[6], acc);
+        acc = fmaf(b.w, f[7], acc);
+        act[o * nt] = activation<ACT>(acc);
+    }
+    float h[W];
+    for (int l = 0; l < 3; ++l) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) h[k] = act[k * nt];
+#pragma unroll 2
+        for (int o = 0; o < W; ++o) act[o * nt] = activation<ACT>(dot50(s.Wh[l] + o * WS, h, s.bh[l][o]));
+    }
+#pragma unroll
+    for (int k = 0; k < W; ++k) h[k] = act[k * nt];
+#pragma unroll
+    for (int o = 0; o < SL_MAX_M; ++o) y[o] = dot50(s.W5 + o * WS, h, s.b5[o]);
+}
+
+// MODEL: SL_MODEL_MLP / GBM_EXACT / OU_EXACT.
+template <int MODEL, int ACT>
+__global__ void __launch_bounds__(256) simt_7l_kernel(const SimArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemNet& net = *reinterpret_cast<SmemNet*>(smem_raw);
+    float* act = reinterpret_cast<float*>(smem_raw + sizeof(SmemNet)) + threadIdx.x;
+    const int m = a.m;
+    if (MODEL == SL_MODEL_MLP) {
+        stage_net(net, a.params, a.d_in, m);
+        __syncthreads();
+    }
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < a.total;
+         g += stride) {
+        int s = 0;
+        int64_t q = g;
+        if (a.offsets) {
+            s = owning_set(a.offsets, a.n_sets, g);
+            q = g - __ldg(a.offsets + s);
+        }
+        const float* th = a.theta + static_cast<int64_t>(s) * a.p;
+        float Y = a.Y0 ? __ldg(a.Y0 + s) : a.y0_scalar;
+        if (a.out_grid) a.out_grid[g] = Y;
+
+        // Per-path constants of the exact maps (theta is fixed along the path).
+        float ex[SL_MAX_M];   // GBM: y_j = Y * ex[j];  OU: y_j = c1 * Y + ex[j]
+        float c1 = 0.0f;
+        float f[DS];
+#pragma unroll
+        for (int k = 0; k < DS; ++k) f[k] = 0.0f;
+        if (MODEL == SL_MODEL_GBM_EXACT) {
+            const float mu = __ldg(th), sg = __ldg(th + 1);
+            const float am = (mu - 0.5f * sg * sg) * a.dt, bm = sg * sqrtf(a.dt);
+#pragma unroll
+            for (int j = 0; j < SL_MAX_M; ++j) ex[j] = (j < m) ? expf(fmaf(bm, a.gh.x[j], am)) : 0.0f;
+        } else if (MODEL == SL_MODEL_OU_EXACT) {
+            const float yb = __ldg(th), sg = __ldg(th + 1), lam = __ldg(th + 2);
+            c1 = expf(-lam * a.dt);
+            const float sd = sg * sqrtf(-expm1f(-2.0f * lam * a.dt) / (2.0f * lam));
+            const float c0 = yb * (-expm1f(-lam * a.dt));
+#pragma unroll
+            for (int j = 0; j < SL_MAX_M; ++j) ex[j] = fmaf(sd, a.gh.x[j], c0);
+        } else {
+            f[1] = a.dt;
+            for (int k = 0; k < a.p && k < DS - 2; ++k) f[2 + k] = __ldg(th + k);
+        }
+
+        float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int i = 0; i < a.n_steps; ++i) {
+            if ((i & 3) == 0)
+                z4 = normal4(a.seed, 0u, static_cast<uint32_t>(s), static_cast<uint32_t>(q),
+                             static_cast<uint32_t>(i >> 2));
+            const float X = pick4(z4, i & 3);
+            float y[SL_MAX_M];
+            if (MODEL == SL_MODEL_MLP) {
+                f[0] = Y;
+                mlp_forward<ACT>(net, act, blockDim.x, f, y);
+            } else if (MODEL == SL_MODEL_GBM_EXACT) {
+#pragma unroll
+                for (int j = 0; j < SL_MAX_M; ++j) y[j] = Y * ex[j];
+            } else {
+#pragma unroll
+                for (int j = 0; j < SL_MAX_M; ++j) y[j] = fmaf(c1, Y, ex[j]);
+            }
+            Y = lagrange_eval_m(y, X, a.gh, m);
+            if (a.out_grid) a.out_grid[static_cast<int64_t>(i + 1) * a.total + g] = Y;
+        }
+        if (a.out_YT) a.out_YT[g] = Y;
+        if (!isfinite(Y)) raise_status(a.status, SL_DEV_NONFINITE);
+    }
+}
+
+constexpr int kSimtThreads = 256;
+
+template <int MODEL, int ACT>
+int launch_one(const SimArgs& a, cudaStream_t st) {
+    auto kern = simt_7l_kernel<MODEL, ACT>;
+    const size_t smem = (MODEL == SL_MODEL_MLP)
+                            ? sizeof(SmemNet) + static_cast<size_t>(W) * kSimtThreads * sizeof(float)
+                            : 0;
+    int rc = cuda_error(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem)),
+                        "simt_7l attribute");
+    if (rc) return rc;
+    int per_sm = 0;
+    rc = cuda_error(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSimtThreads, smem),
+                    "simt_7l occupancy");
+    if (rc) return rc;
+    const int64_t need = (a.total + kSimtThreads - 1) / kSimtThreads;
+    int64_t blocks = static_cast<int64_t>(sm_count()) * (per_sm > 0 ? per_sm : 1);
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    kern<<<static_cast<unsigned>(blocks), kSimtThreads, smem, st>>>(a);
+    return cuda_error(cudaGetLastError(), "simt_7l launch");
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic per-set moments.  Set s is cut into R equal chunks; CTA (s, r)
+// accumulates, in FP64, the count, sum and sum of squares of (Y_T - K_s) over
+// its chunk (K_s = the set's first value, a shift that keeps the variance
+// free of cancellation), in a fixed thread order and a fixed tree.  A second
+// kernel adds the R partials of each set in order.
+// ---------------------------------------------------------------------------
+constexpr int kMomThreads = 256;
+
+__global__ void __launch_bounds__(kMomThreads)
+set_moments_partial(const float* __restrict__ y, const int64_t* __restrict__ off, int R,
+                    double* __restrict__ part) {
+    const int s = blockIdx.x, r = blockIdx.y;
+    const int64_t a = off[s], b = off[s + 1], n = b - a;
+    const int64_t lo = a + n * r / R, hi = a + n * (r + 1) / R;
+    const double K = n > 0 ? static_cast<double>(y[a]) : 0.0;
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t g = lo + threadIdx.x; g < hi; g += kMomThreads) {
+        const double d = static_cast<double>(y[g]) - K;
+        s1 += d;
+        s2 = fma(d, d, s2);
+    }
+    __shared__ double sh1[kMomThreads], sh2[kMomThreads];
+    sh1[threadIdx.x] = s1;
+    sh2[threadIdx.x] = s2;
+    __syncthreads();
+    for (int w = kMomThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sh1[threadIdx.x] += sh1[threadIdx.x + w];
+            sh2[threadIdx.x] += sh2[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double* o = part + (static_cast<int64_t>(s) * R + r) * 2;
+        o[0] = sh1[0];
+        o[1] = sh2[0];
+    }
+}
+
+__global__ void set_moments_final(const float* __restrict__ y, const int64_t* __restrict__ off,
+                                  int n_sets, int R, const double* __restrict__ part,
+                                  double* __restrict__ mean, double* __restrict__ var) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_sets) return;
+    const int64_t a = off[s], n = off[s + 1] - a;
+    double s1 = 0.0, s2 = 0.0;
+    for (int r = 0; r < R; ++r) {
+        s1 += part[(static_cast<int64_t>(s) * R + r) * 2];
+        s2 += part[(static_cast<int64_t>(s) * R + r) * 2 + 1];
+    }
+    const double K = n > 0 ? static_cast<double>(y[a]) : 0.0;
+    const double nn = static_cast<double>(n);
+    if (mean) mean[s] = n > 0 ? K + s1 / nn : 0.0;
+    if (var) var[s] = n > 1 ? fmax(s2 - s1 * s1 / nn, 0.0) / (nn - 1.0) : 0.0;
+}
+
+int moments_chunks(int n_sets) {
+    int R = 4096 / (n_sets > 0 ? n_sets : 1);
+    return R < 1 ? 1 : (R > 64 ? 64 : R);
+}
+
+}  // namespace
+
+int launch_simt_7l(int model, int m, const SimArgs& a, cudaStream_t st) {
+    if (m < SL_MIN_M || m > SL_MAX_M) return set_error(SL_ERR_UNSUPPORTED, "m=%d", m);
+    if (model == SL_MODEL_GBM_EXACT) return launch_one<SL_MODEL_GBM_EXACT, 0>(a, st);
+    if (model == SL_MODEL_OU_EXACT) return launch_one<SL_MODEL_OU_EXACT, 0>(a, st);
+    if (a.act == SL_ACT_SOFTPLUS) return launch_one<SL_MODEL_MLP, SL_ACT_SOFTPLUS>(a, st);
+    return launch_one<SL_MODEL_MLP, SL_ACT_RELU>(a, st);
+}
+
+size_t set_moments_scratch_bytes(int n_sets) {
+    return align256(static_cast<size_t>(n_sets) * moments_chunks(n_sets) * 2 * sizeof(double));
+}
+
+int launch_set_moments(const float* y, const int64_t* offsets, int n_sets, int64_t total,
+                       double* mean, double* var, void* part, cudaStream_t st) {
+    (void)total;
+    const int R = moments_chunks(n_sets);
+    set_moments_partial<<<dim3(n_sets, R), kMomThreads, 0, st>>>(y, offsets, R,
+                                                                   static_cast<double*>(part));
+    int rc = cuda_error(cudaGetLastError(), "set_moments_partial launch");
+    if (rc) return rc;
+    set_moments_final<<<(n_sets + 127) / 128, 128, 0, st>>>(
+        y, offsets, n_sets, R, static_cast<const double*>(part), mean, var);
+    return cuda_error(cudaGetLastError(), "set_moments_final launch");
+}
+
+}  // namespace sl

@@ -1,0 +1,125 @@
+"""GPU parity of the offline stage (Algorithm I step 1) against the oracle.
+
+* Euler-Maruyama terminal samples (Eq. 6.2) for GBM, OU and CIR (full
+  truncation): FP32 against FP64 on the same Philox normals, per path within
+  1e-5 of |a - b| / (|b| + s) (s = the row's start value or long-run level).
+* Segmented order statistics: bit-exact against the oracle's sort on ragged
+  segments (empty, length 1, ties, NaN for ranks past the end).
+* Labels: the GPU's empirical quantiles differ from the oracle's by at most
+  the largest per-path sample difference of the row (order statistics are
+  1-Lipschitz in the sup norm), and equal the select of the GPU's own samples.
+* Full-size CIR workload (1024 rows x 1e5 paths x 100 fine steps): sampled
+  rows against the oracle.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2302_05170_b300 import workloads as W
+from tests.helpers import rel_err
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def _dev(a, dtype=torch.float32):
+    return torch.as_tensor(np.asarray(a), dtype=dtype, device="cuda")
+
+
+def _scale(sde, th, yi):
+    if sde == 2:
+        return np.maximum(th[:, 1], np.abs(yi))[:, None]
+    return np.abs(yi)[:, None] + 0.1
+
+
+@pytest.mark.parametrize("sde", [0, 1, 2])
+def test_em_terminal(sl, orc, sde):
+    if sde == 0:
+        th = np.array([[0.1, 0.3], [0.0, 0.5], [0.2, 0.1]], np.float32)
+        yi = np.array([1.0, 0.5, 3.0], np.float32)
+    elif sde == 1:
+        th = np.array([[0.4, 0.3, 1.5], [-0.2, 0.6, 0.3], [1.0, 0.1, 2.0]], np.float32)
+        yi = np.array([1.0, 0.0, -1.0], np.float32)
+    else:
+        th, yi, _ = W.cir_label_rows(3)
+    dt = np.array([0.5, 1.0, 0.1], np.float32)
+    n, nf = 3001, 100
+    got = sl.em_terminal(sde, _dev(th), _dev(yi), _dev(dt), n, nf, 5).cpu().numpy()
+    want = orc.em_terminal(sde, th, yi, dt, n, nf, 5)
+    err = rel_err(got, want, _scale(sde, th, yi))
+    assert err.max() <= TOL, err.max()
+    if sde == 2:
+        assert got.min() >= 0.0
+
+
+def test_em_ragged_fine_steps(sl, orc):
+    th, yi, dt = W.cir_label_rows(2)
+    for nf in (1, 3, 7, 101):
+        got = sl.em_terminal(2, _dev(th), _dev(yi), _dev(dt), 300, nf, 8).cpu().numpy()
+        want = orc.em_terminal(2, th, yi, dt, 300, nf, 8)
+        assert rel_err(got, want, _scale(2, th, yi)).max() <= TOL
+
+
+@pytest.mark.parametrize("ties", [False, True])
+def test_select_bit_exact(sl, orc, ties):
+    v, off = W.random_segments(300, 5000, seed=12, ties=ties)
+    v[:50] = -0.0 if ties else v[:50]
+    ranks = np.array([0, 1, 7, 100, 2499, 4999])
+    got = sl.segmented_select(_dev(v), _dev(off, torch.int64), ranks).cpu().numpy()
+    want = orc.order_statistics(v, off, ranks)
+    assert np.array_equal(np.isnan(got), np.isnan(want))
+    fin = ~np.isnan(want)
+    assert np.array_equal(got[fin], want[fin].astype(np.float32))
+
+
+def test_select_large_segment(sl, orc):
+    rng = np.random.default_rng(3)
+    n = 1_000_003
+    v = (rng.standard_normal(n) ** 3).astype(np.float32)
+    v[::97] = 0.0
+    off = np.array([0, 17, n], np.int64)
+    ranks = orc.quantile_ranks(7, n - 17)
+    got = sl.segmented_select(_dev(v), _dev(off, torch.int64), ranks).cpu().numpy()
+    want = orc.order_statistics(v, off, ranks)
+    assert np.array_equal(got[1], want[1].astype(np.float32))
+
+
+def test_labels_small(sl, orc):
+    th, yi, dt = W.cir_label_rows(6)
+    n, nf, m = 4000, 100, 7
+    lab = sl.em_collocation_labels(2, _dev(th), _dev(yi), _dev(dt), n, nf, m, 3).cpu().numpy()
+    got_t = sl.em_terminal(2, _dev(th), _dev(yi), _dev(dt), n, nf, 3)
+    want_t = orc.em_terminal(2, th, yi, dt, n, nf, 3)
+    want = orc.em_labels(2, th, yi, dt, n, nf, m, 3)
+    bound = np.abs(got_t.cpu().numpy() - want_t).max(axis=1)
+    assert np.all(np.abs(lab - want) <= bound[:, None] + 1e-12)
+    # labels are the select of the GPU's own samples at the oracle's ranks
+    ranks = orc.quantile_ranks(m, n)
+    offs = torch.arange(0, (len(yi) + 1) * n, n, dtype=torch.int64, device="cuda")
+    sel = sl.segmented_select(got_t.reshape(-1), offs, ranks).cpu().numpy()
+    assert np.array_equal(sel, lab)
+    assert np.array_equal(ranks, sl.quantile_ranks(m, n))
+
+
+@pytest.mark.parametrize("sde,m", [(0, 5), (1, 7)])
+def test_labels_gbm_ou(sl, orc, sde, m):
+    if sde == 0:
+        th = np.array([[0.1, 0.3], [0.05, 0.2]], np.float32)
+        yi = np.array([1.0, 0.4], np.float32)
+    else:
+        th = np.array([[0.4, 0.3, 1.5], [0.0, 0.5, 0.7]], np.float32)
+        yi = np.array([1.0, -0.3], np.float32)
+    dt = np.array([0.25, 0.5], np.float32)
+    lab = sl.em_collocation_labels(sde, _dev(th), _dev(yi), _dev(dt), 5000, 100, m, 11).cpu().numpy()
+    want = orc.em_labels(sde, th, yi, dt, 5000, 100, m, 11)
+    assert rel_err(lab, want, _scale(sde, th, yi)).max() <= TOL
+
+
+def test_full_size_cir_labels_sampled(sl, orc):
+    th, yi, dt = W.cir_label_rows(1024)
+    n, nf, m = 100_000, 100, 7
+    lab = sl.em_collocation_labels(2, _dev(th), _dev(yi), _dev(dt), n, nf, m, 1).cpu().numpy()
+    assert np.all(np.isfinite(lab)) and np.all(np.diff(lab, axis=1) >= 0) and lab.min() >= 0
+    for r in (0, 511, 1023):
+        want = orc.em_labels(2, th, yi, dt, n, nf, m, 1, row0=r, n_rows=1)[0]
+        assert rel_err(lab[r], want, max(th[r, 1], yi[r])).max() <= TOL
