@@ -166,6 +166,14 @@ int seven_league_simulate(int model, const float* theta, int p, float Y0, float 
                           int m, const sl_net* weights, int64_t n_paths, uint64_t seed,
                           float* out, void* stream);
 
+/*
+ * Tuning of the BF16 tensor-core form: number of 128-path tiles each
+ * persistent CTA keeps in flight (2..5, default 4).  Process-wide setting,
+ * read at launch time.  Returns SL_ERR_ARG outside [2,5].
+ */
+int sl_tc_set_slots(int slots);
+int sl_tc_get_slots(void);
+
 /* ------------------------------------------------------------------------
  * Offline stage (Algorithm I, step 1).
  * ---------------------------------------------------------------------- */

@@ -37,7 +37,7 @@ EXPORTED = [
     "sl_quantile_ranks", "sl_workspace_status", "sl_simulate_workspace_size",
     "seven_league_simulate_batched", "seven_league_simulate", "sl_em_terminal",
     "sl_select_workspace_size", "sl_segmented_select", "sl_em_labels_workspace_size",
-    "em_collocation_labels",
+    "em_collocation_labels", "sl_tc_set_slots", "sl_tc_get_slots",
 ]
 
 
@@ -92,6 +92,8 @@ def load(path: str = LIB_PATH):
     L.sl_em_labels_workspace_size.argtypes = [_i, _i64, _i]
     L.sl_em_labels_workspace_size.restype = _sz
     L.em_collocation_labels.argtypes = [_i, _vp, _vp, _vp, _i, _i64, _i, _i, _u64, _vp, _vp, _sz, _vp]
+    L.sl_tc_set_slots.argtypes = [_i]
+    L.sl_tc_get_slots.restype = _i
     _lib = L
     return L
 
@@ -132,12 +134,15 @@ def _workspace(nbytes, device):
 
 
 def make_net(params, d_in, m, act=ACT_RELU, prec=PREC_FP32):
-    """sl_net descriptor for a device FP32 parameter tensor (kept alive by the caller)."""
+    """sl_net descriptor for a device FP32 parameter tensor.  The descriptor keeps
+    a reference to the tensor, so its memory stays valid while the descriptor lives."""
     torch = _torch()
     _ptr(params, torch.float32, "params")
     if params.numel() != n_params(d_in, m):
         raise ValueError("params has %d values, the network needs %d" % (params.numel(), n_params(d_in, m)))
-    return sl_net(params.data_ptr(), d_in, m, act, prec)
+    net = sl_net(params.data_ptr(), d_in, m, act, prec)
+    net._params = params
+    return net
 
 
 # ---------------------------------------------------------------------------
@@ -173,6 +178,15 @@ def workspace_status(ws, stream=None):
     if rc not in (SL_OK, SL_ERR_DEVICE, SL_ERR_TIMEOUT):
         _check(rc)
     return int(bits.value)
+
+
+def tc_set_slots(slots):
+    """Path tiles in flight per CTA of the BF16 tensor-core form (2..5)."""
+    _check(load().sl_tc_set_slots(int(slots)))
+
+
+def tc_get_slots():
+    return int(load().sl_tc_get_slots())
 
 
 # ---------------------------------------------------------------------------

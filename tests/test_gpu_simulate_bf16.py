@@ -1,0 +1,131 @@
+"""GPU parity of the BF16 tcgen05 7L sampler against the FP64 oracle.
+
+The oracle runs with the same BF16-valued weights and biases (rounded to
+nearest, ties to even), so the difference measures the tensor-core form's own
+arithmetic: hi+lo BF16 activations, FP32 accumulation, FP32 state.
+Tolerance: 2e-3 on |a - b| / (|b| + Y0) per path, gated on paths whose normals
+stay within |X| <= 4 plus the 99.99th percentile over all paths.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2302_05170_b300 import workloads as W
+from tests.helpers import flat_sets, gate, max_abs_normals, rel_err
+
+pytestmark = pytest.mark.gpu
+TOL = 2e-3
+
+
+def _dev(a, dtype=torch.float32):
+    return torch.as_tensor(np.asarray(a), dtype=dtype, device="cuda")
+
+
+def _sim(sl, P, d_in, m, theta, Y0, offsets, T, n_steps, seed, prec, grid=False):
+    net = sl.make_net(_dev(P), d_in, m, prec=prec)
+    total = int(offsets[-1])
+    yt = torch.full((total,), float("nan"), dtype=torch.float32, device="cuda")
+    gr = torch.empty((n_steps + 1, total), dtype=torch.float32, device="cuda") if grid else None
+    mean = torch.empty(len(offsets) - 1, dtype=torch.float64, device="cuda")
+    ws = sl.seven_league_simulate_batched(sl.MODEL_MLP, net, _dev(theta), _dev(Y0),
+                                          _dev(offsets, torch.int64), T, n_steps, m, seed,
+                                          out_YT=yt, out_grid=gr, out_mean=mean)
+    bits = sl.workspace_status(ws)
+    assert bits == 0, bits
+    out = (yt.cpu().numpy(), mean.cpu().numpy())
+    return out + ((gr.cpu().numpy(),) if grid else ())
+
+
+def _oracle(orc, P, d_in, m, theta, Y0, offsets, T, n_steps, seed, idx=None):
+    Pb = W.bf16_round(P).astype(np.float64)
+    return orc.seven_league_paths(0, Pb, theta, Y0, offsets, T, n_steps, m, seed, d_in=d_in, idx=idx)
+
+
+def _check(orc, got, want, offsets, seed, n_steps, idx=None, tol=TOL):
+    idx = np.arange(len(want)) if idx is None else idx
+    s, q = flat_sets(offsets, idx)
+    err = rel_err(got, want, 1.0)
+    mx = max_abs_normals(orc, seed, 0, s, q, n_steps)
+    ok, max_in, p, max_all = gate(err, mx, tol)
+    assert ok, (max_in, p, max_all)
+    return max_in, p, max_all
+
+
+def test_tiny_one_tile(sl, orc):
+    """A single partial tile (37 paths), one step: the smallest launch."""
+    P = W.xavier_params(3, 5, seed=0)
+    th = np.array([[0.3]], np.float32)
+    off = W.offsets_from_counts([37])
+    yt, _ = _sim(sl, P, 3, 5, th, [1.0], off, 1.0, 1, 1, sl.PREC_BF16)
+    want = _oracle(orc, P, 3, 5, th, [1.0], off, 1.0, 1, 1)
+    assert np.all(np.isfinite(yt))
+    _check(orc, yt, want, off, 1, 1)
+
+
+def test_gbm_small(sl, orc):
+    w = W.gbm_small()
+    yt, _ = _sim(sl, w["params"], 3, 5, w["theta"], w["Y0"], w["offsets"], w["T"], w["n_steps"],
+                 w["seed"], sl.PREC_BF16)
+    want = _oracle(orc, w["params"], 3, 5, w["theta"], w["Y0"], w["offsets"], w["T"], w["n_steps"], w["seed"])
+    _check(orc, yt, want, w["offsets"], w["seed"], w["n_steps"])
+
+
+@pytest.mark.parametrize("m,d_in", [(2, 3), (5, 4), (7, 4), (7, 5), (8, 7)])
+def test_ragged_batched_grid(sl, orc, m, d_in):
+    P = W.xavier_params(d_in, m, seed=m + d_in)
+    rng = np.random.default_rng(m)
+    n_sets = 6
+    th = rng.uniform(0.05, 0.4, size=(n_sets, d_in - 2)).astype(np.float32)
+    counts = [0, 129, 1, 0, 5000, 383]
+    off = W.offsets_from_counts(counts)
+    y0 = rng.uniform(0.5, 1.5, n_sets).astype(np.float32)
+    yt, mean, grid = _sim(sl, P, d_in, m, th, y0, off, 1.5, 6, 3, sl.PREC_BF16, grid=True)
+    want = _oracle(orc, P, d_in, m, th, y0, off, 1.5, 6, 3)
+    _check(orc, yt, want, off, 3, 6)
+    assert np.array_equal(grid[-1], yt)
+    for s, c in enumerate(counts):
+        if c:
+            assert mean[s] == pytest.approx(yt[off[s]:off[s + 1]].astype(np.float64).mean(), rel=1e-12)
+
+
+@pytest.mark.parametrize("slots", [2, 3, 4, 5])
+def test_slots_bit_identical(sl, orc, slots):
+    P = W.xavier_params(4, 7, seed=1)
+    th = W.gbm_online_thetas(3)
+    off = W.offsets_from_counts([10000, 777, 20001])
+    old = sl.tc_get_slots()
+    try:
+        sl.tc_set_slots(4)
+        ref, _ = _sim(sl, P, 4, 7, th, np.ones(3, np.float32), off, 2.0, 16, 5, sl.PREC_BF16)
+        sl.tc_set_slots(slots)
+        got, _ = _sim(sl, P, 4, 7, th, np.ones(3, np.float32), off, 2.0, 16, 5, sl.PREC_BF16)
+    finally:
+        sl.tc_set_slots(old)
+    assert np.array_equal(ref, got)
+    if slots == 4:
+        idx = np.arange(0, len(ref), 7)
+        want = _oracle(orc, P, 4, 7, th, np.ones(3), off, 2.0, 16, 5, idx=idx)
+        _check(orc, ref[idx], want, off, 5, 16, idx=idx)
+
+
+def test_bf16_vs_fp32_same_paths(sl, orc):
+    P = W.xavier_params(4, 7, seed=2)
+    th = W.gbm_online_thetas(4)
+    off = W.offsets_from_counts([3000] * 4)
+    a, _ = _sim(sl, P, 4, 7, th, np.ones(4, np.float32), off, 2.0, 16, 9, sl.PREC_BF16)
+    b, _ = _sim(sl, W.bf16_round(P), 4, 7, th, np.ones(4, np.float32), off, 2.0, 16, 9, sl.PREC_FP32)
+    # both forms on the same (BF16-valued) weights and normals agree to the BF16 tolerance
+    err = rel_err(a, b, 1.0)
+    assert np.percentile(err, 99.99) <= TOL
+
+
+def test_full_size_gbm_online_sampled(sl, orc):
+    w = W.gbm_online()
+    off = w["offsets"]
+    yt, mean = _sim(sl, w["params"], 4, 7, w["theta"], w["Y0"], off, w["T"], w["n_steps"], w["seed"],
+                    sl.PREC_BF16)
+    rng = np.random.default_rng(1)
+    idx = np.unique(np.concatenate([rng.integers(0, off[-1], 3000), off[1:-1] - 1, off[:-1], [off[-1] - 1]]))
+    want = _oracle(orc, w["params"], 4, 7, w["theta"], w["Y0"], off, w["T"], w["n_steps"], w["seed"], idx=idx)
+    _check(orc, yt[idx], want, off, w["seed"], w["n_steps"], idx=idx)
+    assert np.all(np.isfinite(yt))
