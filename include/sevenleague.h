@@ -214,6 +214,47 @@ int em_collocation_labels(int sde, const float* theta, const float* Yi, const fl
                           int n_rows, int64_t n_paths, int n_fine, int m, uint64_t seed,
                           float* labels, void* ws, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Training of the network H (Algorithm I step 1: learn the map from
+ * (Y_i, dt, theta) to the collocation labels; Section "Numerical Results":
+ * Adam, batch 1024, learning rate 1e-3).  FP32 throughout.
+ * ---------------------------------------------------------------------- */
+
+/* Bytes of workspace sl_mse_grad / sl_train need for a minibatch of `batch` rows. */
+size_t sl_train_workspace_size(int d_in, int m, int batch);
+
+/* out[r][j] = H_j(feats[r]) (device FP32 [n_rows][d_in] -> [n_rows][m]); net->prec ignored. */
+int sl_mlp_forward(const sl_net* net, const float* feats, int64_t n_rows, float* out, void* stream);
+
+/*
+ * Gradient of L = 1/(n_rows*m) sum_r sum_j (H_j(f_r) - y_rj)^2 over the rows
+ * rows[0..n_rows) (device int32, NULL = 0..n_rows-1) of feats [N][d_in] and
+ * labels [N][m]: grad device FP32 [sl_n_params], *loss device FP32 (may be
+ * NULL).  Deterministic (fixed reduction order).
+ */
+int sl_mse_grad(const sl_net* net, const float* feats, const float* labels, const int32_t* rows,
+                int n_rows, float* grad, float* loss, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * One Adam step (Kingma & Ba) with step counter t >= 1 on n parameters:
+ * m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * p -= lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps).
+ */
+int sl_adam_step(float* params, float* adam_m, float* adam_v, const float* grad, int64_t n,
+                 int64_t t, float lr, float b1, float b2, float eps, void* stream);
+
+/*
+ * n_batches Adam steps (t = t0+1 .. t0+n_batches) of the MSE loss on the
+ * minibatches batch_rows[b*batch .. (b+1)*batch) (device int32): params,
+ * adam_m, adam_v device FP32 [sl_n_params(d_in, m)] updated in place;
+ * losses device FP32 [n_batches] (loss of each minibatch before its update,
+ * may be NULL).  Only kernel launches on `stream`: capturable in a CUDA graph.
+ */
+int sl_train(float* params, int d_in, int m, int act, float* adam_m, float* adam_v, int64_t t0,
+             const float* feats, const float* labels, const int32_t* batch_rows, int n_batches,
+             int batch, float lr, float b1, float b2, float eps, float* losses, void* ws,
+             size_t ws_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

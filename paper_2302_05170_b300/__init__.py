@@ -37,7 +37,8 @@ EXPORTED = [
     "sl_quantile_ranks", "sl_workspace_status", "sl_simulate_workspace_size",
     "seven_league_simulate_batched", "seven_league_simulate", "sl_em_terminal",
     "sl_select_workspace_size", "sl_segmented_select", "sl_em_labels_workspace_size",
-    "em_collocation_labels", "sl_tc_set_slots", "sl_tc_get_slots",
+    "em_collocation_labels", "sl_tc_set_slots", "sl_tc_get_slots", "sl_train_workspace_size",
+    "sl_mlp_forward", "sl_mse_grad", "sl_adam_step", "sl_train",
 ]
 
 
@@ -92,6 +93,13 @@ def load(path: str = LIB_PATH):
     L.sl_em_labels_workspace_size.argtypes = [_i, _i64, _i]
     L.sl_em_labels_workspace_size.restype = _sz
     L.em_collocation_labels.argtypes = [_i, _vp, _vp, _vp, _i, _i64, _i, _i, _u64, _vp, _vp, _sz, _vp]
+    L.sl_train_workspace_size.argtypes = [_i, _i, _i]
+    L.sl_train_workspace_size.restype = _sz
+    L.sl_mlp_forward.argtypes = [ctypes.POINTER(sl_net), _vp, _i64, _vp, _vp]
+    L.sl_mse_grad.argtypes = [ctypes.POINTER(sl_net), _vp, _vp, _vp, _i, _vp, _vp, _vp, _sz, _vp]
+    L.sl_adam_step.argtypes = [_vp, _vp, _vp, _vp, _i64, _i64, _f, _f, _f, _f, _vp]
+    L.sl_train.argtypes = [_vp, _i, _i, _i, _vp, _vp, _i64, _vp, _vp, _vp, _i, _i, _f, _f, _f, _f,
+                           _vp, _vp, _sz, _vp]
     L.sl_tc_set_slots.argtypes = [_i]
     L.sl_tc_get_slots.restype = _i
     _lib = L
@@ -281,3 +289,60 @@ def em_collocation_labels(sde, theta, Yi, dt, n_paths, n_fine, m, seed, labels=N
                                    _ptr(labels, torch.float32, "labels"), _ptr(ws), ws.numel(),
                                    _stream(stream)))
     return labels
+
+
+# ---------------------------------------------------------------------------
+# Training of the network
+# ---------------------------------------------------------------------------
+def train_workspace_size(d_in, m, batch):
+    return int(load().sl_train_workspace_size(d_in, m, batch))
+
+
+def mlp_forward(net, feats, out=None, stream=None):
+    torch = _torch()
+    L = load()
+    n = feats.shape[0]
+    if out is None:
+        out = torch.empty((n, net.m), dtype=torch.float32, device=feats.device)
+    _check(L.sl_mlp_forward(ctypes.byref(net), _ptr(feats, torch.float32, "feats"), n,
+                            _ptr(out, torch.float32, "out"), _stream(stream)))
+    return out
+
+
+def mse_grad(net, feats, labels, rows=None, stream=None):
+    """(loss tensor [1], grad tensor [n_params]) of the MSE over the given rows."""
+    torch = _torch()
+    L = load()
+    n = feats.shape[0] if rows is None else rows.numel()
+    grad = torch.empty(n_params(net.d_in, net.m), dtype=torch.float32, device=feats.device)
+    loss = torch.empty(1, dtype=torch.float32, device=feats.device)
+    ws = _workspace(L.sl_train_workspace_size(net.d_in, net.m, n), feats.device)
+    _check(L.sl_mse_grad(ctypes.byref(net), _ptr(feats, torch.float32, "feats"),
+                         _ptr(labels, torch.float32, "labels"), _ptr(rows, torch.int32, "rows"), n,
+                         _ptr(grad), _ptr(loss), _ptr(ws), ws.numel(), _stream(stream)))
+    return loss, grad
+
+
+def adam_step(params, adam_m, adam_v, grad, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, stream=None):
+    torch = _torch()
+    _check(load().sl_adam_step(_ptr(params, torch.float32), _ptr(adam_m, torch.float32),
+                               _ptr(adam_v, torch.float32), _ptr(grad, torch.float32), params.numel(),
+                               int(t), lr, b1, b2, eps, _stream(stream)))
+
+
+def train(params, d_in, m, adam_m, adam_v, t0, feats, labels, batch_rows, batch, lr=1e-3, b1=0.9,
+          b2=0.999, eps=1e-8, act=ACT_RELU, losses=None, ws=None, stream=None):
+    """len(batch_rows)//batch Adam steps in place; returns the per-step losses (device)."""
+    torch = _torch()
+    L = load()
+    nb = batch_rows.numel() // batch
+    if losses is None:
+        losses = torch.empty(nb, dtype=torch.float32, device=params.device)
+    if ws is None:
+        ws = _workspace(L.sl_train_workspace_size(d_in, m, batch), params.device)
+    _check(L.sl_train(_ptr(params, torch.float32, "params"), d_in, m, act, _ptr(adam_m, torch.float32),
+                      _ptr(adam_v, torch.float32), int(t0), _ptr(feats, torch.float32, "feats"),
+                      _ptr(labels, torch.float32, "labels"), _ptr(batch_rows, torch.int32, "batch_rows"),
+                      nb, batch, lr, b1, b2, eps, _ptr(losses, torch.float32), _ptr(ws), ws.numel(),
+                      _stream(stream)))
+    return losses
