@@ -200,6 +200,12 @@ def main():
                                          out_YT=out_yt, out_mean=out_mean, out_var=out_var, ws=ws,
                                          total_paths=total)
 
+    tuning = None
+    if prec == sl.PREC_BF16:
+        from paper_2302_05170_b300 import autotune
+        best, tms = autotune.tune_slots(lambda: step(out_mean=None, out_var=None),
+                                        "gbm-online d4 m7 s16 n%d" % total, use_cache=False)
+        tuning = {"tc_slots": best, "ms_by_slots": tms}
     for _ in range(max(args.warmup, 3)):
         step()
     assert sl.workspace_status(ws) == 0, "device status set during warm-up"
@@ -357,7 +363,8 @@ def main():
                            "parallelism": "dp%d" % world},
                 "roofline": roof, "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                "cpu_baseline": cpu, "accuracy": accuracy, "kernel_ms": k_ms, "secondary": secondary}
+                "cpu_baseline": cpu, "accuracy": accuracy, "kernel_ms": k_ms, "autotune": tuning,
+                "secondary": secondary}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

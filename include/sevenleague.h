@@ -215,6 +215,36 @@ int em_collocation_labels(int sde, const float* theta, const float* Yi, const fl
                           float* labels, void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Pathwise sensitivities (adjoint) of E[f(Y_T)], f(Y) = max(Y - K, 0).
+ * ---------------------------------------------------------------------- */
+
+/* Bytes of workspace seven_league_adjoint needs. */
+size_t sl_adjoint_workspace_size(int64_t total_paths, int n_sets, int n_steps, int ckpt_k, int p);
+
+/*
+ * Same sampling as seven_league_simulate_batched (same arguments, normals and
+ * paths); then, per path, f(Y_T) and its derivatives f'(Y_T) dY_T/dY0 and
+ * f'(Y_T) dY_T/dtheta by reverse-mode differentiation through g_m and the
+ * collocation map (network input gradient, or the exact map's derivative),
+ * with Y_i checkpointed every ckpt_k steps (1..32) in the workspace and
+ * recomputed between checkpoints.  Out-of-the-money paths (Y_T <= K) have
+ * zero sensitivities.  Per set, FP64 means (deterministic reduction):
+ *   out_value  [n_sets]       E[f(Y_T)]                      (or NULL)
+ *   out_dY0    [n_sets]       dE/dY0   * seed_grad[s]        (or NULL)
+ *   out_dtheta [n_sets][p]    dE/dtheta * seed_grad[s]       (or NULL)
+ * seed_grad: device FP64 [n_sets] upstream factors (NULL = 1), for use as the
+ * backward of an autograd function.  out_paths: device FP32 [(2+p)][total]
+ * per-path (f, df/dY0, df/dtheta_0..) or NULL (kept in the workspace).
+ * The network form is the FP32 CUDA-core form (net->prec is not used here).
+ */
+int seven_league_adjoint(int model, const sl_net* net, const float* theta, int p, const float* Y0,
+                         const int64_t* path_offsets, int n_sets, int64_t total_paths, float T,
+                         int n_steps, int m, uint64_t seed, int payoff, float K, int ckpt_k,
+                         double* out_value, double* out_dY0, double* out_dtheta,
+                         const double* seed_grad, float* out_paths, void* ws, size_t ws_bytes,
+                         void* stream);
+
+/* ------------------------------------------------------------------------
  * Training of the network H (Algorithm I step 1: learn the map from
  * (Y_i, dt, theta) to the collocation labels; Section "Numerical Results":
  * Adam, batch 1024, learning rate 1e-3).  FP32 throughout.

@@ -38,7 +38,8 @@ EXPORTED = [
     "seven_league_simulate_batched", "seven_league_simulate", "sl_em_terminal",
     "sl_select_workspace_size", "sl_segmented_select", "sl_em_labels_workspace_size",
     "em_collocation_labels", "sl_tc_set_slots", "sl_tc_get_slots", "sl_train_workspace_size",
-    "sl_mlp_forward", "sl_mse_grad", "sl_adam_step", "sl_train",
+    "sl_mlp_forward", "sl_mse_grad", "sl_adam_step", "sl_train", "sl_adjoint_workspace_size",
+    "seven_league_adjoint",
 ]
 
 
@@ -100,6 +101,10 @@ def load(path: str = LIB_PATH):
     L.sl_adam_step.argtypes = [_vp, _vp, _vp, _vp, _i64, _i64, _f, _f, _f, _f, _vp]
     L.sl_train.argtypes = [_vp, _i, _i, _i, _vp, _vp, _i64, _vp, _vp, _vp, _i, _i, _f, _f, _f, _f,
                            _vp, _vp, _sz, _vp]
+    L.sl_adjoint_workspace_size.argtypes = [_i64, _i, _i, _i, _i]
+    L.sl_adjoint_workspace_size.restype = _sz
+    L.seven_league_adjoint.argtypes = [_i, ctypes.POINTER(sl_net), _vp, _i, _vp, _vp, _i, _i64, _f, _i, _i,
+                                       _u64, _i, _f, _i, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
     L.sl_tc_set_slots.argtypes = [_i]
     L.sl_tc_get_slots.restype = _i
     _lib = L
@@ -237,6 +242,77 @@ def seven_league_simulate(model, theta, Y0, T, n_steps, m, weights, n_paths, see
                                    float(Y0), float(T), n_steps, m, netp, int(n_paths), seed,
                                    _ptr(out, torch.float32, "out"), _stream(stream)))
     return out
+
+
+def adjoint_workspace_size(total_paths, n_sets, n_steps, ckpt_k, p):
+    return int(load().sl_adjoint_workspace_size(total_paths, n_sets, n_steps, ckpt_k, p))
+
+
+def seven_league_adjoint(model, net, theta, Y0, path_offsets, T, n_steps, m, seed, K, ckpt_k=8,
+                         seed_grad=None, out_paths=None, total_paths=None, ws=None, stream=None):
+    """Returns (value [n_sets], dY0 [n_sets], dtheta [n_sets, p]) as FP64 device tensors."""
+    torch = _torch()
+    L = load()
+    n_sets = path_offsets.numel() - 1
+    p = theta.shape[1] if theta.dim() == 2 else theta.numel() // max(n_sets, 1)
+    if total_paths is None:
+        total_paths = int(path_offsets[-1].item())
+    dev = theta.device
+    value = torch.empty(n_sets, dtype=torch.float64, device=dev)
+    dY0 = torch.empty(n_sets, dtype=torch.float64, device=dev)
+    dth = torch.empty((n_sets, p), dtype=torch.float64, device=dev)
+    if ws is None:
+        ws = _workspace(L.sl_adjoint_workspace_size(total_paths, n_sets, n_steps, ckpt_k, p), dev)
+    netp = ctypes.byref(net) if net is not None else None
+    _check(L.seven_league_adjoint(
+        model, netp, _ptr(theta, torch.float32, "theta"), p, _ptr(Y0, torch.float32, "Y0"),
+        _ptr(path_offsets, torch.int64, "path_offsets"), n_sets, int(total_paths), float(T), n_steps, m,
+        seed, PAYOFF_CALL, float(K), ckpt_k, _ptr(value), _ptr(dY0), _ptr(dth),
+        _ptr(seed_grad, torch.float64, "seed_grad"), _ptr(out_paths, torch.float32, "out_paths"),
+        _ptr(ws), ws.numel(), _stream(stream)))
+    return value, dY0, dth
+
+
+class SevenLeagueCall:
+    """torch.autograd.Function: E[max(Y_T - K, 0)] per set as a differentiable
+    function of (Y0, theta); forward and backward both run the adjoint kernel
+    (the backward passes the upstream gradient in as seed_grad)."""
+
+    @staticmethod
+    def apply(Y0, theta, **kw):
+        return _autograd_fn().apply(Y0, theta, kw)
+
+
+_FN = None
+
+
+def _autograd_fn():
+    global _FN
+    if _FN is None:
+        torch = _torch()
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, Y0, theta, kw):
+                ctx.kw = kw
+                ctx.save_for_backward(Y0, theta)
+                v, _, _ = seven_league_adjoint(kw["model"], kw.get("net"), theta.detach().float().contiguous(),
+                                               Y0.detach().float().contiguous(), kw["path_offsets"], kw["T"],
+                                               kw["n_steps"], kw["m"], kw["seed"], kw["K"], kw.get("ckpt_k", 8))
+                return v
+
+            @staticmethod
+            def backward(ctx, gv):
+                Y0, theta = ctx.saved_tensors
+                kw = ctx.kw
+                _, d0, dth = seven_league_adjoint(kw["model"], kw.get("net"), theta.detach().float().contiguous(),
+                                                  Y0.detach().float().contiguous(), kw["path_offsets"], kw["T"],
+                                                  kw["n_steps"], kw["m"], kw["seed"], kw["K"], kw.get("ckpt_k", 8),
+                                                  seed_grad=gv.detach().double().contiguous())
+                return d0.to(Y0.dtype), dth.to(theta.dtype), None
+
+        _FN = _Fn
+    return _FN
 
 
 # ---------------------------------------------------------------------------

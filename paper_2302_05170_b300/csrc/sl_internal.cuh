@@ -169,7 +169,8 @@ struct SimArgs {
 int launch_simt_7l(int model, int m, const SimArgs& a, cudaStream_t s);
 int launch_tc_7l(int m, const SimArgs& a, cudaStream_t s);
 int launch_set_moments(const float* y, const int64_t* offsets, int n_sets, int64_t total,
-                       double* mean, double* var, void* part, cudaStream_t s);
+                       double* mean, double* var, void* part, cudaStream_t s, int mean_stride = 1,
+                       const double* scale = nullptr);
 size_t set_moments_scratch_bytes(int n_sets);
 
 }  // namespace sl

@@ -10,71 +10,12 @@
 #include <math.h>
 
 #include "sl_internal.cuh"
+#include "sl_simt_net.cuh"
 
 namespace sl {
 namespace {
 
-constexpr int W = SL_WIDTH;   // 50
-constexpr int WS = 52;        // padded row stride (16-byte aligned rows)
-constexpr int DS = 8;         // padded input width of layer 1
-
-// Shared-memory image of the network (floats).
-struct SmemNet {
-    float W1[W * DS];
-    float b1[WS];
-    float Wh[3][W * WS];
-    float bh[3][WS];
-    float W5[SL_MAX_M * WS];
-    float b5[SL_MAX_M];
-};
-
-__device__ void stage_net(SmemNet& s, const float* __restrict__ P, int d_in, int m) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const float* p = P;
-    for (int i = tid; i < W * DS; i += nt) {
-        const int o = i / DS, k = i % DS;
-        s.W1[i] = (k < d_in) ? p[o * d_in + k] : 0.0f;
-    }
-    p += W * d_in;
-    for (int i = tid; i < WS; i += nt) s.b1[i] = (i < W) ? p[i] : 0.0f;
-    p += W;
-    for (int l = 0; l < 3; ++l) {
-        for (int i = tid; i < W * WS; i += nt) {
-            const int o = i / WS, k = i % WS;
-            s.Wh[l][i] = (k < W) ? p[o * W + k] : 0.0f;
-        }
-        p += W * W;
-        for (int i = tid; i < WS; i += nt) s.bh[l][i] = (i < W) ? p[i] : 0.0f;
-        p += W;
-    }
-    for (int i = tid; i < SL_MAX_M * WS; i += nt) {
-        const int o = i / WS, k = i % WS;
-        s.W5[i] = (o < m && k < W) ? p[o * W + k] : 0.0f;
-    }
-    p += m * W;
-    for (int i = tid; i < SL_MAX_M; i += nt) s.b5[i] = (i < m) ? p[i] : 0.0f;
-}
-
-template <int ACT>
-__device__ __forceinline__ float activation(float z) {
-    if (ACT == SL_ACT_SOFTPLUS) return z > 0.0f ? z + log1pf(expf(-z)) : log1pf(expf(z));
-    return fmaxf(z, 0.0f);
-}
-
-// sum_k row[k] * in[k] over the 50 inputs (row: 16-byte aligned, stride WS).
-__device__ __forceinline__ float dot50(const float* __restrict__ row, const float (&in)[W], float acc) {
-#pragma unroll
-    for (int k = 0; k < 48; k += 4) {
-        const float4 w4 = *reinterpret_cast<const float4*>(row + k);
-        acc = fmaf(w4.x, in[k], acc);
-        acc = fmaf(w4.y, in[k + 1], acc);
-        acc = fmaf(w4.z, in[k + 2], acc);
-        acc = fmaf(w4.w, in[k + 3], acc);
-    }
-    const float2 w2 = *reinterpret_cast<const float2*>(row + 48);
-    acc = fmaf(w2.x, in[48], acc);
-    return fmaf(w2.y, in[49], acc);
-}
+using namespace simt;
 
 // The network H: features f -> collocation points y (Eq. 6.4).  The inputs of
 // a layer live in registers; its outputs go to the thread's column of `act`
@@ -249,7 +190,8 @@ set_moments_partial(const float* __restrict__ y, const int64_t* __restrict__ off
 
 __global__ void set_moments_final(const float* __restrict__ y, const int64_t* __restrict__ off,
                                   int n_sets, int R, const double* __restrict__ part,
-                                  double* __restrict__ mean, double* __restrict__ var) {
+                                  double* __restrict__ mean, double* __restrict__ var,
+                                  int mean_stride, const double* __restrict__ scale) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_sets) return;
     const int64_t a = off[s], n = off[s + 1] - a;
@@ -260,7 +202,7 @@ __global__ void set_moments_final(const float* __restrict__ y, const int64_t* __
     }
     const double K = n > 0 ? static_cast<double>(y[a]) : 0.0;
     const double nn = static_cast<double>(n);
-    if (mean) mean[s] = n > 0 ? K + s1 / nn : 0.0;
+    if (mean) mean[static_cast<int64_t>(s) * mean_stride] = (n > 0 ? K + s1 / nn : 0.0) * (scale ? scale[s] : 1.0);
     if (var) var[s] = n > 1 ? fmax(s2 - s1 * s1 / nn, 0.0) / (nn - 1.0) : 0.0;
 }
 
@@ -284,7 +226,8 @@ size_t set_moments_scratch_bytes(int n_sets) {
 }
 
 int launch_set_moments(const float* y, const int64_t* offsets, int n_sets, int64_t total,
-                       double* mean, double* var, void* part, cudaStream_t st) {
+                       double* mean, double* var, void* part, cudaStream_t st, int mean_stride,
+                       const double* scale) {
     (void)total;
     const int R = moments_chunks(n_sets);
     set_moments_partial<<<dim3(n_sets, R), kMomThreads, 0, st>>>(y, offsets, R,
@@ -292,7 +235,7 @@ int launch_set_moments(const float* y, const int64_t* offsets, int n_sets, int64
     int rc = cuda_error(cudaGetLastError(), "set_moments_partial launch");
     if (rc) return rc;
     set_moments_final<<<(n_sets + 127) / 128, 128, 0, st>>>(
-        y, offsets, n_sets, R, static_cast<const double*>(part), mean, var);
+        y, offsets, n_sets, R, static_cast<const double*>(part), mean, var, mean_stride, scale);
     return cuda_error(cudaGetLastError(), "set_moments_final launch");
 }
 

@@ -1,0 +1,74 @@
+// sl_simt_net.cuh -- the network H of Eq. (6.4) for FP32 CUDA-core kernels:
+// shared-memory staging of the FP32 parameters and the broadcast dot product.
+#pragma once
+
+#include "sl_internal.cuh"
+
+namespace sl {
+namespace simt {
+
+constexpr int W = SL_WIDTH;   // 50
+constexpr int WS = 52;        // padded row stride (16-byte aligned rows)
+constexpr int DS = 8;         // padded input width of layer 1
+
+// Shared-memory image of the network (floats).
+struct SmemNet {
+    float W1[W * DS];
+    float b1[WS];
+    float Wh[3][W * WS];
+    float bh[3][WS];
+    float W5[SL_MAX_M * WS];
+    float b5[SL_MAX_M];
+};
+
+__device__ inline void stage_net(SmemNet& s, const float* __restrict__ P, int d_in, int m) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const float* p = P;
+    for (int i = tid; i < W * DS; i += nt) {
+        const int o = i / DS, k = i % DS;
+        s.W1[i] = (k < d_in) ? p[o * d_in + k] : 0.0f;
+    }
+    p += W * d_in;
+    for (int i = tid; i < WS; i += nt) s.b1[i] = (i < W) ? p[i] : 0.0f;
+    p += W;
+    for (int l = 0; l < 3; ++l) {
+        for (int i = tid; i < W * WS; i += nt) {
+            const int o = i / WS, k = i % WS;
+            s.Wh[l][i] = (k < W) ? p[o * W + k] : 0.0f;
+        }
+        p += W * W;
+        for (int i = tid; i < WS; i += nt) s.bh[l][i] = (i < W) ? p[i] : 0.0f;
+        p += W;
+    }
+    for (int i = tid; i < SL_MAX_M * WS; i += nt) {
+        const int o = i / WS, k = i % WS;
+        s.W5[i] = (o < m && k < W) ? p[o * W + k] : 0.0f;
+    }
+    p += m * W;
+    for (int i = tid; i < SL_MAX_M; i += nt) s.b5[i] = (i < m) ? p[i] : 0.0f;
+}
+
+template <int ACT>
+__device__ __forceinline__ float activation(float z) {
+    if (ACT == SL_ACT_SOFTPLUS) return z > 0.0f ? z + log1pf(expf(-z)) : log1pf(expf(z));
+    return fmaxf(z, 0.0f);
+}
+
+// sum_k row[k] * in[k] over the 50 inputs (row: 16-byte aligned, stride WS).
+__device__ __forceinline__ float dot50(const float* __restrict__ row, const float (&in)[W], float acc) {
+#pragma unroll
+    for (int k = 0; k < 48; k += 4) {
+        const float4 w4 = *reinterpret_cast<const float4*>(row + k);
+        acc = fmaf(w4.x, in[k], acc);
+        acc = fmaf(w4.y, in[k + 1], acc);
+        acc = fmaf(w4.z, in[k + 2], acc);
+        acc = fmaf(w4.w, in[k + 3], acc);
+    }
+    const float2 w2 = *reinterpret_cast<const float2*>(row + 48);
+    acc = fmaf(w2.x, in[48], acc);
+    return fmaf(w2.y, in[49], acc);
+}
+
+
+}  // namespace simt
+}  // namespace sl

@@ -40,7 +40,6 @@ namespace {
 
 constexpr int kTile = 128;                    // paths per slot (MMA M, TMEM lanes)
 constexpr int kRowBytes = 128;                // one 128B-swizzle row = 64 BF16
-constexpr int kAtomRows = 8;                  // rows per swizzle atom (1024 B)
 constexpr int kAAtomBytes = kTile * kRowBytes;           // 16 KB: 128 rows x 64 cols
 constexpr int kASlotBytes = 2 * kAAtomBytes;             // K = 112 -> two 64-col atoms
 constexpr int kB1Bytes = 64 * kRowBytes;                 // layer 1: 64 rows x (16 of 64) cols
@@ -82,24 +81,37 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
     return ok != 0;
 }
 
+__device__ __forceinline__ bool mbar_test(uint32_t addr, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait for the phase with the given parity; false on abort/timeout.
-__device__ __noinline__ bool mbar_wait(uint32_t addr, uint32_t parity, volatile int* abort_flag,
-                                       unsigned* status) {
-    uint64_t t0 = 0;
-    for (uint32_t it = 0;; ++it) {
+__device__ __noinline__ bool mbar_wait_slow(uint32_t addr, uint32_t parity, volatile int* abort_flag,
+                                            unsigned* status) {
+    const uint64_t t0 = global_ns();
+    while (true) {
         if (mbar_try_wait(addr, parity)) return true;
-        if ((it & 255u) == 255u) {
-            if (*abort_flag) return false;
-            const uint64_t now = global_ns();
-            if (t0 == 0) {
-                t0 = now;
-            } else if (now - t0 > kTimeoutNs) {
-                *abort_flag = 1;
-                raise_status(status, SL_DEV_TIMEOUT);
-                return false;
-            }
+        if (*abort_flag) return false;
+        if (global_ns() - t0 > kTimeoutNs) {
+            *abort_flag = 1;
+            raise_status(status, SL_DEV_TIMEOUT);
+            return false;
         }
     }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, volatile int* abort_flag,
+                                          unsigned* status) {
+#pragma unroll 1
+    for (int it = 0; it < 64; ++it)
+        if (mbar_try_wait(addr, parity)) return true;
+    return mbar_wait_slow(addr, parity, abort_flag, status);
 }
 
 __device__ __forceinline__ void fence_proxy_async_smem() {
@@ -151,6 +163,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
           "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
           "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
           "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15])
         : "r"(taddr));
 }
 
@@ -288,28 +309,25 @@ __global__ void __launch_bounds__(32 * (4 * S + 1), 1) tc_7l_kernel(const SimArg
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t sB_u = smem_u32(sB), sA_u = smem_u32(sA);
-            int64_t remaining[S];
+            int remaining[S];
             int layer[S];
             uint32_t aph[S];
+            int64_t left = 0;
 #pragma unroll
             for (int t = 0; t < S; ++t) {
                 const int64_t first = static_cast<int64_t>(blockIdx.x) * S + t;
                 const int64_t ntl = first < n_tiles ? (n_tiles - 1 - first) / tile_stride + 1 : 0;
-                remaining[t] = ntl * a.n_steps * 5;
+                remaining[t] = static_cast<int>(ntl * a.n_steps * 5);
+                left += remaining[t];
                 layer[t] = 0;
                 aph[t] = 0;
             }
-            bool ok = true, any = true;
-            while (ok && any) {
-                any = false;
+            uint64_t idle_since = 0;
+            while (left > 0) {
+                bool issued = false;
 #pragma unroll
                 for (int t = 0; t < S; ++t) {
-                    if (!ok || remaining[t] == 0) continue;
-                    any = true;
-                    if (!mbar_wait(smem_u32(&bars[t]), aph[t], abort_flag, a.status)) {
-                        ok = false;
-                        continue;
-                    }
+                    if (remaining[t] == 0 || !mbar_test(smem_u32(&bars[t]), aph[t])) continue;
                     aph[t] ^= 1u;
                     tc_fence_after();
                     const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(t * 64);
@@ -333,6 +351,20 @@ __global__ void __launch_bounds__(32 * (4 * S + 1), 1) tc_7l_kernel(const SimArg
                     mma_commit(smem_u32(&bars[S + t]));
                     layer[t] = (l == 4) ? 0 : l + 1;
                     --remaining[t];
+                    --left;
+                    issued = true;
+                }
+                if (issued) {
+                    idle_since = 0;
+                } else {   // bounded idling: give up after ~1 s with nothing ready
+                    const uint64_t now = global_ns();
+                    if (idle_since == 0) idle_since = now;
+                    else if (now - idle_since > kTimeoutNs) {
+                        *abort_flag = 1;
+                        raise_status(a.status, SL_DEV_TIMEOUT);
+                        break;
+                    }
+                    if (*abort_flag) break;
                 }
             }
             // Drain: wait until every MMA this thread issued has completed.
@@ -371,10 +403,10 @@ __global__ void __launch_bounds__(32 * (4 * S + 1), 1) tc_7l_kernel(const SimArg
             ts.q = static_cast<uint32_t>(qq);
             const float* th = a.theta + static_cast<int64_t>(ts.s) * a.p;
             float feat[SL_MAX_DIN_TC];
-#pragma unroll
-            for (int k = 0; k < SL_MAX_DIN_TC; ++k) feat[k] = 0.0f;
+            feat[0] = 0.0f;
             feat[1] = dt;
-            for (int k = 0; k < a.p && k < SL_MAX_DIN_TC - 2; ++k) feat[2 + k] = __ldg(th + k);
+#pragma unroll
+            for (int k = 0; k < SL_MAX_DIN_TC - 2; ++k) feat[2 + k] = (k < a.p) ? __ldg(th + k) : 0.0f;
             float Y = a.Y0 ? __ldg(a.Y0 + ts.s) : a.y0_scalar;
             if (a.out_grid && ts.valid) a.out_grid[ts.g] = Y;
             float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -389,8 +421,7 @@ __global__ void __launch_bounds__(32 * (4 * S + 1), 1) tc_7l_kernel(const SimArg
                 for (int k = 0; k < SL_MAX_DIN_TC; ++k) {
                     const float hi = __uint_as_float(__float_as_uint(feat[k]) & 0xFFFF0000u);
                     const uint32_t wv = pack_rn(hi, feat[k] - hi);
-                    if (k < a.d_in) fw[k] = wv;
-                    else if (k == a.d_in) fw[k] = 0x00003F80u;    // 1.0 in the low half
+                    fw[k] = (k < a.d_in) ? wv : ((k == a.d_in) ? 0x00003F80u : 0u);   // 1.0 after the features
                 }
                 if (a.d_in == SL_MAX_DIN_TC) fw[7] = 0x00003F80u;
                 st_shared_v4(a_slot + sw128_chunk(r, 0), fw[0], fw[1], fw[2], fw[3]);
@@ -407,35 +438,52 @@ __global__ void __launch_bounds__(32 * (4 * S + 1), 1) tc_7l_kernel(const SimArg
                     if (!ok) break;
                     dph ^= 1u;
                     tc_fence_after();
-                    uint32_t v0[32], v1[32];
-                    tmem_ld32(taddr, v0);
-                    tmem_ld32(taddr + 32, v1);
-                    tmem_wait_ld();
-                    uint32_t hw[26], lw[26];
+                    // columns 0..31: hi words 0..15 (chunks 0-3), lo words 28..43
+                    // (chunk 7, atom-1 chunks 0-2)
+                    {
+                        uint32_t v[32];
+                        tmem_ld32(taddr, v);
+                        tmem_wait_ld();
+                        uint32_t hw[16], lw[16];
 #pragma unroll
-                    for (int i2 = 0; i2 < 25; ++i2) {
-                        const uint32_t ua = (i2 < 16) ? v0[2 * i2] : v1[2 * i2 - 32];
-                        const uint32_t ub = (i2 < 16) ? v0[2 * i2 + 1] : v1[2 * i2 + 1 - 32];
-                        const float fa = __uint_as_float(ua), fb = __uint_as_float(ub);
-                        const float ha = __uint_as_float(ua & 0xFFFF0000u);
-                        const float hb = __uint_as_float(ub & 0xFFFF0000u);
-                        hw[i2] = pack_relu(ha, hb);
-                        lw[i2] = pack_relu(fa - ha, fb - hb);
+                        for (int i2 = 0; i2 < 16; ++i2) {
+                            const float ha = __uint_as_float(v[2 * i2] & 0xFFFF0000u);
+                            const float hb = __uint_as_float(v[2 * i2 + 1] & 0xFFFF0000u);
+                            hw[i2] = pack_relu(ha, hb);
+                            lw[i2] = pack_relu(__uint_as_float(v[2 * i2]) - ha, __uint_as_float(v[2 * i2 + 1]) - hb);
+                        }
+#pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            st_shared_v4(a_slot + sw128_chunk(r, c), hw[4 * c], hw[4 * c + 1], hw[4 * c + 2], hw[4 * c + 3]);
+                        st_shared_v4(a_slot + sw128_chunk(r, 7), lw[0], lw[1], lw[2], lw[3]);
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            st_shared_v4(a_slot + kAAtomBytes + sw128_chunk(r, c), lw[4 + 4 * c], lw[5 + 4 * c],
+                                         lw[6 + 4 * c], lw[7 + 4 * c]);
                     }
-                    hw[25] = 0x00003F80u;   // columns 50 (bias unit = 1.0) and 51 (0)
-                    lw[25] = 0u;
-                    // words: hi 0..24, 25 = {1,0}, 26..27 = 0, lo 28..52, 53..55 = 0
+                    // columns 32..49: hi words 16..24 (+ the constant-1 word 25), lo words 44..52
+                    {
+                        uint32_t v[16], u[8];
+                        tmem_ld16(taddr + 32, v);
+                        tmem_ld8(taddr + 48, u);
+                        tmem_wait_ld();
+                        uint32_t hw[9], lw[9];
 #pragma unroll
-                    for (int c = 0; c < 6; ++c)
-                        st_shared_v4(a_slot + sw128_chunk(r, c), hw[4 * c], hw[4 * c + 1],
-                                     hw[4 * c + 2], hw[4 * c + 3]);
-                    st_shared_v4(a_slot + sw128_chunk(r, 6), hw[24], hw[25], 0u, 0u);
-                    st_shared_v4(a_slot + sw128_chunk(r, 7), lw[0], lw[1], lw[2], lw[3]);
-#pragma unroll
-                    for (int c = 0; c < 5; ++c)
-                        st_shared_v4(a_slot + kAAtomBytes + sw128_chunk(r, c), lw[4 + 4 * c],
-                                     lw[5 + 4 * c], lw[6 + 4 * c], lw[7 + 4 * c]);
-                    st_shared_v4(a_slot + kAAtomBytes + sw128_chunk(r, 5), lw[24], 0u, 0u, 0u);
+                        for (int i2 = 0; i2 < 9; ++i2) {
+                            const uint32_t ua = (i2 < 8) ? v[2 * i2] : u[0];
+                            const uint32_t ub = (i2 < 8) ? v[2 * i2 + 1] : u[1];
+                            const float ha = __uint_as_float(ua & 0xFFFF0000u);
+                            const float hb = __uint_as_float(ub & 0xFFFF0000u);
+                            hw[i2] = pack_relu(ha, hb);
+                            lw[i2] = pack_relu(__uint_as_float(ua) - ha, __uint_as_float(ub) - hb);
+                        }
+                        st_shared_v4(a_slot + sw128_chunk(r, 4), hw[0], hw[1], hw[2], hw[3]);
+                        st_shared_v4(a_slot + sw128_chunk(r, 5), hw[4], hw[5], hw[6], hw[7]);
+                        st_shared_v4(a_slot + sw128_chunk(r, 6), hw[8], 0x00003F80u, 0u, 0u);
+                        st_shared_v4(a_slot + kAAtomBytes + sw128_chunk(r, 3), lw[0], lw[1], lw[2], lw[3]);
+                        st_shared_v4(a_slot + kAAtomBytes + sw128_chunk(r, 4), lw[4], lw[5], lw[6], lw[7]);
+                        st_shared_v4(a_slot + kAAtomBytes + sw128_chunk(r, 5), lw[8], 0u, 0u, 0u);
+                    }
                     fence_proxy_async_smem();
                     tc_fence_before();
                     __syncwarp();
@@ -494,6 +542,11 @@ int launch_s(const SimArgs& a, cudaStream_t st) {
     const int64_t need = (n_tiles + S - 1) / S;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
+    // per-slot MMA-group counters are 32-bit
+    const int64_t tiles_per_slot = (n_tiles + grid * S - 1) / (grid * S);
+    if (tiles_per_slot * a.n_steps * 5 >= (int64_t(1) << 31))
+        return set_error(SL_ERR_UNSUPPORTED, "too many path-steps for one launch (%lld tiles per slot x %d steps)",
+                         static_cast<long long>(tiles_per_slot), a.n_steps);
     kern<<<static_cast<unsigned>(grid), 32 * (4 * S + 1), smem, st>>>(a);
     return cuda_error(cudaGetLastError(), "tc_7l launch");
 }
