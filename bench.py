@@ -154,6 +154,8 @@ def main():
     ap.add_argument("--cpu-paths", type=int, default=20000, help="oracle paths per set for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--weights", default="trained", choices=["trained", "xavier"])
+    ap.add_argument("--train-steps", type=int, default=40000)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -176,8 +178,17 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    params_np = W.xavier_params(4, 7, seed=0)
-    weights_kind = "Xavier-uniform seed 0 (untrained)"
+    if args.weights == "trained":
+        from paper_2302_05170_b300 import pipeline
+        P_tr, losses_tr, _ = pipeline.train_gbm_online_network(n_rows=1 << 15, n_steps=args.train_steps)
+        torch.cuda.synchronize()
+        params_np = P_tr.cpu().numpy()
+        weights_kind = ("trained on the GPU: em_collocation_labels (GBM, 32768 rows x 1e5 paths x 100 fine "
+                        "steps, dt in {0.125,0.25,0.5,1}) + %d Adam steps (final loss %.3g)"
+                        % (args.train_steps, float(np.mean(losses_tr[-100:]))))
+    else:
+        params_np = W.xavier_params(4, 7, seed=0)
+        weights_kind = "Xavier-uniform seed 0 (untrained)"
     w = W.gbm_online(n_paths_per_set=args.paths, params=params_np)
     seed = w["seed"] + rank
     total = int(w["offsets"][-1])
@@ -300,6 +311,67 @@ def main():
         secondary["em_fine_steps_per_s"] = 1024 * 10 ** 5 * 100 / (l_ms * 1e-3)
         secondary["em_labels_workload"] = "CIR 1024 rows x 1e5 paths x 100 fine steps, 7 quantiles"
         del wsl
+        # CIR network trained on those labels, then the batched CIR workload: 4096 theta sets with
+        # log-uniform path counts in [1e3, 1e5], 32 steps, in one persistent launch replayed from a
+        # captured CUDA graph
+        from paper_2302_05170_b300 import pipeline
+        feats_c = torch.cat([yid[:, None], dtd[:, None], thd], 1).contiguous()
+        P_c = torch.as_tensor(W.xavier_params(5, 7, seed=0), device=dev)
+        am_c, av_c = torch.zeros_like(P_c), torch.zeros_like(P_c)
+        for c in range(10):
+            rows_c = torch.as_tensor(W.minibatch_rows(1024, 1024, 1000, seed=40 + c), device=dev)
+            sl.train(P_c, 5, 7, am_c, av_c, 1000 * c, feats_c, lab, rows_c, 1024, lr=1e-3 * 0.01 ** (c / 9))
+        cb = W.cir_batched()
+        tot_c = int(cb["offsets"][-1])
+        net_c = sl.make_net(P_c, 5, 7, prec=prec)
+        th_c, y0_c = torch.as_tensor(cb["theta"], device=dev), torch.as_tensor(cb["Y0"], device=dev)
+        off_c = torch.as_tensor(cb["offsets"], device=dev)
+        yt_c = torch.empty(tot_c, dtype=f32, device=dev)
+        mean_c = torch.empty(4096, dtype=torch.float64, device=dev)
+        var_c = torch.empty_like(mean_c)
+        ws_c = torch.empty(sl.simulate_workspace_size(tot_c, 4096), dtype=torch.uint8, device=dev)
+        run_c = lambda: sl.seven_league_simulate_batched(sl.MODEL_MLP, net_c, th_c, y0_c, off_c, cb["T"],
+                                                         cb["n_steps"], 7, cb["seed"], out_YT=yt_c,
+                                                         out_mean=mean_c, out_var=var_c, ws=ws_c,
+                                                         total_paths=tot_c)
+        run_c()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            run_c()
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        c_ms = e0.elapsed_time(e1) / 3
+        assert sl.workspace_status(ws_c) == 0
+        secondary["cir_batched_path_steps_per_s"] = tot_c * cb["n_steps"] / (c_ms * 1e-3)
+        secondary["cir_batched_workload"] = ("CIR 4096 theta sets, %d paths (log-uniform 1e3..1e5 per set), "
+                                             "32 steps, m=7, one persistent launch in a CUDA graph" % tot_c)
+        del yt_c, ws_c
+        # adjoint: GBM network, 1e6 paths, 64 steps, checkpoint every 8 steps, K = 1
+        n_a = 10 ** 6
+        off_a = torch.as_tensor(W.offsets_from_counts([n_a]), device=dev)
+        net_a = sl.make_net(P, 4, 7, prec=sl.PREC_FP32)
+        th_a = torch.tensor([[0.1, 0.3]], device=dev)
+        y0_a = torch.ones(1, device=dev)
+        ws_a = torch.empty(sl.adjoint_workspace_size(n_a, 1, 64, 8, 2), dtype=torch.uint8, device=dev)
+        run_a = lambda: sl.seven_league_adjoint(sl.MODEL_MLP, net_a, th_a, y0_a, off_a, 1.0, 64, 7, 1, 1.0,
+                                                ckpt_k=8, ws=ws_a, total_paths=n_a)
+        run_a()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        v_a, d0_a, dth_a = run_a()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        secondary["adjoint_path_steps_per_s"] = n_a * 64 / (e0.elapsed_time(e1) * 1e-3)
+        secondary["adjoint_workload"] = ("GBM network (FP32 form), 1e6 paths x 64 steps, checkpoint every 8, "
+                                         "call K=1: value %.5f dY0 %.5f dtheta %s"
+                                         % (v_a.item(), d0_a.item(), [round(x, 5) for x in dth_a[0].tolist()]))
 
     # --- end to end through the C ABI with host buffers (pinned), copies timed
     h_theta = torch.as_tensor(w["theta"]).pin_memory()

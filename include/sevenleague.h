@@ -173,6 +173,10 @@ int seven_league_simulate(int model, const float* theta, int p, float Y0, float 
  */
 int sl_tc_set_slots(int slots);
 int sl_tc_get_slots(void);
+/* 1 (default): the BF16 form keeps the network's activations (the MMA A
+ * operand) in tensor memory beside the accumulator (used when slots <= 4);
+ * 0: in shared memory.  Process-wide, read at launch time. */
+int sl_tc_set_a_operand(int in_tensor_memory);
 
 /* ------------------------------------------------------------------------
  * Offline stage (Algorithm I, step 1).

@@ -37,7 +37,7 @@ EXPORTED = [
     "sl_quantile_ranks", "sl_workspace_status", "sl_simulate_workspace_size",
     "seven_league_simulate_batched", "seven_league_simulate", "sl_em_terminal",
     "sl_select_workspace_size", "sl_segmented_select", "sl_em_labels_workspace_size",
-    "em_collocation_labels", "sl_tc_set_slots", "sl_tc_get_slots", "sl_train_workspace_size",
+    "em_collocation_labels", "sl_tc_set_slots", "sl_tc_get_slots", "sl_tc_set_a_operand", "sl_train_workspace_size",
     "sl_mlp_forward", "sl_mse_grad", "sl_adam_step", "sl_train", "sl_adjoint_workspace_size",
     "seven_league_adjoint",
 ]
@@ -105,6 +105,7 @@ def load(path: str = LIB_PATH):
     L.sl_adjoint_workspace_size.restype = _sz
     L.seven_league_adjoint.argtypes = [_i, ctypes.POINTER(sl_net), _vp, _i, _vp, _vp, _i, _i64, _f, _i, _i,
                                        _u64, _i, _f, _i, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
+    L.sl_tc_set_a_operand.argtypes = [_i]
     L.sl_tc_set_slots.argtypes = [_i]
     L.sl_tc_get_slots.restype = _i
     _lib = L
@@ -200,6 +201,11 @@ def tc_set_slots(slots):
 
 def tc_get_slots():
     return int(load().sl_tc_get_slots())
+
+
+def tc_set_a_operand(in_tensor_memory):
+    """Where the BF16 form keeps the MMA A operand: tensor memory (True) or shared memory."""
+    _check(load().sl_tc_set_a_operand(1 if in_tensor_memory else 0))
 
 
 # ---------------------------------------------------------------------------

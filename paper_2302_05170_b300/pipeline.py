@@ -1,0 +1,50 @@
+"""Offline stage of the 7L scheme (Algorithm I, step 1), end to end on the GPU.
+
+Label rows (theta, Y_i, dt) -> em_collocation_labels (fine-step Euler-Maruyama
+and empirical quantiles at Phi(x_j)) -> Adam training of the network on
+(Y_i, dt, theta) -> labels, in the library's kernels.  Adam with batch 1024
+and learning rate 1e-3 are the experiments section's settings; the rate then
+decays geometrically to lr_end over the run (piecewise constant, n_chunks
+pieces), because at a fixed 1e-3 the Adam noise keeps the network's per-step
+error, and so the sampler's strong error, from settling.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import workloads as W
+
+
+def train_network(sde, theta, Yi, dt, m, n_paths=100_000, n_fine=100, label_seed=7, n_steps=40_000,
+                  batch=1024, lr0=1e-3, lr_end=1e-5, n_chunks=20, act=0, init_seed=0, shuffle_seed=3,
+                  device="cuda"):
+    """Returns (params FP32 device tensor, losses numpy array, labels device tensor)."""
+    import torch
+    import paper_2302_05170_b300 as sl
+
+    th = torch.as_tensor(np.asarray(theta, np.float32), device=device)
+    yi = torch.as_tensor(np.asarray(Yi, np.float32), device=device)
+    dtv = torch.as_tensor(np.asarray(dt, np.float32), device=device)
+    n_rows = yi.numel()
+    labels = sl.em_collocation_labels(sde, th, yi, dtv, n_paths, n_fine, m, label_seed)
+    feats = torch.cat([yi[:, None], dtv[:, None], th.reshape(n_rows, -1)], 1).contiguous()
+    d_in = feats.shape[1]
+    P = torch.as_tensor(W.xavier_params(d_in, m, seed=init_seed), device=device)
+    am, av = torch.zeros_like(P), torch.zeros_like(P)
+    ws = torch.empty(sl.train_workspace_size(d_in, m, batch), dtype=torch.uint8, device=device)
+    per = max(1, n_steps // n_chunks)
+    losses, t0 = [], 0
+    for c in range(n_chunks):
+        lr = lr0 * (lr_end / lr0) ** (c / max(1, n_chunks - 1))
+        rows = torch.as_tensor(W.minibatch_rows(n_rows, batch, per, seed=shuffle_seed + c), device=device)
+        lo = sl.train(P, d_in, m, am, av, t0, feats, labels, rows, batch, lr=float(lr), act=act, ws=ws)
+        losses.append(lo)
+        t0 += per
+    return P, torch.cat(losses).cpu().numpy(), labels
+
+
+def train_gbm_online_network(n_rows=1 << 15, n_steps=40_000, dts=(0.125, 0.25, 0.5, 1.0), device="cuda"):
+    """The network of the GBM online workload (d_in = 4: Y, dt, mu, sigma; m = 7), trained
+    on labels for theta in [0,0.2]x[0.1,0.5], Y_i log-uniform on [0.25,4] and dt in `dts`."""
+    th, yi, dt = W.gbm_training_rows(n_rows, seed=2, dts=dts)
+    return train_network(0, th, yi, dt, 7, n_steps=n_steps, device=device)

@@ -107,15 +107,16 @@ def gbm_online(n_paths_per_set: int = 1_000_000, n_sets: int = 16, params=None):
                 seed=1, params=params if params is not None else xavier_params(4, 7, seed=0))
 
 
-def gbm_training_rows(n_rows: int, seed: int = 2, dt: float = 0.125):
+def gbm_training_rows(n_rows: int, seed: int = 2, dt: float = 0.125, dts=None):
     """Training rows (theta=(mu,sigma), Y_i, dt) for the GBM network of GBM_ONLINE:
-    mu ~ U[0,0.2], sigma ~ U[0.1,0.5], Y_i log-uniform on [0.25, 4], dt fixed."""
+    mu ~ U[0,0.2], sigma ~ U[0.1,0.5], Y_i log-uniform on [0.25, 4]; dt fixed, or
+    drawn uniformly from the values `dts`."""
     rng = np.random.default_rng(seed)
     mu = rng.uniform(0.0, 0.2, n_rows)
     sg = rng.uniform(0.1, 0.5, n_rows)
     yi = np.exp(rng.uniform(np.log(0.25), np.log(4.0), n_rows))
-    return (np.stack([mu, sg], 1).astype(np.float32), yi.astype(np.float32),
-            np.full(n_rows, dt, dtype=np.float32))
+    dtv = np.full(n_rows, dt) if dts is None else rng.choice(np.asarray(dts, np.float64), n_rows)
+    return (np.stack([mu, sg], 1).astype(np.float32), yi.astype(np.float32), dtv.astype(np.float32))
 
 
 def cir_label_rows(n_rows: int = 1024, seed: int = 3):

@@ -80,43 +80,62 @@ def test_adam_steps(sl, orc):
     assert np.abs(dP - dPo).max() <= 2e-3 * nb
 
 
+def _strong_errors(sl, orc, P, n_steps, n=4000, mu=0.1, sg=0.3, T=2.0, m=7, seed=11):
+    """Mean |Y_T - exact| for the trained 7L sampler (FP32 and BF16 forms), the
+    exact-collocation 7L sampler, and Euler-Maruyama with the same coarse step, each
+    against the exact GBM solution driven by that method's own normals; plus the
+    call price E[(Y_T - 1)+] of each method."""
+    dt = T / n_steps
+    off = W.offsets_from_counts([n])
+    th, y0, offd = _dev([[mu, sg]]), _dev([1.0]), _dev(off, torch.int64)
+    sx = np.array([orc.normals(seed, 0, 0, q, 0, n_steps).sum() for q in range(n)])
+    exact7 = np.exp((mu - 0.5 * sg * sg) * T + sg * math.sqrt(dt) * sx)
+    out = {}
+    for name, model, net in (("fp32", 0, sl.make_net(P, 4, m, prec=sl.PREC_FP32)),
+                             ("bf16", 0, sl.make_net(P, 4, m, prec=sl.PREC_BF16)),
+                             ("exact", 1, None)):
+        yt = torch.empty(n, device="cuda")
+        sl.seven_league_simulate_batched(model, net, th, y0, offd, T, n_steps, m, seed, out_YT=yt)
+        y = yt.cpu().numpy().astype(np.float64)
+        out[name] = (np.abs(y - exact7).mean(), np.maximum(y - 1, 0).mean())
+    em = sl.em_terminal(0, th, y0, _dev([T]), n, n_steps, seed).cpu().numpy()[0].astype(np.float64)
+    sxe = np.array([orc.normals(seed, 1, 0, q, 0, n_steps).sum() for q in range(n)])
+    exact_em = np.exp((mu - 0.5 * sg * sg) * T + sg * math.sqrt(dt) * sxe)
+    out["em"] = (np.abs(em - exact_em).mean(), np.maximum(em - 1, 0).mean())
+    return out
+
+
 def test_train_gbm_and_gain(sl, orc):
-    """Labels -> training -> 7L sampling, all on the GPU (GBM, m = 7, dt = 0.125)."""
-    d_in, m, dt = 4, 7, 0.125
-    n_rows, n_paths = 1 << 14, 100_000
-    th, yi, dts = W.gbm_training_rows(n_rows, seed=2, dt=dt)
-    lab = sl.em_collocation_labels(0, _dev(th), _dev(yi), _dev(dts), n_paths, 100, m, 7)
-    feats = _dev(np.concatenate([yi[:, None], dts[:, None], th], 1).astype(np.float32))
-    P = _dev(W.xavier_params(d_in, m, seed=0))
-    am, av = torch.zeros_like(P), torch.zeros_like(P)
-    batch, nb = 1024, 20000
-    rows = _dev(W.minibatch_rows(n_rows, batch, nb, seed=3), torch.int32)
-    losses = sl.train(P, d_in, m, am, av, 0, feats, lab, rows, batch).cpu().numpy()
-    assert losses[-200:].mean() < 0.05 * losses[:20].mean()
-    # trained map vs the exact lognormal collocation map on a grid
+    """Labels -> training -> 7L sampling, all on the GPU (GBM, m = 7), and the gain
+    over plain Euler-Maruyama: the 7L error does not grow with the step size (the
+    paper's claim) while Euler-Maruyama's does."""
+    from paper_2302_05170_b300 import pipeline
+    P, losses, lab = pipeline.train_gbm_online_network(n_rows=1 << 14, n_steps=40000)
+    assert losses[-500:].mean() < 0.02 * losses[:20].mean()
+    d_in, m = 4, 7
+    # trained map vs the exact lognormal collocation map on a grid (dt = 0.5)
     x, _, _ = sl.gauss_hermite(m)
     net = sl.make_net(P, d_in, m)
     gy, gmu, gsg = np.meshgrid(np.linspace(0.5, 2.0, 7), np.linspace(0.02, 0.18, 5), np.linspace(0.15, 0.45, 5))
-    G = np.stack([gy.ravel(), np.full(gy.size, dt), gmu.ravel(), gsg.ravel()], 1).astype(np.float32)
+    G = np.stack([gy.ravel(), np.full(gy.size, 0.5), gmu.ravel(), gsg.ravel()], 1).astype(np.float32)
     yh = sl.mlp_forward(net, _dev(G)).cpu().numpy()
-    ex = G[:, :1] * np.exp((G[:, 2:3] - 0.5 * G[:, 3:4] ** 2) * dt + G[:, 3:4] * math.sqrt(dt) * x[None, :])
-    assert np.abs(yh - ex).max() / G[:, 0].max() < 0.05
-    # gain test on one theta of the online workload: strong error vs the exact solution
-    mu, sg, T, n_steps, n = 0.1, 0.3, 2.0, 16, 4000
-    off = W.offsets_from_counts([n])
-    for prec in (sl.PREC_FP32, sl.PREC_BF16):
-        netp = sl.make_net(P, d_in, m, prec=prec)
-        yt = torch.empty(n, device="cuda")
-        sl.seven_league_simulate_batched(0, netp, _dev([[mu, sg]]), _dev([1.0]), _dev(off, torch.int64), T,
-                                         n_steps, m, 11, out_YT=yt)
-        y7 = yt.cpu().numpy().astype(np.float64)
-        sx = np.array([orc.normals(11, 0, 0, q, 0, n_steps).sum() for q in range(n)])
-        exact7 = np.exp((mu - 0.5 * sg * sg) * T + sg * math.sqrt(dt) * sx)
-        err7 = np.abs(y7 - exact7).mean()
-        # coarse Euler-Maruyama, same step, its own normals (tag 1 stream of row 0)
-        em = sl.em_terminal(0, _dev([[mu, sg]]), _dev([1.0]), _dev([T]), n, n_steps, 11).cpu().numpy()[0]
-        sxe = np.array([orc.normals(11, 1, 0, q, 0, n_steps).sum() for q in range(n)])
-        exact_em = np.exp((mu - 0.5 * sg * sg) * T + sg * math.sqrt(dt) * sxe)
-        err_em = np.abs(em - exact_em).mean()
-        print('gain', prec, err7, err_em)
-        assert err7 < 0.25 * err_em, (prec, err7, err_em)
+    ex = G[:, :1] * np.exp((G[:, 2:3] - 0.5 * G[:, 3:4] ** 2) * 0.5 + G[:, 3:4] * math.sqrt(0.5) * x[None, :])
+    print("max |H - exact map| / max Y on the grid:", np.abs(yh - ex).max() / G[:, 0].max())
+    assert np.abs(yh - ex).max() / G[:, 0].max() < 0.1
+    errs = {k: _strong_errors(sl, orc, P, k) for k in (16, 4, 2)}
+    print("strong / call-price errors by number of steps:", errs)
+    bs = math.exp(0.2) * stats_norm_cdf((0.2 + 0.045 * 2) / (0.3 * math.sqrt(2))) - \
+        stats_norm_cdf((0.2 - 0.045 * 2) / (0.3 * math.sqrt(2)))
+    # Euler-Maruyama degrades with the step; the trained 7L scheme does not
+    assert errs[2]["em"][0] > 2.0 * errs[16]["em"][0]
+    assert errs[2]["fp32"][0] <= errs[16]["fp32"][0]
+    # gain at the largest step (dt = 1): strong and call-price (weak) error
+    assert errs[2]["fp32"][0] < 0.4 * errs[2]["em"][0]
+    assert abs(errs[2]["fp32"][1] - bs) < abs(errs[2]["em"][1] - bs)
+    for k in (16, 4, 2):   # BF16 tensor-core form tracks the FP32 form; the exact map is far better
+        assert abs(errs[k]["bf16"][0] - errs[k]["fp32"][0]) < 0.2 * errs[k]["fp32"][0]
+        assert errs[k]["exact"][0] < 0.2 * errs[k]["fp32"][0]
+
+
+def stats_norm_cdf(x):
+    return 0.5 * math.erfc(-x / math.sqrt(2.0))
