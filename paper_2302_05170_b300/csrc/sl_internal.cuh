@@ -112,6 +112,23 @@ __device__ __forceinline__ float lagrange_eval_m(const float (&y)[SL_MAX_M], flo
     return acc;
 }
 
+// The Lagrange basis ell_j(X) for a runtime m <= SL_MAX_M (ell_j = 0 for j >= m),
+// so that g_m(X) = sum_j y_j ell_j can be finished with m FMAs once y is known.
+__device__ __forceinline__ void lagrange_basis_m(float X, const GHConst& gh, int m, float (&l)[SL_MAX_M]) {
+    float d[SL_MAX_M], pre[SL_MAX_M];
+#pragma unroll
+    for (int j = 0; j < SL_MAX_M; ++j) d[j] = (j < m) ? X - gh.x[j] : 1.0f;
+    pre[0] = 1.0f;
+#pragma unroll
+    for (int j = 1; j < SL_MAX_M; ++j) pre[j] = pre[j - 1] * d[j - 1];
+    float suf = 1.0f;
+#pragma unroll
+    for (int j = SL_MAX_M - 1; j >= 0; --j) {
+        l[j] = gh.bary[j] * (pre[j] * suf);
+        suf *= d[j];
+    }
+}
+
 // The Lagrange basis values ell_j(X) (for the adjoint: d g_m / d y_j).
 template <int M>
 __device__ __forceinline__ void lagrange_basis(float X, const GHConst& gh, float (&l)[M]) {

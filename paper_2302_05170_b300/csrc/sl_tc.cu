@@ -484,6 +484,12 @@ __global__ void __launch_bounds__(128 * S, 1) tc_7l_kernel(const SimArgs a) {
             ok = bar_and(bar_id, ok);          // slot-uniform from here
             if (!ok) break;
             if (issuer) issue(0);
+            // While layer 1 runs: this step's normal and the Lagrange basis at it
+            // (independent of the network's output).
+            if ((i & 3) == 0)
+                z4 = normal4(a.seed, 0u, static_cast<uint32_t>(ts.s), ts.q, static_cast<uint32_t>(i >> 2));
+            float lb[SL_MAX_M];
+            lagrange_basis_m(pick4(z4, i & 3), a.gh, a.m, lb);
 
             // ---- hidden layers: accumulator -> ReLU -> hi/lo BF16 -> next A
             // (unrolled: each layer's MMA issue is specialised at compile time)
@@ -497,11 +503,14 @@ __global__ void __launch_bounds__(128 * S, 1) tc_7l_kernel(const SimArgs a) {
                     // Row layout of the next A (BF16 words): hi 0..24 (columns 0..49),
                     // word 25 = {1.0, 0} (bias unit), 26..27 = 0, lo 28..52, 53..55 = 0.
                     // columns 0..31 of the accumulator -> hi words 0..15, lo words 28..43
+                    // all three loads in flight before one wait
+                    uint32_t v[32], v2[16], u[8];
+                    tmem_ld32(taddr, v);
+                    tmem_ld16(taddr + 32, v2);
+                    tmem_ld8(taddr + 48, u);
+                    tmem_wait_ld();
                     uint32_t hw[16], lw[16];
                     {
-                        uint32_t v[32];
-                        tmem_ld32(taddr, v);
-                        tmem_wait_ld();
 #pragma unroll
                         for (int i2 = 0; i2 < 16; ++i2) {
                             const float ha = __uint_as_float(v[2 * i2] & 0xFFFF0000u);
@@ -524,15 +533,11 @@ __global__ void __launch_bounds__(128 * S, 1) tc_7l_kernel(const SimArgs a) {
                     }
                     // columns 32..49 -> hi words 16..24, lo words 44..52
                     {
-                        uint32_t v[16], u[8];
-                        tmem_ld16(taddr + 32, v);
-                        tmem_ld8(taddr + 48, u);
-                        tmem_wait_ld();
                         uint32_t h9[9], l9[9];
 #pragma unroll
                         for (int i2 = 0; i2 < 9; ++i2) {
-                            const uint32_t ua = (i2 < 8) ? v[2 * i2] : u[0];
-                            const uint32_t ub = (i2 < 8) ? v[2 * i2 + 1] : u[1];
+                            const uint32_t ua = (i2 < 8) ? v2[2 * i2] : u[0];
+                            const uint32_t ub = (i2 < 8) ? v2[2 * i2 + 1] : u[1];
                             const float ha = __uint_as_float(ua & 0xFFFF0000u);
                             const float hb = __uint_as_float(ub & 0xFFFF0000u);
                             h9[i2] = pack_relu(ha, hb);
@@ -576,13 +581,11 @@ __global__ void __launch_bounds__(128 * S, 1) tc_7l_kernel(const SimArgs a) {
                 tmem_ld8(taddr, yv);
                 tmem_wait_ld();
                 tc_fence_before();
-                float y[SL_MAX_M];
+                // ---- the 7L map g_m (Algorithm I steps 5-6): Y = sum_j y_j ell_j(X)
+                float acc = 0.0f;
 #pragma unroll
-                for (int j = 0; j < SL_MAX_M; ++j) y[j] = __uint_as_float(yv[j]);
-                // ---- Philox normal and the 7L map g_m (Algorithm I steps 5-6)
-                if ((i & 3) == 0)
-                    z4 = normal4(a.seed, 0u, static_cast<uint32_t>(ts.s), ts.q, static_cast<uint32_t>(i >> 2));
-                Y = lagrange_eval_m(y, pick4(z4, i & 3), a.gh, a.m);
+                for (int j = SL_MAX_M - 1; j >= 0; --j) acc = fmaf(__uint_as_float(yv[j]), lb[j], acc);
+                Y = acc;
                 if (a.out_grid && ts.valid) a.out_grid[static_cast<int64_t>(i + 1) * a.total + ts.g] = Y;
             }
         }
