@@ -218,6 +218,33 @@ int em_collocation_labels(int sde, const float* theta, const float* Yi, const fl
                           int n_rows, int64_t n_paths, int n_fine, int m, uint64_t seed,
                           float* labels, void* ws, size_t ws_bytes, void* stream);
 
+/*
+ * em_collocation_labels for callers that cannot allocate device memory (the
+ * paper has no counterpart: this is a deployment convenience).  A plugin
+ * inside a host application that owns all device allocations, a service with
+ * a memory budget fixed at start-up, or code that must not enter the CUDA
+ * allocator at a given point can pass its inputs and the label output but not
+ * a scratch buffer.  This entry point uses instead a fixed 16 MiB array that
+ * the library keeps in device memory (a file-scope __device__ variable, held
+ * on every GPU that loads the library until the process exits) and calls no
+ * allocation routine.  Limits and behaviour:
+ *  - n_rows * n_paths must not exceed sl_em_labels_noalloc_max_samples()
+ *    (4,194,240 samples); larger calls return SL_ERR_WORKSPACE;
+ *  - the first call on a device looks the array's address up
+ *    (cudaGetSymbolAddress, with that device current) and caches it: make that
+ *    first call before any stream capture on that device;
+ *  - every call uses the same array, so calls whose work overlaps on the GPU
+ *    (different streams, or different host threads) race; order them on one
+ *    stream.  The array keeps the previous call's contents; the call clears
+ *    its status word and overwrites every sample it reads.
+ * Arguments, results and errors are otherwise those of em_collocation_labels.
+ */
+int em_collocation_labels_noalloc(int sde, const float* theta, const float* Yi, const float* dt,
+                                  int n_rows, int64_t n_paths, int n_fine, int m, uint64_t seed,
+                                  float* labels, void* stream);
+/* Largest n_rows * n_paths em_collocation_labels_noalloc accepts. */
+size_t sl_em_labels_noalloc_max_samples(void);
+
 /* ------------------------------------------------------------------------
  * Pathwise sensitivities (adjoint) of E[f(Y_T)], f(Y) = max(Y - K, 0).
  * ---------------------------------------------------------------------- */

@@ -39,7 +39,7 @@ EXPORTED = [
     "sl_select_workspace_size", "sl_segmented_select", "sl_em_labels_workspace_size",
     "em_collocation_labels", "sl_tc_set_slots", "sl_tc_get_slots", "sl_tc_set_a_operand", "sl_train_workspace_size",
     "sl_mlp_forward", "sl_mse_grad", "sl_adam_step", "sl_train", "sl_adjoint_workspace_size",
-    "seven_league_adjoint",
+    "seven_league_adjoint", "em_collocation_labels_noalloc", "sl_em_labels_noalloc_max_samples",
 ]
 
 
@@ -105,6 +105,8 @@ def load(path: str = LIB_PATH):
     L.sl_adjoint_workspace_size.restype = _sz
     L.seven_league_adjoint.argtypes = [_i, ctypes.POINTER(sl_net), _vp, _i, _vp, _vp, _i, _i64, _f, _i, _i,
                                        _u64, _i, _f, _i, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
+    L.em_collocation_labels_noalloc.argtypes = [_i, _vp, _vp, _vp, _i, _i64, _i, _i, _u64, _vp, _vp]
+    L.sl_em_labels_noalloc_max_samples.restype = _sz
     L.sl_tc_set_a_operand.argtypes = [_i]
     L.sl_tc_set_slots.argtypes = [_i]
     L.sl_tc_get_slots.restype = _i
@@ -371,6 +373,24 @@ def em_collocation_labels(sde, theta, Yi, dt, n_paths, n_fine, m, seed, labels=N
                                    _ptr(labels, torch.float32, "labels"), _ptr(ws), ws.numel(),
                                    _stream(stream)))
     return labels
+
+
+def em_collocation_labels_noalloc(sde, theta, Yi, dt, n_paths, n_fine, m, seed, labels=None, stream=None):
+    """em_collocation_labels without a caller workspace (the library's fixed
+    device buffer; see include/sevenleague.h for its limit and its rules)."""
+    torch = _torch()
+    L = load()
+    n_rows = Yi.numel()
+    if labels is None:
+        labels = torch.empty((n_rows, m), dtype=torch.float32, device=Yi.device)
+    _check(L.em_collocation_labels_noalloc(sde, _ptr(theta, torch.float32, "theta"), _ptr(Yi, torch.float32, "Yi"),
+                                           _ptr(dt, torch.float32, "dt"), n_rows, int(n_paths), n_fine, m, seed,
+                                           _ptr(labels, torch.float32, "labels"), _stream(stream)))
+    return labels
+
+
+def em_labels_noalloc_max_samples():
+    return int(load().sl_em_labels_noalloc_max_samples())
 
 
 # ---------------------------------------------------------------------------
