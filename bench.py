@@ -216,7 +216,7 @@ def main():
         from paper_2302_05170_b300 import autotune
         best, tms = autotune.tune_slots(lambda: step(out_mean=None, out_var=None),
                                         "gbm-online d4 m7 s16 n%d" % total, use_cache=False)
-        tuning = {"tc_slots": best, "ms_by_slots": tms}
+        tuning = {"tc_slots": best[0], "tc_tiles_per_warpgroup": best[1], "ms_by_config": tms}
     for _ in range(max(args.warmup, 3)):
         step()
     assert sl.workspace_status(ws) == 0, "device status set during warm-up"

@@ -167,16 +167,18 @@ int seven_league_simulate(int model, const float* theta, int p, float Y0, float 
                           float* out, void* stream);
 
 /*
- * Tuning of the BF16 tensor-core form: number of 128-path tiles each
- * persistent CTA keeps in flight (2..5, default 4).  Process-wide setting,
- * read at launch time.  Returns SL_ERR_ARG outside [2,5].
+ * Tuning of the BF16 tensor-core form (process-wide, read at launch time):
+ *  - slots: 128-path tiles each persistent CTA keeps in flight (2..4, default 4);
+ *  - pipeline: tiles per warpgroup (1 or 2, default 1).  With 2, a warpgroup
+ *    alternates between two tiles layer by layer (one tile's epilogue beside
+ *    the other's tensor-core work); slots must then be 2 or 4.  On the GBM
+ *    workload 4 slots x 1 tile per warpgroup is fastest.
+ * Both return SL_ERR_ARG for an unsupported value or combination.
  */
 int sl_tc_set_slots(int slots);
 int sl_tc_get_slots(void);
-/* 1 (default): the BF16 form keeps the network's activations (the MMA A
- * operand) in tensor memory beside the accumulator (used when slots <= 4);
- * 0: in shared memory.  Process-wide, read at launch time. */
-int sl_tc_set_a_operand(int in_tensor_memory);
+int sl_tc_set_pipeline(int tiles_per_warpgroup);
+int sl_tc_get_pipeline(void);
 
 /* ------------------------------------------------------------------------
  * Offline stage (Algorithm I, step 1).

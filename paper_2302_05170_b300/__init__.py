@@ -37,7 +37,8 @@ EXPORTED = [
     "sl_quantile_ranks", "sl_workspace_status", "sl_simulate_workspace_size",
     "seven_league_simulate_batched", "seven_league_simulate", "sl_em_terminal",
     "sl_select_workspace_size", "sl_segmented_select", "sl_em_labels_workspace_size",
-    "em_collocation_labels", "sl_tc_set_slots", "sl_tc_get_slots", "sl_tc_set_a_operand", "sl_train_workspace_size",
+    "em_collocation_labels", "sl_tc_set_slots", "sl_tc_get_slots", "sl_tc_set_pipeline",
+    "sl_tc_get_pipeline", "sl_train_workspace_size",
     "sl_mlp_forward", "sl_mse_grad", "sl_adam_step", "sl_train", "sl_adjoint_workspace_size",
     "seven_league_adjoint", "em_collocation_labels_noalloc", "sl_em_labels_noalloc_max_samples",
 ]
@@ -107,7 +108,8 @@ def load(path: str = LIB_PATH):
                                        _u64, _i, _f, _i, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
     L.em_collocation_labels_noalloc.argtypes = [_i, _vp, _vp, _vp, _i, _i64, _i, _i, _u64, _vp, _vp]
     L.sl_em_labels_noalloc_max_samples.restype = _sz
-    L.sl_tc_set_a_operand.argtypes = [_i]
+    L.sl_tc_set_pipeline.argtypes = [_i]
+    L.sl_tc_get_pipeline.restype = _i
     L.sl_tc_set_slots.argtypes = [_i]
     L.sl_tc_get_slots.restype = _i
     _lib = L
@@ -197,7 +199,7 @@ def workspace_status(ws, stream=None):
 
 
 def tc_set_slots(slots):
-    """Path tiles in flight per CTA of the BF16 tensor-core form (2..5)."""
+    """Path tiles in flight per CTA of the BF16 tensor-core form (2..4)."""
     _check(load().sl_tc_set_slots(int(slots)))
 
 
@@ -205,9 +207,13 @@ def tc_get_slots():
     return int(load().sl_tc_get_slots())
 
 
-def tc_set_a_operand(in_tensor_memory):
-    """Where the BF16 form keeps the MMA A operand: tensor memory (True) or shared memory."""
-    _check(load().sl_tc_set_a_operand(1 if in_tensor_memory else 0))
+def tc_set_pipeline(tiles_per_warpgroup):
+    """Tiles per warpgroup of the BF16 form: 1 (default) or 2 (ping-pong)."""
+    _check(load().sl_tc_set_pipeline(int(tiles_per_warpgroup)))
+
+
+def tc_get_pipeline():
+    return int(load().sl_tc_get_pipeline())
 
 
 # ---------------------------------------------------------------------------

@@ -20,19 +20,27 @@ def _load():
         return {}
 
 
-def tune_slots(run, key, candidates=(2, 3, 4, 5), reps=3, use_cache=True):
-    """run(): one call of the workload on the current stream.  Returns (best_slots, timings_ms)."""
+CANDIDATES = ((4, 1), (3, 1), (2, 1), (4, 2), (2, 2))   # (slots, tiles per warpgroup)
+
+
+def tune_slots(run, key, candidates=CANDIDATES, reps=3, use_cache=True):
+    """run(): one call of the workload on the current stream.  Tries each
+    (slots, tiles per warpgroup); returns (best, timings_ms)."""
     import torch
     import paper_2302_05170_b300 as sl
 
     full_key = "%s|%s" % (torch.cuda.get_device_name(), key)
     cache = _load()
+    def apply(c):
+        sl.tc_set_pipeline(1)          # every slot count is valid with one tile per warpgroup
+        sl.tc_set_slots(c[0])
+        sl.tc_set_pipeline(c[1])
     if use_cache and full_key in cache:
-        sl.tc_set_slots(cache[full_key]["slots"])
-        return cache[full_key]["slots"], cache[full_key]["ms"]
+        apply(tuple(cache[full_key]["best"]))
+        return tuple(cache[full_key]["best"]), cache[full_key]["ms"]
     times = {}
-    for s in candidates:
-        sl.tc_set_slots(s)
+    for c in candidates:
+        apply(c)
         run()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -41,10 +49,10 @@ def tune_slots(run, key, candidates=(2, 3, 4, 5), reps=3, use_cache=True):
             run()
         b.record()
         b.synchronize()
-        times[str(s)] = a.elapsed_time(b) / reps
-    best = int(min(times, key=times.get))
-    sl.tc_set_slots(best)
-    cache[full_key] = {"slots": best, "ms": times}
+        times["%d/%d" % c] = a.elapsed_time(b) / reps
+    best = min(candidates, key=lambda c: times["%d/%d" % c])
+    apply(best)
+    cache[full_key] = {"best": list(best), "ms": times}
     try:
         with open(CACHE + ".tmp", "w") as f:
             json.dump(cache, f, indent=1)

@@ -42,8 +42,6 @@ namespace {
 
 constexpr int kTile = 128;                    // paths per slot (MMA M, TMEM lanes)
 constexpr int kRowBytes = 128;                // one 128B-swizzle row = 64 BF16
-constexpr int kAAtomBytes = kTile * kRowBytes;           // 16 KB: 128 rows x 64 cols
-constexpr int kASlotBytes = 2 * kAAtomBytes;             // K = 112 -> two 64-col atoms
 constexpr int kB1Bytes = 64 * kRowBytes;                 // layer 1: 64 rows x (16 of 64) cols
 constexpr int kBHBytes = 2 * 64 * kRowBytes;             // hidden: 64 rows x 112 cols
 constexpr int kB5Bytes = 2 * 16 * kRowBytes;             // output: 16 rows x 112 cols
@@ -134,22 +132,6 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 // the same (warp-uniform) operands and one lane, chosen by elect.sync, issues.
 // Keeping the control flow converged lets the descriptors stay in uniform
 // registers; issuing from a divergent single-lane branch costs ~2.5x per MMA.
-__device__ __forceinline__ void mma_bf16_w(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
-                                           uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n.reg .pred p, e;\nelect.sync _|e, 0xffffffff;\nsetp.ne.b32 p, %4, 0;\n"
-        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-__device__ __forceinline__ void mma_bf16_ta_w(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
-                                              uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n.reg .pred p, e;\nelect.sync _|e, 0xffffffff;\nsetp.ne.b32 p, %4, 0;\n"
-        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(d_tmem),
-        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
 __device__ __forceinline__ void mma_commit_w(uint32_t mbar) {
     asm volatile(
         "{\n.reg .pred e;\nelect.sync _|e, 0xffffffff;\n"
@@ -256,12 +238,6 @@ __device__ __forceinline__ uint32_t pack_rn(float lo_elem, float hi_elem) {
     return d;
 }
 
-__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
-                                             uint32_t d) {
-    asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
-                 : "memory");
-}
-
 // Byte offset of 16-byte chunk `c` (0..7) of row `r` inside a 128B-swizzled atom.
 __device__ __forceinline__ uint32_t sw128_chunk(int r, int c) {
     return static_cast<uint32_t>((r >> 3) * 1024 + (r & 7) * kRowBytes + ((c ^ (r & 7)) << 4));
@@ -314,13 +290,6 @@ __device__ void stage_weights(unsigned char* sB, const float* __restrict__ P, in
     }
 }
 
-struct TileState {
-    int64_t g;      // flat path index
-    int s;          // owning set
-    uint32_t q;     // path index within the set
-    bool valid;
-};
-
 // AND of `v` over the 128 threads of named barrier `id` (also a barrier).
 __device__ __forceinline__ bool bar_and(int id, bool v) {
     uint32_t r;
@@ -332,37 +301,185 @@ __device__ __forceinline__ bool bar_and(int id, bool v) {
     return r != 0;
 }
 
-// One path tile ("slot") is owned by one warpgroup: warp w (w = 0..3) reads and
-// writes TMEM lanes 32w..32w+31, i.e. paths 32w..32w+31 of the tile, and warp 0
-// also issues the tile's MMAs (one elected lane) once all four warps have
-// written the next A operand (named barrier 1 + slot).  There is no separate
-// MMA warp: a hand-off to a shared issuer costs a round trip per layer.
-//
-// AT = false: the A operand (features / activations) is staged in shared
-// memory (128B-swizzled); AT = true: it lives in tensor memory next to the
-// slot's accumulator (columns 64..119 of a 128-column slot).
-template <int S, bool AT>
-__global__ void __launch_bounds__(128 * S, 1) tc_7l_kernel(const SimArgs a) {
+// Per-thread state of one path tile (128 paths; this thread owns row `r`).
+struct Tile {
+    int64_t g;        // flat path index of this thread's row
+    int s;            // owning parameter set
+    uint32_t q;       // path index within the set (Philox counter)
+    bool valid;       // row holds a real path
+    float Y;          // state
+    float feat[SL_MAX_DIN_TC];
+    float4 z4;        // normals of the current block of 4 steps
+    float lb[SL_MAX_M];   // Lagrange basis at this step's normal
+    uint32_t dph;     // phase of the tile's d_ready barrier
+    uint32_t d_tmem;  // accumulator (lane 0 of the tile; A at +64)
+    uint32_t taddr;   // accumulator, this warp's lanes
+    uint32_t d_bar;   // mbarrier: the tile's MMAs completed
+    int bar_id;       // named barrier of the tile's warpgroup
+};
+
+// Kernel-wide constants of the issue path.
+struct IssueConst {
+    uint64_t db0, db1, db2, db3, db4;   // B descriptors of layers 1..5
+};
+
+__device__ __forceinline__ void tile_begin(Tile& T, const SimArgs& a, int64_t tile, int r) {
+    T.g = tile * kTile + r;
+    T.valid = T.g < a.total;
+    T.s = 0;
+    int64_t qq = T.g;
+    if (a.offsets) {
+        T.s = owning_set(a.offsets, a.n_sets, T.valid ? T.g : a.total - 1);
+        qq = T.g - __ldg(a.offsets + T.s);
+    }
+    T.q = static_cast<uint32_t>(qq);
+    const float* th = a.theta + static_cast<int64_t>(T.s) * a.p;
+    T.feat[0] = 0.0f;
+    T.feat[1] = a.dt;
+#pragma unroll
+    for (int k = 0; k < SL_MAX_DIN_TC - 2; ++k) T.feat[2 + k] = (k < a.p) ? __ldg(th + k) : 0.0f;
+    T.Y = a.Y0 ? __ldg(a.Y0 + T.s) : a.y0_scalar;
+    if (a.out_grid && T.valid) a.out_grid[T.g] = T.Y;
+    T.z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Layer-1 A row: features [Y, dt, theta] as (hi, lo) BF16 pairs, then the constant 1.
+__device__ __forceinline__ void tile_features(Tile& T, const SimArgs& a) {
+    T.feat[0] = T.Y;
+    uint32_t fw[8];
+#pragma unroll
+    for (int k = 0; k < SL_MAX_DIN_TC; ++k) {
+        const float hi = __uint_as_float(__float_as_uint(T.feat[k]) & 0xFFFF0000u);
+        const uint32_t wv = pack_rn(hi, T.feat[k] - hi);
+        fw[k] = (k < a.d_in) ? wv : ((k == a.d_in) ? 0x00003F80u : 0u);   // 1.0 after the features
+    }
+    fw[7] = (a.d_in == SL_MAX_DIN_TC) ? 0x00003F80u : 0u;
+    tmem_st8(T.taddr + 64, fw);
+    tmem_wait_st();
+    tc_fence_before();
+}
+
+// All four warps agree (named-barrier AND) that the next A is written; warp 0
+// then issues layer l's MMAs and commits them to the tile's d_ready.
+__device__ __forceinline__ bool tile_sync_issue(const Tile& T, const IssueConst& C, int l, bool ok, bool issuer) {
+    ok = bar_and(T.bar_id, ok);
+    if (ok && issuer) {
+        constexpr uint32_t kIdesc64 = idesc_bf16(128, 64), kIdesc16 = idesc_bf16(128, 16);
+        tc_fence_after();
+        if (l == 0) {
+            mma1_ta_commit(T.d_tmem, T.d_tmem + 64, C.db0, kIdesc64, T.d_bar);
+        } else {
+            const uint64_t db = (l == 1) ? C.db1 : (l == 2) ? C.db2 : (l == 3) ? C.db3 : C.db4;
+            mma7_ta_commit(T.d_tmem, T.d_tmem + 64, db, (l < 4) ? (64 * kRowBytes) >> 4 : (16 * kRowBytes) >> 4,
+                           (l < 4) ? kIdesc64 : kIdesc16, T.d_bar);
+        }
+    }
+    return ok;
+}
+
+// Normal of step i and the Lagrange basis at it (independent of the network).
+__device__ __forceinline__ void tile_rng(Tile& T, const SimArgs& a, int i) {
+    if ((i & 3) == 0)
+        T.z4 = normal4(a.seed, 0u, static_cast<uint32_t>(T.s), T.q, static_cast<uint32_t>(i >> 2));
+    lagrange_basis_m(pick4(T.z4, i & 3), a.gh, a.m, T.lb);
+}
+
+__device__ __forceinline__ bool tile_wait(Tile& T, volatile int* abort_flag, unsigned* status) {
+    bool w = mbar_wait(T.d_bar, T.dph, abort_flag, status);
+    T.dph ^= 1u;
+    return __all_sync(0xffffffffu, w);
+}
+
+// Hidden-layer epilogue: accumulator row -> ReLU -> BF16 hi + lo -> next A row.
+// A row (BF16 words): hi 0..24 (columns 0..49), word 25 = {1.0, 0} (bias unit),
+// 26..27 = 0, lo 28..52, 53..55 = 0.
+__device__ __forceinline__ void tile_hidden(const Tile& T) {
+    tc_fence_after();
+    uint32_t v[32], v2[16], u[8];
+    tmem_ld32(T.taddr, v);
+    tmem_ld16(T.taddr + 32, v2);
+    tmem_ld8(T.taddr + 48, u);
+    tmem_wait_ld();
+    const uint32_t at = T.taddr + 64;
+    uint32_t hw[16], lw[16];
+#pragma unroll
+    for (int i2 = 0; i2 < 16; ++i2) {   // columns 0..31 -> hi words 0..15, lo words 28..43
+        const float ha = __uint_as_float(v[2 * i2] & 0xFFFF0000u);
+        const float hb = __uint_as_float(v[2 * i2 + 1] & 0xFFFF0000u);
+        hw[i2] = pack_relu(ha, hb);
+        lw[i2] = pack_relu(__uint_as_float(v[2 * i2]) - ha, __uint_as_float(v[2 * i2 + 1]) - hb);
+    }
+    tmem_st16(at, hw);
+    uint32_t h9[9], l9[9];
+#pragma unroll
+    for (int i2 = 0; i2 < 9; ++i2) {    // columns 32..49 -> hi words 16..24, lo words 44..52
+        const uint32_t ua = (i2 < 8) ? v2[2 * i2] : u[0];
+        const uint32_t ub = (i2 < 8) ? v2[2 * i2 + 1] : u[1];
+        const float ha = __uint_as_float(ua & 0xFFFF0000u);
+        const float hb = __uint_as_float(ub & 0xFFFF0000u);
+        h9[i2] = pack_relu(ha, hb);
+        l9[i2] = pack_relu(__uint_as_float(ua) - ha, __uint_as_float(ub) - hb);
+    }
+    const uint32_t gb[16] = {h9[0], h9[1], h9[2], h9[3], h9[4], h9[5], h9[6], h9[7],
+                             h9[8], 0x00003F80u, 0u, 0u, lw[0], lw[1], lw[2], lw[3]};
+    const uint32_t gc[16] = {lw[4], lw[5], lw[6], lw[7], lw[8], lw[9], lw[10], lw[11],
+                             lw[12], lw[13], lw[14], lw[15], l9[0], l9[1], l9[2], l9[3]};
+    const uint32_t gd[8] = {l9[4], l9[5], l9[6], l9[7], l9[8], 0u, 0u, 0u};
+    tmem_st16(at + 16, gb);
+    tmem_st16(at + 32, gc);
+    tmem_st8(at + 48, gd);
+    tmem_wait_st();
+    tc_fence_before();
+}
+
+// Output layer: collocation points y_j, then Y_{i+1} = g_m(X) = sum_j y_j ell_j(X)
+// (Algorithm I steps 5-6).
+__device__ __forceinline__ void tile_out(Tile& T, const SimArgs& a, int i) {
+    tc_fence_after();
+    uint32_t yv[8];
+    tmem_ld8(T.taddr, yv);
+    tmem_wait_ld();
+    tc_fence_before();
+    float acc = 0.0f;
+#pragma unroll
+    for (int j = SL_MAX_M - 1; j >= 0; --j) acc = fmaf(__uint_as_float(yv[j]), T.lb[j], acc);
+    T.Y = acc;
+    if (a.out_grid && T.valid) a.out_grid[static_cast<int64_t>(i + 1) * a.total + T.g] = T.Y;
+}
+
+__device__ __forceinline__ void tile_end(const Tile& T, const SimArgs& a) {
+    if (!T.valid) return;
+    if (a.out_YT) a.out_YT[T.g] = T.Y;
+    if (!isfinite(T.Y)) raise_status(a.status, SL_DEV_NONFINITE);
+}
+
+// WG warpgroups per CTA, TPW path tiles per warpgroup (S = WG * TPW tiles in
+// flight).  Warp w of a warpgroup reads and writes TMEM lanes 32(w%4).., i.e.
+// paths 32(w%4).. of each of its tiles; warp 0 of the warpgroup also issues the
+// tiles' MMAs.  With TPW = 2 the warpgroup alternates between its two tiles
+// layer by layer, so one tile's epilogue runs while the other tile's MMAs run
+// ("ping-pong"); with TPW = 1 the overlap comes only from other warpgroups.
+template <int WG, int TPW>
+__global__ void __launch_bounds__(128 * WG, 1) tc_7l_kernel(const SimArgs a) {
+    constexpr int S = WG * TPW;
+    constexpr uint32_t kCols = (S * 128 <= 128) ? 128 : (S * 128 <= 256) ? 256 : 512;
+    static_assert(S * 128 <= 512, "tensor memory holds 512 columns");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-    unsigned char* sB = smem;                                  // weights (1024-aligned)
-    unsigned char* sA = smem + kBBytes;                        // S slots x 32 KB (AT = false)
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sA + (AT ? 0 : S * kASlotBytes));   // d_ready[S], drain
+    unsigned char* sB = smem;                                              // weights (1024-aligned)
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kBBytes);            // d_ready[S], drain
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + S + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int t = warp >> 2, wq = warp & 3;
-    const int r = wq * 32 + lane;                              // row = TMEM lane = path in tile
-    constexpr int kSlotCols = AT ? 128 : 64;                   // TMEM columns per slot (D, then A)
-    constexpr uint32_t kCols = (S * kSlotCols <= 64) ? 64 : (S * kSlotCols <= 128) ? 128
-                               : (S * kSlotCols <= 256) ? 256 : 512;
-    static_assert(S * kSlotCols <= 512, "tensor memory holds 512 columns");
+    const int wg = warp >> 2, wq = warp & 3;
+    const int r = wq * 32 + lane;                                          // row = TMEM lane = path in tile
+    const bool issuer = (wq == 0);
 
     if (threadIdx.x == 0) {
         for (int k = 0; k < S; ++k) mbar_init(smem_u32(&bars[k]), 1);   // d_ready: tcgen05.commit
-        mbar_init(smem_u32(&bars[S]), S);                               // drain: one commit per slot
+        mbar_init(smem_u32(&bars[S]), WG);                              // drain: one commit per issuer
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -380,222 +497,74 @@ __global__ void __launch_bounds__(128 * S, 1) tc_7l_kernel(const SimArgs a) {
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
+    IssueConst C;
+    const uint32_t sB_u = smem_u32(sB);
+    C.db0 = sw128_desc(sB_u);
+    C.db1 = sw128_desc(sB_u + kB1Bytes);
+    C.db2 = sw128_desc(sB_u + kB1Bytes + kBHBytes);
+    C.db3 = sw128_desc(sB_u + kB1Bytes + 2 * kBHBytes);
+    C.db4 = sw128_desc(sB_u + kB1Bytes + 3 * kBHBytes);
+
+    Tile T[TPW];
+#pragma unroll
+    for (int j = 0; j < TPW; ++j) {
+        const int slot = wg * TPW + j;
+        T[j].d_tmem = tmem_base + static_cast<uint32_t>(slot * 128);
+        T[j].taddr = T[j].d_tmem + (static_cast<uint32_t>(wq * 32) << 16);
+        T[j].d_bar = smem_u32(&bars[slot]);
+        T[j].bar_id = 1 + slot;
+        T[j].dph = 0;
+    }
+
     const int64_t n_tiles = (a.total + kTile - 1) / kTile;
     const int64_t tile_stride = static_cast<int64_t>(gridDim.x) * S;
-    const int bar_id = 1 + t;
-    const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(t * kSlotCols);   // lane 0 of the slot
-    const uint32_t taddr = d_tmem + (static_cast<uint32_t>(wq * 32) << 16);
-    const uint32_t a_taddr = taddr + 64;
-    const uint32_t a_slot = smem_u32(sA) + static_cast<uint32_t>(t * kASlotBytes);
-    const uint32_t d_bar = smem_u32(&bars[t]);
-    const bool issuer = (wq == 0);
-    // descriptors (warp-uniform)
-    const uint32_t sB_u = smem_u32(sB);
-    constexpr uint32_t kIdesc64 = idesc_bf16(128, 64), kIdesc16 = idesc_bf16(128, 16);
-    const uint64_t da = sw128_desc(a_slot);
-    const uint64_t db0 = sw128_desc(sB_u);
-    const uint64_t db1 = sw128_desc(sB_u + kB1Bytes);
-    const uint64_t db2 = sw128_desc(sB_u + kB1Bytes + kBHBytes);
-    const uint64_t db3 = sw128_desc(sB_u + kB1Bytes + 2 * kBHBytes);
-    const uint64_t db4 = sw128_desc(sB_u + kB1Bytes + 3 * kBHBytes);
-
-    // MMAs of layer l of this slot (warp-converged, one elected lane issues).
-    auto issue = [&](int l) {
-        tc_fence_after();
-        if (AT) {
-            if (l == 0) {
-                mma1_ta_commit(d_tmem, d_tmem + 64, db0, kIdesc64, d_bar);
-            } else {
-                const uint64_t db = (l == 1) ? db1 : (l == 2) ? db2 : (l == 3) ? db3 : db4;
-                mma7_ta_commit(d_tmem, d_tmem + 64, db, (l < 4) ? (64 * kRowBytes) >> 4 : (16 * kRowBytes) >> 4,
-                               (l < 4) ? kIdesc64 : kIdesc16, d_bar);
-            }
-            return;
-        }
-        if (l == 0) {
-            if (AT) mma_bf16_ta_w(d_tmem, d_tmem + 64, db0, kIdesc64, 0u);
-            else mma_bf16_w(d_tmem, da, db0, kIdesc64, 0u);
-        } else {
-            const uint64_t db = (l == 1) ? db1 : (l == 2) ? db2 : (l == 3) ? db3 : db4;
-            const uint32_t b_atom1 = (l < 4) ? (64 * kRowBytes) >> 4 : (16 * kRowBytes) >> 4;
-            const uint32_t idesc = (l < 4) ? kIdesc64 : kIdesc16;
-#pragma unroll
-            for (int k = 0; k < 7; ++k) {
-                // K steps 0-3 in the first 64-column atom, 4-6 in the second; descriptor start
-                // addresses are in 16-byte units (bits 0-13)
-                const uint64_t bk = db + ((k < 4) ? 2u * k : b_atom1 + 2u * (k - 4));
-                if (AT) {
-                    mma_bf16_ta_w(d_tmem, d_tmem + 64 + 8 * k, bk, idesc, k > 0 ? 1u : 0u);
-                } else {
-                    const uint64_t ak = da + ((k < 4) ? 2u * k : (kAAtomBytes >> 4) + 2u * (k - 4));
-                    mma_bf16_w(d_tmem, ak, bk, idesc, k > 0 ? 1u : 0u);
-                }
-            }
-        }
-        mma_commit_w(d_bar);
-    };
-
-    uint32_t dph = 0;
     bool ok = true;
-    const float dt = a.dt;
-    for (int64_t tile = static_cast<int64_t>(blockIdx.x) * S + t; tile < n_tiles; tile += tile_stride) {
-        TileState ts;
-        ts.g = tile * kTile + r;
-        ts.valid = ts.g < a.total;
-        ts.s = 0;
-        int64_t qq = ts.g;
-        if (a.offsets) {
-            ts.s = owning_set(a.offsets, a.n_sets, ts.valid ? ts.g : a.total - 1);
-            qq = ts.g - __ldg(a.offsets + ts.s);
-        }
-        ts.q = static_cast<uint32_t>(qq);
-        const float* th = a.theta + static_cast<int64_t>(ts.s) * a.p;
-        float feat[SL_MAX_DIN_TC];
-        feat[0] = 0.0f;
-        feat[1] = dt;
+    // The warpgroup's tiles are consecutive: tile j of round k is base + j.
+    for (int64_t base = static_cast<int64_t>(blockIdx.x) * S + wg * TPW; base < n_tiles; base += tile_stride) {
 #pragma unroll
-        for (int k = 0; k < SL_MAX_DIN_TC - 2; ++k) feat[2 + k] = (k < a.p) ? __ldg(th + k) : 0.0f;
-        float Y = a.Y0 ? __ldg(a.Y0 + ts.s) : a.y0_scalar;
-        if (a.out_grid && ts.valid) a.out_grid[ts.g] = Y;
-        float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-
-        for (int i = 0; i < a.n_steps; ++i) {
-            // ---- features [Y, dt, theta] as (hi, lo) BF16 pairs + constant 1 (layer-1 A)
-            if (ok) {
-                feat[0] = Y;
-                uint32_t fw[8];
-#pragma unroll
-                for (int k = 0; k < SL_MAX_DIN_TC; ++k) {
-                    const float hi = __uint_as_float(__float_as_uint(feat[k]) & 0xFFFF0000u);
-                    const uint32_t wv = pack_rn(hi, feat[k] - hi);
-                    fw[k] = (k < a.d_in) ? wv : ((k == a.d_in) ? 0x00003F80u : 0u);   // 1.0 after the features
-                }
-                fw[7] = (a.d_in == SL_MAX_DIN_TC) ? 0x00003F80u : 0u;
-                if (AT) {
-                    tmem_st8(a_taddr, fw);
-                    tmem_wait_st();
-                } else {
-                    st_shared_v4(a_slot + sw128_chunk(r, 0), fw[0], fw[1], fw[2], fw[3]);
-                    st_shared_v4(a_slot + sw128_chunk(r, 1), fw[4], fw[5], fw[6], fw[7]);
-                    fence_proxy_async_smem();
-                }
-                tc_fence_before();
-            }
-            ok = bar_and(bar_id, ok);          // slot-uniform from here
+        for (int j = 0; j < TPW; ++j) {   // a tile past the end computes garbage rows and stores nothing
+            tile_begin(T[j], a, base + j, r);
+            if (base + j >= n_tiles) T[j].valid = false;
+            if (ok) tile_features(T[j], a);
+            ok = tile_sync_issue(T[j], C, 0, ok, issuer);
             if (!ok) break;
-            if (issuer) issue(0);
-            // While layer 1 runs: this step's normal and the Lagrange basis at it
-            // (independent of the network's output).
-            if ((i & 3) == 0)
-                z4 = normal4(a.seed, 0u, static_cast<uint32_t>(ts.s), ts.q, static_cast<uint32_t>(i >> 2));
-            float lb[SL_MAX_M];
-            lagrange_basis_m(pick4(z4, i & 3), a.gh, a.m, lb);
-
-            // ---- hidden layers: accumulator -> ReLU -> hi/lo BF16 -> next A
-            // (unrolled: each layer's MMA issue is specialised at compile time)
-#pragma unroll
-            for (int l = 1; l <= 4; ++l) {
-                bool w = mbar_wait(d_bar, dph, abort_flag, a.status);
-                dph ^= 1u;
-                w = __all_sync(0xffffffffu, w);
-                if (w) {
-                    tc_fence_after();
-                    // Row layout of the next A (BF16 words): hi 0..24 (columns 0..49),
-                    // word 25 = {1.0, 0} (bias unit), 26..27 = 0, lo 28..52, 53..55 = 0.
-                    // columns 0..31 of the accumulator -> hi words 0..15, lo words 28..43
-                    // all three loads in flight before one wait
-                    uint32_t v[32], v2[16], u[8];
-                    tmem_ld32(taddr, v);
-                    tmem_ld16(taddr + 32, v2);
-                    tmem_ld8(taddr + 48, u);
-                    tmem_wait_ld();
-                    uint32_t hw[16], lw[16];
-                    {
-#pragma unroll
-                        for (int i2 = 0; i2 < 16; ++i2) {
-                            const float ha = __uint_as_float(v[2 * i2] & 0xFFFF0000u);
-                            const float hb = __uint_as_float(v[2 * i2 + 1] & 0xFFFF0000u);
-                            hw[i2] = pack_relu(ha, hb);
-                            lw[i2] = pack_relu(__uint_as_float(v[2 * i2]) - ha, __uint_as_float(v[2 * i2 + 1]) - hb);
-                        }
-                    }
-                    if (AT) {
-                        tmem_st16(a_taddr, hw);
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < 4; ++c)
-                            st_shared_v4(a_slot + sw128_chunk(r, c), hw[4 * c], hw[4 * c + 1], hw[4 * c + 2], hw[4 * c + 3]);
-                        st_shared_v4(a_slot + sw128_chunk(r, 7), lw[0], lw[1], lw[2], lw[3]);
-#pragma unroll
-                        for (int c = 0; c < 3; ++c)
-                            st_shared_v4(a_slot + kAAtomBytes + sw128_chunk(r, c), lw[4 + 4 * c], lw[5 + 4 * c],
-                                         lw[6 + 4 * c], lw[7 + 4 * c]);
-                    }
-                    // columns 32..49 -> hi words 16..24, lo words 44..52
-                    {
-                        uint32_t h9[9], l9[9];
-#pragma unroll
-                        for (int i2 = 0; i2 < 9; ++i2) {
-                            const uint32_t ua = (i2 < 8) ? v2[2 * i2] : u[0];
-                            const uint32_t ub = (i2 < 8) ? v2[2 * i2 + 1] : u[1];
-                            const float ha = __uint_as_float(ua & 0xFFFF0000u);
-                            const float hb = __uint_as_float(ub & 0xFFFF0000u);
-                            h9[i2] = pack_relu(ha, hb);
-                            l9[i2] = pack_relu(__uint_as_float(ua) - ha, __uint_as_float(ub) - hb);
-                        }
-                        if (AT) {
-                            const uint32_t gb[16] = {h9[0], h9[1], h9[2], h9[3], h9[4], h9[5], h9[6], h9[7],
-                                                     h9[8], 0x00003F80u, 0u, 0u, lw[0], lw[1], lw[2], lw[3]};
-                            const uint32_t gc[16] = {lw[4], lw[5], lw[6], lw[7], lw[8], lw[9], lw[10], lw[11],
-                                                     lw[12], lw[13], lw[14], lw[15], l9[0], l9[1], l9[2], l9[3]};
-                            const uint32_t gd[8] = {l9[4], l9[5], l9[6], l9[7], l9[8], 0u, 0u, 0u};
-                            tmem_st16(a_taddr + 16, gb);
-                            tmem_st16(a_taddr + 32, gc);
-                            tmem_st8(a_taddr + 48, gd);
-                        } else {
-                            st_shared_v4(a_slot + sw128_chunk(r, 4), h9[0], h9[1], h9[2], h9[3]);
-                            st_shared_v4(a_slot + sw128_chunk(r, 5), h9[4], h9[5], h9[6], h9[7]);
-                            st_shared_v4(a_slot + sw128_chunk(r, 6), h9[8], 0x00003F80u, 0u, 0u);
-                            st_shared_v4(a_slot + kAAtomBytes + sw128_chunk(r, 3), l9[0], l9[1], l9[2], l9[3]);
-                            st_shared_v4(a_slot + kAAtomBytes + sw128_chunk(r, 4), l9[4], l9[5], l9[6], l9[7]);
-                            st_shared_v4(a_slot + kAAtomBytes + sw128_chunk(r, 5), l9[8], 0u, 0u, 0u);
-                        }
-                    }
-                    if (AT) tmem_wait_st();
-                    else fence_proxy_async_smem();
-                    tc_fence_before();
-                }
-                ok = bar_and(bar_id, w);
-                if (!ok) break;
-                if (issuer) issue(l);
-            }
-            if (!ok) break;
-            // ---- output layer: collocation points y_0..y_{m-1}
-            bool w = mbar_wait(d_bar, dph, abort_flag, a.status);
-            dph ^= 1u;
-            w = __all_sync(0xffffffffu, w);
-            ok = w;     // combined across the slot at the next barrier
-            if (w) {
-                tc_fence_after();
-                uint32_t yv[8];
-                tmem_ld8(taddr, yv);
-                tmem_wait_ld();
-                tc_fence_before();
-                // ---- the 7L map g_m (Algorithm I steps 5-6): Y = sum_j y_j ell_j(X)
-                float acc = 0.0f;
-#pragma unroll
-                for (int j = SL_MAX_M - 1; j >= 0; --j) acc = fmaf(__uint_as_float(yv[j]), lb[j], acc);
-                Y = acc;
-                if (a.out_grid && ts.valid) a.out_grid[static_cast<int64_t>(i + 1) * a.total + ts.g] = Y;
-            }
+            tile_rng(T[j], a, 0);
         }
         if (!ok) break;
-        if (ts.valid) {
-            if (a.out_YT) a.out_YT[ts.g] = Y;
-            if (!isfinite(Y)) raise_status(a.status, SL_DEV_NONFINITE);
+        for (int i = 0; i < a.n_steps; ++i) {
+#pragma unroll
+            for (int l = 1; l <= 4; ++l) {
+#pragma unroll
+                for (int j = 0; j < TPW; ++j) {
+                    const bool w = tile_wait(T[j], abort_flag, a.status);
+                    if (w) tile_hidden(T[j]);
+                    ok = tile_sync_issue(T[j], C, l, w, issuer);
+                    if (!ok) break;
+                }
+                if (!ok) break;
+            }
+            if (!ok) break;
+#pragma unroll
+            for (int j = 0; j < TPW; ++j) {
+                bool w = tile_wait(T[j], abort_flag, a.status);
+                if (w) tile_out(T[j], a, i);
+                if (i + 1 < a.n_steps) {
+                    if (w) tile_features(T[j], a);
+                    w = tile_sync_issue(T[j], C, 0, w, issuer);
+                    if (w) tile_rng(T[j], a, i + 1);
+                }
+                ok = ok && w;
+            }
+            // Every warp of the warpgroup must take the same branch below and meet the
+            // same named barriers afterwards: agree on `ok` (also after the last step).
+            ok = bar_and(T[0].bar_id, ok);
+            if (!ok) break;
         }
+        if (!ok) break;
+#pragma unroll
+        for (int j = 0; j < TPW; ++j) tile_end(T[j], a);
     }
-    // Drain: each slot's issuer commits once more; the allocating warp waits for all
+    // Drain: each issuer commits once more; the allocating warp waits for all
     // (bounded) before releasing tensor memory.
     if (issuer) mma_commit_w(smem_u32(&bars[S]));
     tc_fence_before();
@@ -617,15 +586,16 @@ __global__ void __launch_bounds__(128 * S, 1) tc_7l_kernel(const SimArgs a) {
     }
 }
 
-template <int S, bool AT>
+template <int WG, int TPW>
 size_t tc_smem_bytes() {
-    return 1024 + kBBytes + (AT ? 0 : static_cast<size_t>(S) * kASlotBytes) + (S + 1) * 8 + 16;
+    return 1024 + kBBytes + (WG * TPW + 1) * 8 + 16;
 }
 
-template <int S, bool AT>
-int launch_s(const SimArgs& a, cudaStream_t st) {
-    auto kern = tc_7l_kernel<S, AT>;
-    const size_t smem = tc_smem_bytes<S, AT>();
+template <int WG, int TPW>
+int launch_cfg(const SimArgs& a, cudaStream_t st) {
+    constexpr int S = WG * TPW;
+    auto kern = tc_7l_kernel<WG, TPW>;
+    const size_t smem = tc_smem_bytes<WG, TPW>();
     int rc = cuda_error(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(smem)),
                         "tc_7l attribute");
@@ -635,50 +605,43 @@ int launch_s(const SimArgs& a, cudaStream_t st) {
     const int64_t need = (n_tiles + S - 1) / S;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    // per-slot MMA-group counters are 32-bit
-    const int64_t tiles_per_slot = (n_tiles + grid * S - 1) / (grid * S);
-    if (tiles_per_slot * a.n_steps * 5 >= (int64_t(1) << 31))
-        return set_error(SL_ERR_UNSUPPORTED, "too many path-steps for one launch (%lld tiles per slot x %d steps)",
-                         static_cast<long long>(tiles_per_slot), a.n_steps);
-    kern<<<static_cast<unsigned>(grid), 128 * S, smem, st>>>(a);
+    kern<<<static_cast<unsigned>(grid), 128 * WG, smem, st>>>(a);
     return cuda_error(cudaGetLastError(), "tc_7l launch");
 }
 
-int g_slots = 4;   // path tiles in flight per CTA (set by sl_tc_set_slots)
-int g_a_tmem = 1;  // 1: A operand in tensor memory (slots <= 4)
+int g_slots = 4;   // path tiles in flight per CTA (sl_tc_set_slots)
+int g_tpw = 1;     // tiles per warpgroup (sl_tc_set_pipeline)
 
 }  // namespace
 
 int launch_tc_7l(int m, const SimArgs& a, cudaStream_t st) {
     (void)m;
     if (a.d_in > SL_MAX_DIN_TC) return set_error(SL_ERR_UNSUPPORTED, "d_in=%d > %d", a.d_in, SL_MAX_DIN_TC);
-    if (g_a_tmem && g_slots <= 4) {
-        switch (g_slots) {
-            case 2: return launch_s<2, true>(a, st);
-            case 3: return launch_s<3, true>(a, st);
-            default: return launch_s<4, true>(a, st);
-        }
-    }
+    if (g_tpw == 2) return (g_slots == 2) ? launch_cfg<1, 2>(a, st) : launch_cfg<2, 2>(a, st);
     switch (g_slots) {
-        case 2: return launch_s<2, false>(a, st);
-        case 3: return launch_s<3, false>(a, st);
-        case 5: return launch_s<5, false>(a, st);
-        default: return launch_s<4, false>(a, st);
+        case 2: return launch_cfg<2, 1>(a, st);
+        case 3: return launch_cfg<3, 1>(a, st);
+        default: return launch_cfg<4, 1>(a, st);
     }
 }
 
 int tc_set_slots(int s) {
-    if (s < 2 || s > 5) return set_error(SL_ERR_ARG, "slots=%d outside [2,5]", s);
+    if (s < 2 || s > 4) return set_error(SL_ERR_ARG, "slots=%d outside [2,4]", s);
+    if (g_tpw == 2 && s == 3) return set_error(SL_ERR_ARG, "slots=3 needs one tile per warpgroup");
     g_slots = s;
     return SL_OK;
 }
 
 int tc_get_slots() { return g_slots; }
 
-int tc_set_a_tmem(int on) {
-    g_a_tmem = on ? 1 : 0;
+int tc_set_pipeline(int tpw) {
+    if (tpw != 1 && tpw != 2) return set_error(SL_ERR_ARG, "tiles per warpgroup=%d (1 or 2)", tpw);
+    if (tpw == 2 && g_slots == 3) return set_error(SL_ERR_ARG, "slots=3 needs one tile per warpgroup");
+    g_tpw = tpw;
     return SL_OK;
 }
+
+int tc_get_pipeline() { return g_tpw; }
 
 }  // namespace sl
 
@@ -686,6 +649,7 @@ extern "C" {
 
 int sl_tc_set_slots(int slots) { return sl::tc_set_slots(slots); }
 int sl_tc_get_slots(void) { return sl::tc_get_slots(); }
-int sl_tc_set_a_operand(int in_tensor_memory) { return sl::tc_set_a_tmem(in_tensor_memory); }
+int sl_tc_set_pipeline(int tiles_per_warpgroup) { return sl::tc_set_pipeline(tiles_per_warpgroup); }
+int sl_tc_get_pipeline(void) { return sl::tc_get_pipeline(); }
 
 }  // extern "C"

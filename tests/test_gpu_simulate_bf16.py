@@ -88,21 +88,31 @@ def test_ragged_batched_grid(sl, orc, m, d_in):
             assert mean[s] == pytest.approx(yt[off[s]:off[s + 1]].astype(np.float64).mean(), rel=1e-12)
 
 
-@pytest.mark.parametrize("slots", [2, 3, 4, 5])
-def test_slots_bit_identical(sl, orc, slots):
+def _set_cfg(sl, slots, tpw):
+    sl.tc_set_pipeline(1)
+    sl.tc_set_slots(slots)
+    sl.tc_set_pipeline(tpw)
+
+
+@pytest.mark.parametrize("slots,tpw", [(4, 2), (2, 2), (4, 1), (3, 1), (2, 1)])
+def test_launch_configs_agree(sl, orc, slots, tpw):
+    """Per-path results do not depend on tiles in flight or the pipeline shape: the
+    same arithmetic on the same inputs, identical up to FP32 rounding (different
+    kernel instantiations may contract or schedule a few operations differently)."""
     P = W.xavier_params(4, 7, seed=1)
     th = W.gbm_online_thetas(3)
     off = W.offsets_from_counts([10000, 777, 20001])
-    old = sl.tc_get_slots()
+    old = (sl.tc_get_slots(), sl.tc_get_pipeline())
     try:
-        sl.tc_set_slots(4)
+        _set_cfg(sl, 4, 1)
         ref, _ = _sim(sl, P, 4, 7, th, np.ones(3, np.float32), off, 2.0, 16, 5, sl.PREC_BF16)
-        sl.tc_set_slots(slots)
+        _set_cfg(sl, slots, tpw)
         got, _ = _sim(sl, P, 4, 7, th, np.ones(3, np.float32), off, 2.0, 16, 5, sl.PREC_BF16)
     finally:
-        sl.tc_set_slots(old)
-    assert np.array_equal(ref, got)
-    if slots == 4:
+        _set_cfg(sl, *old)
+    assert np.all(rel_err(got, ref, 1.0) <= 1e-6)
+    assert np.mean(got == ref) > 0.999
+    if (slots, tpw) == (4, 1):
         idx = np.arange(0, len(ref), 7)
         want = _oracle(orc, P, 4, 7, th, np.ones(3), off, 2.0, 16, 5, idx=idx)
         _check(orc, ref[idx], want, off, 5, 16, idx=idx)
