@@ -139,6 +139,30 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_labels_only(args, torch, sl, W, local):
+    """Offline stage alone: em_collocation_labels on the CIR label workload."""
+    sl.load()
+    dev = torch.device("cuda", local)
+    th, yi, dtr = W.cir_label_rows(1024)
+    thd, yid, dtd = (torch.as_tensor(a, device=dev) for a in (th, yi, dtr))
+    lab = torch.empty((1024, 7), dtype=torch.float32, device=dev)
+    wsl = torch.empty(sl.em_labels_workspace_size(1024, 10 ** 5, 7), dtype=torch.uint8, device=dev)
+    run = lambda: sl.em_collocation_labels(2, thd, yid, dtd, 10 ** 5, 100, 7, 1, labels=lab, ws=wsl)
+    for _ in range(max(args.warmup, 1)):
+        run()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        run()
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    print(json.dumps({"metric": "EM label samples/s (CIR 1024 rows x 1e5 paths x 100 fine steps, 7 quantiles)",
+                      "value": 1024 * 10 ** 5 / (ms * 1e-3), "unit": "samples/s", "ms_per_step": ms,
+                      "steps": args.steps, "fine_steps_per_s": 1024 * 10 ** 7 / (ms * 1e-3)}), flush=True)
+
+
 # ---------------------------------------------------------------------------
 # Our arm
 # ---------------------------------------------------------------------------
@@ -155,6 +179,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--weights", default="trained", choices=["trained", "xavier"])
+    ap.add_argument("--only-labels", action="store_true",
+                    help="time only the offline label stage (CIR, 1024 rows x 1e5 paths x 100 fine steps)")
     ap.add_argument("--train-steps", type=int, default=40000)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -166,6 +192,8 @@ def main():
 
     world, rank, local = _dist()
     torch.cuda.set_device(local)
+    if args.only_labels:
+        return run_labels_only(args, torch, sl, W, local)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
