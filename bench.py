@@ -94,6 +94,27 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(value, device="cpu"):
+    """Largest `value` over all ranks (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units processed by all ranks per second of the slowest rank (weak scaling:
+    every rank runs its own copy of the workload)."""
+    return world * units_per_rank / seconds
+
+
+def rank_seed(base_seed, rank):
+    """Each rank samples independent paths: its own Philox key."""
+    return base_seed + rank
+
+
 # ---------------------------------------------------------------------------
 # Reference arm: the FP64 oracle on the host cores (bounded sample per step)
 # ---------------------------------------------------------------------------
@@ -218,7 +239,7 @@ def main():
         params_np = W.xavier_params(4, 7, seed=0)
         weights_kind = "Xavier-uniform seed 0 (untrained)"
     w = W.gbm_online(n_paths_per_set=args.paths, params=params_np)
-    seed = w["seed"] + rank
+    seed = rank_seed(w["seed"], rank)
     total = int(w["offsets"][-1])
     n_steps, m, T = w["n_steps"], w["m"], w["T"]
     theta = torch.as_tensor(w["theta"], device=dev)
@@ -265,12 +286,9 @@ def main():
         barrier()
     ms = [a.elapsed_time(b) for a, b in ev]
     t_local = sum(ms) / 1e3
-    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    t_max = float(t.item())
+    t_max = max_over_ranks(t_local, dev)
     path_steps = total * n_steps
-    value = world * path_steps * args.steps / t_max
+    value = whole_job_rate(path_steps * args.steps, world, t_max)
     launches_per_step = 3          # 7L kernel + 2 moment kernels
 
     # --- dominant kernel alone (Y_T only: status clear + the 7L kernel)
@@ -428,10 +446,7 @@ def main():
         b.synchronize()
         if k:
             e2e_ms.append(a.elapsed_time(b))
-    e2e_t = torch.tensor([float(np.mean(e2e_ms))], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
-    e2e_value = world * path_steps / (float(e2e_t.item()) * 1e-3)
+    e2e_value = whole_job_rate(path_steps, world, max_over_ranks(float(np.mean(e2e_ms)) * 1e-3, dev))
 
     cpu = None
     accuracy = None
