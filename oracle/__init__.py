@@ -88,6 +88,9 @@ def _declare(L):
                                      _i64, _c_int, _c_dbl, _c_int, _c_int, _c_u64, _c_dbl, _i64,
                                      _c_i64, _d, _d, _d, _c_int]
     L.orc_7l_payoff_grad.restype = _c_int
+    L.orc_7l_relu_margin.argtypes = [_d, _c_int, _c_int, _c_int, _d, _c_int, _d, _i64, _c_int, _c_dbl,
+                                     _c_int, _c_int, _c_u64, _i64, _c_i64, _d, _c_int]
+    L.orc_7l_relu_margin.restype = _c_int
     L.orc_em_terminal.argtypes = [_c_int, _d, _d, _d, _c_int, _c_int, _c_i64, _c_int, _c_u64, _d,
                                   _c_int]
     L.orc_order_statistics.argtypes = [_d, _i64, _c_int, _i64, _c_int, _d]
@@ -247,6 +250,24 @@ def seven_league_payoff_grad(model, P, theta, Y0, offsets, T, n_steps, m, seed, 
     if rc:
         raise ValueError("orc_7l_payoff_grad failed")
     return yt, val, gr
+
+
+def seven_league_relu_margin(P, theta, Y0, offsets, T, n_steps, m, seed, idx=None, d_in=3, threads=0,
+                             width=WIDTH, n_hidden=N_HIDDEN):
+    """Per selected path: min |hidden pre-activation| over the network evaluations
+    along the path (the distance of its ReLU pattern from a switch)."""
+    o, n_sets = _offsets(offsets)
+    th = _f64(theta).reshape(n_sets, -1)
+    y0 = _f64(Y0).reshape(n_sets)
+    ix = None if idx is None else _i64a(idx)
+    n = int(o[-1]) if ix is None else ix.shape[0]
+    out = np.zeros(n)
+    rc = lib().orc_7l_relu_margin(_p(_f64(P), _d), d_in, width, n_hidden, _p(th, _d), th.shape[1],
+                                  _p(y0, _d), _p(o, _i64), n_sets, float(T), n_steps, m, seed,
+                                  _p(ix, _i64), n, _p(out, _d), threads)
+    if rc:
+        raise ValueError("orc_7l_relu_margin failed")
+    return out
 
 
 def em_terminal(sde, theta, Yi, dt, n_paths, n_fine, seed, row0=0, n_rows=None, threads=0):

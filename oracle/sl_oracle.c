@@ -596,6 +596,44 @@ int orc_7l_payoff_grad(int model, const double* P, int d_in, int width, int n_hi
     return 0;
 }
 
+/* Smallest |pre-activation| of any hidden unit over the network evaluations
+ * at Y_0 .. Y_{n_steps-1} of each selected path (MLP model).  The ReLU
+ * network is piecewise linear: its derivative jumps where a pre-activation
+ * crosses 0, so two evaluations that differ by rounding can only disagree on
+ * the derivative of paths whose margin is of the size of that rounding. */
+int orc_7l_relu_margin(const double* P, int d_in, int width, int n_hidden, const double* theta,
+                       int p, const double* Y0, const int64_t* offsets, int n_sets, double T,
+                       int n_steps, int m, uint64_t seed, const int64_t* idx, int64_t n_idx,
+                       double* margin, int n_threads) {
+    double xn[64], wn[64];
+    if (orc_gauss_hermite(m, xn, wn) != 0) return 1;
+    if (n_hidden > 8 || width > ORC_MAX_W) return 1;
+    orc_net N = {ORC_MODEL_MLP, d_in, width, n_hidden, ORC_ACT_RELU, m, p, P, xn};
+    double dt = T / (double)n_steps;
+    set_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < n_idx; ++k) {
+        int64_t g = idx ? idx[k] : k;
+        int s = owning_set(offsets, n_sets, g);
+        uint32_t q = (uint32_t)(g - offsets[s]);
+        const double* th = theta + (int64_t)s * p;
+        double* grid = (double*)malloc(sizeof(double) * (size_t)(n_steps + 1));
+        path_7l(&N, th, Y0[s], T, n_steps, seed, (uint32_t)s, q, grid, NULL);
+        double mg = INFINITY;
+        for (int i = 0; i < n_steps; ++i) {
+            double f[64], y[ORC_MAX_W], zs[8 * ORC_MAX_W];
+            f[0] = grid[i];
+            f[1] = dt;
+            for (int c = 0; c < p; ++c) f[2 + c] = th[c];
+            mlp_forward(P, d_in, width, n_hidden, m, ORC_ACT_RELU, f, y, zs, NULL);
+            for (int u = 0; u < n_hidden * width; ++u) mg = fabs(zs[u]) < mg ? fabs(zs[u]) : mg;
+        }
+        margin[k] = mg;
+        free(grid);
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------------------
  * Offline stage (Algorithm I step 1): Euler-Maruyama, Eq. (6.2), with
  * n_fine steps of d_tau = dt / n_fine from Y_i, normals from stream

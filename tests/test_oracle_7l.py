@@ -164,3 +164,43 @@ def test_black_scholes_gbm_exact(orc):
     for est, want in [(val, price), (g[:, 0], delta), (g[:, 2], vega), (g[:, 1], dmu)]:
         se = est.std(ddof=1) / math.sqrt(n)
         assert abs(est.mean() - want) < 4 * se + 2e-4, (est.mean(), want, se)
+
+
+def test_relu_margin_pins(orc):
+    """ReLU margin (min |hidden pre-activation| along a path):
+    (a) all weights 0: every pre-activation is its bias, so the margin is min |b|;
+    (b) only layer 1 active (W2..W4 = 0, b2..b4 = 10): the margin is the brute-force
+        min over steps i < n_steps and units of |W1 f(Y_i) + b1|, with Y_i from the
+        oracle's own path grid (Y_n does not enter: no network call is made there)."""
+    d_in, m, w = 4, 5, orc.WIDTH
+    n_p = orc.n_params(d_in, m)
+    rng = np.random.default_rng(3)
+    P = np.zeros(n_p)
+    o1 = w * d_in
+    bias_idx = [o1 + np.arange(w)]
+    o = o1 + w
+    for _ in range(3):
+        bias_idx.append(o + w * w + np.arange(w))
+        o += w * w + w
+    for bi in bias_idx:
+        P[bi] = rng.uniform(-1, 1, w)
+    th = np.array([[0.1, 0.3]])
+    off = [0, 20]
+    mg = orc.seven_league_relu_margin(P, th, [1.0], off, 1.0, 3, m, 1, d_in=d_in)
+    assert np.all(mg == min(np.abs(P[bi]).min() for bi in bias_idx))
+    # (b)
+    P2 = np.zeros(n_p)
+    P2[:o1] = rng.normal(0, 0.5, o1)
+    P2[bias_idx[0]] = rng.normal(0, 0.3, w)
+    for bi in bias_idx[1:]:
+        P2[bi] = 10.0
+    P2[o:o + m * w] = rng.normal(0, 0.3, m * w)    # output layer: paths move
+    n_steps = 6
+    _, grid = orc.seven_league_paths(0, P2, th, [1.0], off, 1.0, n_steps, m, 2, d_in=d_in, grid=True)
+    mg = orc.seven_league_relu_margin(P2, th, [1.0], off, 1.0, n_steps, m, 2, d_in=d_in)
+    W1, b1 = P2[:o1].reshape(w, d_in), P2[bias_idx[0]]
+    for k in range(20):
+        f = np.stack([grid[k, :n_steps], np.full(n_steps, 1.0 / n_steps), np.full(n_steps, 0.1),
+                      np.full(n_steps, 0.3)], 1)
+        z = f @ W1.T + b1
+        assert mg[k] == pytest.approx(np.abs(z).min(), rel=1e-12, abs=1e-15)
