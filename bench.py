@@ -399,25 +399,28 @@ def main():
         secondary["cir_batched_workload"] = ("CIR 4096 theta sets, %d paths (log-uniform 1e3..1e5 per set), "
                                              "32 steps, m=7, one persistent launch in a CUDA graph" % tot_c)
         del yt_c, ws_c
-        # adjoint: GBM network, 1e6 paths, 64 steps, checkpoint every 8 steps, K = 1
+        # adjoint: GBM network, 1e6 paths, 64 steps, checkpoint every 8 steps, K = 1, in both
+        # network forms (FP32 CUDA cores; BF16 tcgen05)
         n_a = 10 ** 6
         off_a = torch.as_tensor(W.offsets_from_counts([n_a]), device=dev)
-        net_a = sl.make_net(P, 4, 7, prec=sl.PREC_FP32)
         th_a = torch.tensor([[0.1, 0.3]], device=dev)
         y0_a = torch.ones(1, device=dev)
         ws_a = torch.empty(sl.adjoint_workspace_size(n_a, 1, 64, 8, 2), dtype=torch.uint8, device=dev)
-        run_a = lambda: sl.seven_league_adjoint(sl.MODEL_MLP, net_a, th_a, y0_a, off_a, 1.0, 64, 7, 1, 1.0,
-                                                ckpt_k=8, ws=ws_a, total_paths=n_a)
-        run_a()
-        torch.cuda.synchronize()
-        e0.record(stream)
-        v_a, d0_a, dth_a = run_a()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        secondary["adjoint_path_steps_per_s"] = n_a * 64 / (e0.elapsed_time(e1) * 1e-3)
-        secondary["adjoint_workload"] = ("GBM network (FP32 form), 1e6 paths x 64 steps, checkpoint every 8, "
-                                         "call K=1: value %.5f dY0 %.5f dtheta %s"
-                                         % (v_a.item(), d0_a.item(), [round(x, 5) for x in dth_a[0].tolist()]))
+        for pr, key in ((sl.PREC_FP32, "adjoint_fp32"), (sl.PREC_BF16, "adjoint_bf16")):
+            net_a = sl.make_net(P, 4, 7, prec=pr)
+            run_a = lambda: sl.seven_league_adjoint(sl.MODEL_MLP, net_a, th_a, y0_a, off_a, 1.0, 64, 7, 1, 1.0,
+                                                    ckpt_k=8, ws=ws_a, total_paths=n_a)
+            run_a()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            v_a, d0_a, dth_a = run_a()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            assert sl.workspace_status(ws_a) == 0
+            secondary[key + "_path_steps_per_s"] = n_a * 64 / (e0.elapsed_time(e1) * 1e-3)
+            secondary[key + "_result"] = ("value %.5f dY0 %.5f dtheta %s"
+                                          % (v_a.item(), d0_a.item(), [round(x, 5) for x in dth_a[0].tolist()]))
+        secondary["adjoint_workload"] = "GBM network, 1e6 paths x 64 steps, checkpoint every 8, call K=1"
 
     # --- end to end through the C ABI with host buffers (pinned), copies timed
     h_theta = torch.as_tensor(w["theta"]).pin_memory()

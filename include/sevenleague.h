@@ -268,7 +268,10 @@ size_t sl_adjoint_workspace_size(int64_t total_paths, int n_sets, int n_steps, i
  * seed_grad: device FP64 [n_sets] upstream factors (NULL = 1), for use as the
  * backward of an autograd function.  out_paths: device FP32 [(2+p)][total]
  * per-path (f, df/dY0, df/dtheta_0..) or NULL (kept in the workspace).
- * The network form is the FP32 CUDA-core form (net->prec is not used here).
+ * Network forms: net->prec = SL_PREC_FP32 runs the FP32 CUDA-core form;
+ * SL_PREC_BF16 (ReLU, d_in <= SL_MAX_DIN_TC) runs the tcgen05 form, which
+ * samples the same paths as the BF16 sampler and back-propagates through the
+ * same BF16 weights (hi + lo BF16 cotangents, FP32 accumulation).
  */
 int seven_league_adjoint(int model, const sl_net* net, const float* theta, int p, const float* Y0,
                          const int64_t* path_offsets, int n_sets, int64_t total_paths, float T,

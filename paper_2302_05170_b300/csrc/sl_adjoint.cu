@@ -341,6 +341,9 @@ int launch_adj(const AdjArgs& A, cudaStream_t st) {
 int model_p(int model) { return model == SL_MODEL_GBM_EXACT ? 2 : 3; }
 
 }  // namespace
+
+int launch_tc_adjoint(const SimArgs& s, float K, int k, int n_ckpt, float* ckpt, float* pv, cudaStream_t st);
+
 }  // namespace sl
 
 using namespace sl;
@@ -378,6 +381,13 @@ int seven_league_adjoint(int model, const sl_net* net, const float* theta, int p
         if (net->m != m || net->d_in != p + 2) return set_error(SL_ERR_ARG, "network shape");
         if (net->d_in > SL_MAX_DIN) return set_error(SL_ERR_UNSUPPORTED, "d_in=%d", net->d_in);
         if (net->act != SL_ACT_RELU && net->act != SL_ACT_SOFTPLUS) return set_error(SL_ERR_ARG, "act");
+        if (net->prec != SL_PREC_FP32 && net->prec != SL_PREC_BF16) return set_error(SL_ERR_ARG, "prec");
+        if (net->prec == SL_PREC_BF16) {
+            if (net->act != SL_ACT_RELU)
+                return set_error(SL_ERR_UNSUPPORTED, "the BF16 tensor-core form supports ReLU only");
+            if (net->d_in > SL_MAX_DIN_TC)
+                return set_error(SL_ERR_UNSUPPORTED, "BF16 form: d_in=%d > %d", net->d_in, SL_MAX_DIN_TC);
+        }
     } else if (p != model_p(model)) {
         return set_error(SL_ERR_ARG, "model %d needs p=%d", model, model_p(model));
     }
@@ -420,6 +430,7 @@ int seven_league_adjoint(int model, const sl_net* net, const float* theta, int p
     if (total_paths > 0) {
         if (model == SL_MODEL_GBM_EXACT) rc = launch_adj<SL_MODEL_GBM_EXACT, 0>(A, st);
         else if (model == SL_MODEL_OU_EXACT) rc = launch_adj<SL_MODEL_OU_EXACT, 0>(A, st);
+        else if (net->prec == SL_PREC_BF16) rc = launch_tc_adjoint(a, K, ckpt_k, n_ckpt, A.ckpt, A.pv, st);
         else if (net->act == SL_ACT_SOFTPLUS) rc = launch_adj<SL_MODEL_MLP, SL_ACT_SOFTPLUS>(A, st);
         else rc = launch_adj<SL_MODEL_MLP, SL_ACT_RELU>(A, st);
         if (rc) return rc;

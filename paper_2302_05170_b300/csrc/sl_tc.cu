@@ -32,426 +32,12 @@
 // (about one second of global time); on expiry the kernel sets SL_DEV_TIMEOUT
 // in the status word, the slot stops, every issuer drains its own MMAs
 // (bounded) and the tensor memory is released.
-#include <cuda_bf16.h>
-#include <math.h>
-
-#include "sl_internal.cuh"
+#include "sl_tc_common.cuh"
 
 namespace sl {
 namespace {
 
-constexpr int kTile = 128;                    // paths per slot (MMA M, TMEM lanes)
-constexpr int kRowBytes = 128;                // one 128B-swizzle row = 64 BF16
-constexpr int kB1Bytes = 64 * kRowBytes;                 // layer 1: 64 rows x (16 of 64) cols
-constexpr int kBHBytes = 2 * 64 * kRowBytes;             // hidden: 64 rows x 112 cols
-constexpr int kB5Bytes = 2 * 16 * kRowBytes;             // output: 16 rows x 112 cols
-constexpr int kBBytes = kB1Bytes + 3 * kBHBytes + kB5Bytes;
-constexpr int kLoCol = 56;                               // first column of the lo half
-constexpr int kBiasCol = 50;                             // constant-1 column
-constexpr uint64_t kTimeoutNs = 1000000000ull;           // bounded waits: 1 s
-
-// ----------------------------------------------------------------------------
-// PTX wrappers
-// ----------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for the phase with the given parity; false on abort/timeout.
-__device__ __noinline__ bool mbar_wait_slow(uint32_t addr, uint32_t parity, volatile int* abort_flag,
-                                            unsigned* status) {
-    const uint64_t t0 = global_ns();
-    while (true) {
-        if (mbar_try_wait(addr, parity)) return true;
-        if (*abort_flag) return false;
-        if (global_ns() - t0 > kTimeoutNs) {
-            *abort_flag = 1;
-            raise_status(status, SL_DEV_TIMEOUT);
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, volatile int* abort_flag,
-                                          unsigned* status) {
-#pragma unroll 1
-    for (int it = 0; it < 64; ++it)
-        if (mbar_try_wait(addr, parity)) return true;
-    return mbar_wait_slow(addr, parity, abort_flag, status);
-}
-
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, rows of 128 B,
-// 8-row atoms 1024 B apart (stride byte offset), fixed 0b001 at bits 46-48.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-    return (static_cast<uint64_t>((saddr >> 4) & 0x3FFFu)) |
-           (static_cast<uint64_t>(1u) << 16) |                       // leading byte offset (unused)
-           (static_cast<uint64_t>(1024u >> 4) << 32) |               // stride byte offset
-           (static_cast<uint64_t>(1u) << 46) |                       // descriptor version
-           (static_cast<uint64_t>(2u) << 61);                        // SWIZZLE_128B
-}
-
-// Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
-           (static_cast<uint32_t>(M >> 4) << 24);
-}
-
-// MMA (A and B from shared memory, or A from tensor memory: row i of A in lane
-// i, two BF16 values per 32-bit column, K along the columns) and commit.
-// Warp-converged forms: every lane of the issuing warp executes the call with
-// the same (warp-uniform) operands and one lane, chosen by elect.sync, issues.
-// Keeping the control flow converged lets the descriptors stay in uniform
-// registers; issuing from a divergent single-lane branch costs ~2.5x per MMA.
-__device__ __forceinline__ void mma_commit_w(uint32_t mbar) {
-    asm volatile(
-        "{\n.reg .pred e;\nelect.sync _|e, 0xffffffff;\n"
-        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}" ::"r"(mbar)
-        : "memory");
-}
-
-// The seven K-steps of one layer (K = 112) from tensor-memory A, then the
-// commit, in one block with a single elect.sync: A column of step k is
-// a_tmem + 8k; B descriptor of step k is db + 2k (k < 4) or db + b_atom1 + 2(k-4).
-__device__ __forceinline__ void mma7_ta_commit(uint32_t d_tmem, uint32_t a_tmem, uint64_t db,
-                                               uint64_t b_atom1, uint32_t idesc, uint32_t mbar) {
-    asm volatile(
-        "{\n.reg .pred e, pf, pt;\n.reg .b64 b1, b2, b3, b4, b5, b6;\n.reg .b32 a1, a2, a3, a4, a5, a6;\n"
-        "elect.sync _|e, 0xffffffff;\n"
-        "setp.ne.b32 pf, %3, %3;\nsetp.eq.b32 pt, %3, %3;\n"
-        "add.s64 b1, %2, 2;\nadd.s64 b2, %2, 4;\nadd.s64 b3, %2, 6;\n"
-        "add.s64 b4, %2, %4;\nadd.s64 b5, b4, 2;\nadd.s64 b6, b4, 4;\n"
-        "add.u32 a1, %1, 8;\nadd.u32 a2, %1, 16;\nadd.u32 a3, %1, 24;\n"
-        "add.u32 a4, %1, 32;\nadd.u32 a5, %1, 40;\nadd.u32 a6, %1, 48;\n"
-        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, pf;\n"
-        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [a1], b1, %3, pt;\n"
-        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [a2], b2, %3, pt;\n"
-        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [a3], b3, %3, pt;\n"
-        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [a4], b4, %3, pt;\n"
-        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [a5], b5, %3, pt;\n"
-        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [a6], b6, %3, pt;\n"
-        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%5];\n}" ::"r"(d_tmem),
-        "r"(a_tmem), "l"(db), "r"(idesc), "l"(b_atom1), "r"(mbar)
-        : "memory");
-}
-
-// Layer 1 (K = 16) from tensor-memory A, then the commit.
-__device__ __forceinline__ void mma1_ta_commit(uint32_t d_tmem, uint32_t a_tmem, uint64_t db, uint32_t idesc,
-                                               uint32_t mbar) {
-    asm volatile(
-        "{\n.reg .pred e, pf;\nelect.sync _|e, 0xffffffff;\nsetp.ne.b32 pf, %3, %3;\n"
-        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, pf;\n"
-        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%4];\n}" ::"r"(d_tmem),
-        "r"(a_tmem), "l"(db), "r"(idesc), "r"(mbar)
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
-          "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
-          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-          "=r"(v[14]), "=r"(v[15])
-        : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                   "=r"(v[6]), "=r"(v[7])
-                 : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
-        ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),
-        "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
-        "r"(v[15])
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
-                 "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_wait_st() {
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_wait_ld() {
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// (lo element, hi element) -> packed BF16x2 with ReLU; lo element in the low half.
-__device__ __forceinline__ uint32_t pack_relu(float lo_elem, float hi_elem) {
-    uint32_t d;
-    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi_elem), "f"(lo_elem));
-    return d;
-}
-__device__ __forceinline__ uint32_t pack_rn(float lo_elem, float hi_elem) {
-    uint32_t d;
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi_elem), "f"(lo_elem));
-    return d;
-}
-
-// Byte offset of 16-byte chunk `c` (0..7) of row `r` inside a 128B-swizzled atom.
-__device__ __forceinline__ uint32_t sw128_chunk(int r, int c) {
-    return static_cast<uint32_t>((r >> 3) * 1024 + (r & 7) * kRowBytes + ((c ^ (r & 7)) << 4));
-}
-
-// Byte offset of element (row n, column k) of a B tile with `rows` rows.
-__device__ __forceinline__ uint32_t b_elem_off(int rows, int n, int k) {
-    const int atom = k >> 6, kc = k & 63;
-    return static_cast<uint32_t>(atom * rows * kRowBytes) + sw128_chunk(n, kc >> 3) +
-           static_cast<uint32_t>((kc & 7) * 2);
-}
-
-// Stage the network's weights as BF16 B tiles.
-//   B1[n][2i] = B1[n][2i+1] = W1[n][i] (i < d_in), B1[n][2 d_in] = b1[n]
-//   Bl[n][k] = Wl[n][k], Bl[n][50] = bl[n], Bl[n][56+k] = Wl[n][k] (k < 50)
-__device__ void stage_weights(unsigned char* sB, const float* __restrict__ P, int d_in, int m) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int W = SL_WIDTH;
-    for (int i = tid; i < kBBytes / 2; i += nt) reinterpret_cast<uint16_t*>(sB)[i] = 0;
-    __syncthreads();
-    // layer 1
-    const float* W1 = P;
-    const float* b1 = P + W * d_in;
-    for (int i = tid; i < W * 16; i += nt) {
-        const int n = i / 16, k = i % 16;
-        float v = 0.0f;
-        if (k < 2 * d_in) v = W1[n * d_in + (k >> 1)];
-        else if (k == 2 * d_in) v = b1[n];
-        else continue;
-        *reinterpret_cast<__nv_bfloat16*>(sB + b_elem_off(64, n, k)) = __float2bfloat16_rn(v);
-    }
-    const float* p = b1 + W;
-    unsigned char* dst = sB + kB1Bytes;
-    for (int l = 0; l < 4; ++l) {
-        const int rows = (l < 3) ? 64 : 16;
-        const int n_out = (l < 3) ? W : m;
-        const float* Wl = p;
-        const float* bl = p + n_out * W;
-        for (int i = tid; i < n_out * 112; i += nt) {
-            const int n = i / 112, k = i % 112;
-            float v;
-            if (k < W) v = Wl[n * W + k];
-            else if (k == kBiasCol) v = bl[n];
-            else if (k >= kLoCol && k < kLoCol + W) v = Wl[n * W + (k - kLoCol)];
-            else continue;
-            *reinterpret_cast<__nv_bfloat16*>(dst + b_elem_off(rows, n, k)) = __float2bfloat16_rn(v);
-        }
-        p = bl + n_out;
-        dst += (l < 3) ? kBHBytes : kB5Bytes;
-    }
-}
-
-// AND of `v` over the 128 threads of named barrier `id` (also a barrier).
-__device__ __forceinline__ bool bar_and(int id, bool v) {
-    uint32_t r;
-    asm volatile(
-        "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.and.pred q, %2, 128, p;\nselp.u32 %0, 1, 0, q;\n}"
-        : "=r"(r)
-        : "r"(static_cast<uint32_t>(v)), "r"(id)
-        : "memory");
-    return r != 0;
-}
-
-// Per-thread state of one path tile (128 paths; this thread owns row `r`).
-struct Tile {
-    int64_t g;        // flat path index of this thread's row
-    int s;            // owning parameter set
-    uint32_t q;       // path index within the set (Philox counter)
-    bool valid;       // row holds a real path
-    float Y;          // state
-    float feat[SL_MAX_DIN_TC];
-    float4 z4;        // normals of the current block of 4 steps
-    float lb[SL_MAX_M];   // Lagrange basis at this step's normal
-    uint32_t dph;     // phase of the tile's d_ready barrier
-    uint32_t d_tmem;  // accumulator (lane 0 of the tile; A at +64)
-    uint32_t taddr;   // accumulator, this warp's lanes
-    uint32_t d_bar;   // mbarrier: the tile's MMAs completed
-    int bar_id;       // named barrier of the tile's warpgroup
-};
-
-// Kernel-wide constants of the issue path.
-struct IssueConst {
-    uint64_t db0, db1, db2, db3, db4;   // B descriptors of layers 1..5
-};
-
-__device__ __forceinline__ void tile_begin(Tile& T, const SimArgs& a, int64_t tile, int r) {
-    T.g = tile * kTile + r;
-    T.valid = T.g < a.total;
-    T.s = 0;
-    int64_t qq = T.g;
-    if (a.offsets) {
-        T.s = owning_set(a.offsets, a.n_sets, T.valid ? T.g : a.total - 1);
-        qq = T.g - __ldg(a.offsets + T.s);
-    }
-    T.q = static_cast<uint32_t>(qq);
-    const float* th = a.theta + static_cast<int64_t>(T.s) * a.p;
-    T.feat[0] = 0.0f;
-    T.feat[1] = a.dt;
-#pragma unroll
-    for (int k = 0; k < SL_MAX_DIN_TC - 2; ++k) T.feat[2 + k] = (k < a.p) ? __ldg(th + k) : 0.0f;
-    T.Y = a.Y0 ? __ldg(a.Y0 + T.s) : a.y0_scalar;
-    if (a.out_grid && T.valid) a.out_grid[T.g] = T.Y;
-    T.z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-}
-
-// Layer-1 A row: features [Y, dt, theta] as (hi, lo) BF16 pairs, then the constant 1.
-__device__ __forceinline__ void tile_features(Tile& T, const SimArgs& a) {
-    T.feat[0] = T.Y;
-    uint32_t fw[8];
-#pragma unroll
-    for (int k = 0; k < SL_MAX_DIN_TC; ++k) {
-        const float hi = __uint_as_float(__float_as_uint(T.feat[k]) & 0xFFFF0000u);
-        const uint32_t wv = pack_rn(hi, T.feat[k] - hi);
-        fw[k] = (k < a.d_in) ? wv : ((k == a.d_in) ? 0x00003F80u : 0u);   // 1.0 after the features
-    }
-    fw[7] = (a.d_in == SL_MAX_DIN_TC) ? 0x00003F80u : 0u;
-    tmem_st8(T.taddr + 64, fw);
-    tmem_wait_st();
-    tc_fence_before();
-}
-
-// All four warps agree (named-barrier AND) that the next A is written; warp 0
-// then issues layer l's MMAs and commits them to the tile's d_ready.
-__device__ __forceinline__ bool tile_sync_issue(const Tile& T, const IssueConst& C, int l, bool ok, bool issuer) {
-    ok = bar_and(T.bar_id, ok);
-    if (ok && issuer) {
-        constexpr uint32_t kIdesc64 = idesc_bf16(128, 64), kIdesc16 = idesc_bf16(128, 16);
-        tc_fence_after();
-        if (l == 0) {
-            mma1_ta_commit(T.d_tmem, T.d_tmem + 64, C.db0, kIdesc64, T.d_bar);
-        } else {
-            const uint64_t db = (l == 1) ? C.db1 : (l == 2) ? C.db2 : (l == 3) ? C.db3 : C.db4;
-            mma7_ta_commit(T.d_tmem, T.d_tmem + 64, db, (l < 4) ? (64 * kRowBytes) >> 4 : (16 * kRowBytes) >> 4,
-                           (l < 4) ? kIdesc64 : kIdesc16, T.d_bar);
-        }
-    }
-    return ok;
-}
-
-// Normal of step i and the Lagrange basis at it (independent of the network).
-__device__ __forceinline__ void tile_rng(Tile& T, const SimArgs& a, int i) {
-    if ((i & 3) == 0)
-        T.z4 = normal4(a.seed, 0u, static_cast<uint32_t>(T.s), T.q, static_cast<uint32_t>(i >> 2));
-    lagrange_basis_m(pick4(T.z4, i & 3), a.gh, a.m, T.lb);
-}
-
-__device__ __forceinline__ bool tile_wait(Tile& T, volatile int* abort_flag, unsigned* status) {
-    bool w = mbar_wait(T.d_bar, T.dph, abort_flag, status);
-    T.dph ^= 1u;
-    return __all_sync(0xffffffffu, w);
-}
-
-// Hidden-layer epilogue: accumulator row -> ReLU -> BF16 hi + lo -> next A row.
-// A row (BF16 words): hi 0..24 (columns 0..49), word 25 = {1.0, 0} (bias unit),
-// 26..27 = 0, lo 28..52, 53..55 = 0.
-__device__ __forceinline__ void tile_hidden(const Tile& T) {
-    tc_fence_after();
-    uint32_t v[32], v2[16], u[8];
-    tmem_ld32(T.taddr, v);
-    tmem_ld16(T.taddr + 32, v2);
-    tmem_ld8(T.taddr + 48, u);
-    tmem_wait_ld();
-    const uint32_t at = T.taddr + 64;
-    uint32_t hw[16], lw[16];
-#pragma unroll
-    for (int i2 = 0; i2 < 16; ++i2) {   // columns 0..31 -> hi words 0..15, lo words 28..43
-        const float ha = __uint_as_float(v[2 * i2] & 0xFFFF0000u);
-        const float hb = __uint_as_float(v[2 * i2 + 1] & 0xFFFF0000u);
-        hw[i2] = pack_relu(ha, hb);
-        lw[i2] = pack_relu(__uint_as_float(v[2 * i2]) - ha, __uint_as_float(v[2 * i2 + 1]) - hb);
-    }
-    tmem_st16(at, hw);
-    uint32_t h9[9], l9[9];
-#pragma unroll
-    for (int i2 = 0; i2 < 9; ++i2) {    // columns 32..49 -> hi words 16..24, lo words 44..52
-        const uint32_t ua = (i2 < 8) ? v2[2 * i2] : u[0];
-        const uint32_t ub = (i2 < 8) ? v2[2 * i2 + 1] : u[1];
-        const float ha = __uint_as_float(ua & 0xFFFF0000u);
-        const float hb = __uint_as_float(ub & 0xFFFF0000u);
-        h9[i2] = pack_relu(ha, hb);
-        l9[i2] = pack_relu(__uint_as_float(ua) - ha, __uint_as_float(ub) - hb);
-    }
-    const uint32_t gb[16] = {h9[0], h9[1], h9[2], h9[3], h9[4], h9[5], h9[6], h9[7],
-                             h9[8], 0x00003F80u, 0u, 0u, lw[0], lw[1], lw[2], lw[3]};
-    const uint32_t gc[16] = {lw[4], lw[5], lw[6], lw[7], lw[8], lw[9], lw[10], lw[11],
-                             lw[12], lw[13], lw[14], lw[15], l9[0], l9[1], l9[2], l9[3]};
-    const uint32_t gd[8] = {l9[4], l9[5], l9[6], l9[7], l9[8], 0u, 0u, 0u};
-    tmem_st16(at + 16, gb);
-    tmem_st16(at + 32, gc);
-    tmem_st8(at + 48, gd);
-    tmem_wait_st();
-    tc_fence_before();
-}
-
-// Output layer: collocation points y_j, then Y_{i+1} = g_m(X) = sum_j y_j ell_j(X)
-// (Algorithm I steps 5-6).
-__device__ __forceinline__ void tile_out(Tile& T, const SimArgs& a, int i) {
-    tc_fence_after();
-    uint32_t yv[8];
-    tmem_ld8(T.taddr, yv);
-    tmem_wait_ld();
-    tc_fence_before();
-    float acc = 0.0f;
-#pragma unroll
-    for (int j = SL_MAX_M - 1; j >= 0; --j) acc = fmaf(__uint_as_float(yv[j]), T.lb[j], acc);
-    T.Y = acc;
-    if (a.out_grid && T.valid) a.out_grid[static_cast<int64_t>(i + 1) * a.total + T.g] = T.Y;
-}
-
-__device__ __forceinline__ void tile_end(const Tile& T, const SimArgs& a) {
-    if (!T.valid) return;
-    if (a.out_YT) a.out_YT[T.g] = T.Y;
-    if (!isfinite(T.Y)) raise_status(a.status, SL_DEV_NONFINITE);
-}
+using namespace tc;
 
 // WG warpgroups per CTA, TPW path tiles per warpgroup (S = WG * TPW tiles in
 // flight).  Warp w of a warpgroup reads and writes TMEM lanes 32(w%4).., i.e.

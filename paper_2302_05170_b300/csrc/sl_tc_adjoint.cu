@@ -1,0 +1,454 @@
+// sl_tc_adjoint.cu -- BF16 tensor-core (tcgen05) form of the pathwise adjoint:
+// sensitivities of E[max(Y_T - K, 0)] with respect to Y0 and theta through
+// g_m and the network, with Y_i checkpointed every k steps.
+//
+// Per path tile (128 paths, one warpgroup, warp 0 issues the MMAs):
+//  1. forward sweep of the 7L sampler (same MMA chain and epilogues as the
+//     sampling kernel), writing Y_{ck} to the checkpoint buffer;
+//  2. lambda = 1{Y_T > K}; a tile whose paths are all out of the money stops;
+//  3. per segment (last first): recompute Y_{ck} .. Y_{ck+k-1} from the
+//     checkpoint; then per step i, from the segment's last to its first:
+//     a. mask pass: layers 1-4 at Y_i; the ReLU pattern of every hidden layer
+//        is kept in tensor memory (the packed BF16 "hi" words of the layer's
+//        output: non-zero exactly where the pre-activation is positive);
+//     b. backward chain with c_j = lambda * ell_j(X_i) (the cotangent of the
+//        collocation points: d Y_{i+1} / d y_j = ell_j(X_i)):
+//        dh4 = W5^T c, dz_l = dh_l masked, dh_{l-1} = W_l^T dz_l, ...,
+//        d/df = W1^T dz1, as tcgen05 MMAs against transposed BF16 weight
+//        tiles; the cotangents are split into BF16 hi + lo like the forward
+//        activations (A operand in tensor memory);
+//     c. lambda <- d/dY_i, g_theta += d/dtheta.
+//  4. per-path outputs (payoff, lambda, g_theta); per-set FP64 means by the
+//     shared deterministic reduction.
+//
+// Tensor memory per tile: 256 columns -- accumulator 0..63, A operand
+// 64..119, masks of hidden layers 1..4 at 128 + 32 (l-1) (25 words each).
+#include "sl_tc_common.cuh"
+
+namespace sl {
+namespace {
+
+using namespace tc;
+
+constexpr int kMaxCkptK = 32;
+constexpr int kB5TBytes = 64 * kRowBytes;          // W5^T: 64 rows (in-neurons) x K = 16 (m hi, m lo)
+constexpr int kBHTBytes = 2 * 64 * kRowBytes;      // W_l^T: 64 rows x K = 112
+constexpr int kB1TBytes = 2 * 16 * kRowBytes;      // W1^T: 16 rows (features) x K = 112
+constexpr int kBTBytes = kB5TBytes + 3 * kBHTBytes + kB1TBytes;
+
+struct AdjTC {
+    SimArgs s;
+    float K;
+    int k;          // checkpoint interval
+    int n_ckpt;
+    float* ckpt;    // [n_ckpt][total]
+    float* pv;      // [(2+p)][total]
+};
+
+// Transposed weights for the backward chain (BF16, 128B-swizzled, K-major):
+//   B5T[n][j] = B5T[n][8 + j] = W5[j][n]              (n < 50, j < m)
+//   BlT[n][k] = BlT[n][56 + k] = W_l[k][n]            (l = 4, 3, 2; n, k < 50)
+//   B1T[n][k] = B1T[n][56 + k] = W1[k][n]             (n < d_in, k < 50)
+__device__ void stage_weights_T(unsigned char* sBT, const float* __restrict__ P, int d_in, int m) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int W = SL_WIDTH;
+    for (int i = tid; i < kBTBytes / 2; i += nt) reinterpret_cast<uint16_t*>(sBT)[i] = 0;
+    __syncthreads();
+    // offsets of W_l in the flat parameter array
+    const int o1 = 0;
+    const int o2 = W * d_in + W;
+    const int o3 = o2 + W * W + W;
+    const int o4 = o3 + W * W + W;
+    const int o5 = o4 + W * W + W;
+    unsigned char* d5 = sBT;
+    for (int i = tid; i < W * 16; i += nt) {
+        const int n = i / 16, k = i % 16, j = k & 7;
+        if (j >= m) continue;
+        *reinterpret_cast<__nv_bfloat16*>(d5 + b_elem_off(64, n, k)) = __float2bfloat16_rn(P[o5 + j * W + n]);
+    }
+    const int offs[3] = {o4, o3, o2};   // W4^T, W3^T, W2^T
+    for (int q = 0; q < 3; ++q) {
+        unsigned char* d = sBT + kB5TBytes + q * kBHTBytes;
+        for (int i = tid; i < W * 112; i += nt) {
+            const int n = i / 112, k = i % 112;
+            int kk;
+            if (k < W) kk = k;
+            else if (k >= kLoCol && k < kLoCol + W) kk = k - kLoCol;
+            else continue;
+            *reinterpret_cast<__nv_bfloat16*>(d + b_elem_off(64, n, k)) = __float2bfloat16_rn(P[offs[q] + kk * W + n]);
+        }
+    }
+    unsigned char* d1 = sBT + kB5TBytes + 3 * kBHTBytes;
+    for (int i = tid; i < d_in * 112; i += nt) {
+        const int n = i / 112, k = i % 112;
+        int kk;
+        if (k < W) kk = k;
+        else if (k >= kLoCol && k < kLoCol + W) kk = k - kLoCol;
+        else continue;
+        *reinterpret_cast<__nv_bfloat16*>(d1 + b_elem_off(16, n, k)) = __float2bfloat16_rn(P[o1 + kk * d_in + n]);
+    }
+}
+
+struct IssueConstT {
+    uint64_t db5, db4, db3, db2, db1;   // transposed B descriptors, in chain order
+};
+
+// Backward MMAs of chain step lt (0: W5^T, 1: W4^T, 2: W3^T, 3: W2^T, 4: W1^T).
+__device__ __forceinline__ bool tile_sync_issue_T(const Tile& T, const IssueConstT& C, int lt, bool ok, bool issuer) {
+    ok = bar_and(T.bar_id, ok);
+    if (ok && issuer) {
+        constexpr uint32_t kIdesc64 = idesc_bf16(128, 64), kIdesc16 = idesc_bf16(128, 16);
+        tc_fence_after();
+        if (lt == 0) {
+            mma1_ta_commit(T.d_tmem, T.d_tmem + 64, C.db5, kIdesc64, T.d_bar);
+        } else {
+            const uint64_t db = (lt == 1) ? C.db4 : (lt == 2) ? C.db3 : (lt == 3) ? C.db2 : C.db1;
+            mma7_ta_commit(T.d_tmem, T.d_tmem + 64, db, (lt < 4) ? (64 * kRowBytes) >> 4 : (16 * kRowBytes) >> 4,
+                           (lt < 4) ? kIdesc64 : kIdesc16, T.d_bar);
+        }
+    }
+    return ok;
+}
+
+// Forward hidden epilogue that also keeps the layer's ReLU pattern: the packed
+// hi words 0..24 of the next A row go to the mask columns `mcol` as well.
+__device__ __forceinline__ void tile_hidden_keep_mask(const Tile& T, uint32_t mcol) {
+    tc_fence_after();
+    uint32_t v[32], v2[16], u[8];
+    tmem_ld32(T.taddr, v);
+    tmem_ld16(T.taddr + 32, v2);
+    tmem_ld8(T.taddr + 48, u);
+    tmem_wait_ld();
+    const uint32_t at = T.taddr + 64;
+    uint32_t hw[16], lw[16];
+#pragma unroll
+    for (int i2 = 0; i2 < 16; ++i2) split_relu(v[2 * i2], v[2 * i2 + 1], hw[i2], lw[i2]);
+    tmem_st16(at, hw);
+    tmem_st16(T.taddr + mcol, hw);
+    uint32_t h9[9], l9[9];
+#pragma unroll
+    for (int i2 = 0; i2 < 9; ++i2)
+        split_relu((i2 < 8) ? v2[2 * i2] : u[0], (i2 < 8) ? v2[2 * i2 + 1] : u[1], h9[i2], l9[i2]);
+    const uint32_t gb[16] = {h9[0], h9[1], h9[2], h9[3], h9[4], h9[5], h9[6], h9[7],
+                             h9[8], 0x00003F80u, 0u, 0u, lw[0], lw[1], lw[2], lw[3]};
+    const uint32_t gc[16] = {lw[4], lw[5], lw[6], lw[7], lw[8], lw[9], lw[10], lw[11],
+                             lw[12], lw[13], lw[14], lw[15], l9[0], l9[1], l9[2], l9[3]};
+    const uint32_t gd[8] = {l9[4], l9[5], l9[6], l9[7], l9[8], 0u, 0u, 0u};
+    const uint32_t gm[16] = {h9[0], h9[1], h9[2], h9[3], h9[4], h9[5], h9[6], h9[7], h9[8], 0u, 0u, 0u,
+                             0u, 0u, 0u, 0u};
+    tmem_st16(at + 16, gb);
+    tmem_st16(at + 32, gc);
+    tmem_st8(at + 48, gd);
+    tmem_st16(T.taddr + mcol + 16, gm);
+    tmem_wait_st();
+    tc_fence_before();
+}
+
+// Backward epilogue: dh (accumulator columns 0..49) masked by the ReLU pattern
+// kept at `mcol`, split into BF16 hi + lo (no ReLU: cotangents have either
+// sign) and written as the next A row (hi 0..24, 25..27 = 0, lo 28..52).
+__device__ __forceinline__ void tile_backward_hidden(const Tile& T, uint32_t mcol) {
+    tc_fence_after();
+    uint32_t v[32], v2[16], u[8], mk[16], mk2[16];
+    tmem_ld32(T.taddr, v);
+    tmem_ld16(T.taddr + 32, v2);
+    tmem_ld8(T.taddr + 48, u);
+    tmem_ld16(T.taddr + mcol, mk);
+    tmem_ld16(T.taddr + mcol + 16, mk2);
+    tmem_wait_ld();
+    const uint32_t at = T.taddr + 64;
+    uint32_t hw[16], lw[16];
+#pragma unroll
+    for (int i2 = 0; i2 < 16; ++i2)
+        split_rn((mk[i2] & 0x0000FFFFu) ? v[2 * i2] : 0u, (mk[i2] & 0xFFFF0000u) ? v[2 * i2 + 1] : 0u, hw[i2],
+                 lw[i2]);
+    tmem_st16(at, hw);
+    uint32_t h9[9], l9[9];
+#pragma unroll
+    for (int i2 = 0; i2 < 9; ++i2) {
+        const uint32_t ra = (i2 < 8) ? v2[2 * i2] : u[0];
+        const uint32_t rb = (i2 < 8) ? v2[2 * i2 + 1] : u[1];
+        split_rn((mk2[i2] & 0x0000FFFFu) ? ra : 0u, (mk2[i2] & 0xFFFF0000u) ? rb : 0u, h9[i2], l9[i2]);
+    }
+    const uint32_t gb[16] = {h9[0], h9[1], h9[2], h9[3], h9[4], h9[5], h9[6], h9[7],
+                             h9[8], 0u, 0u, 0u, lw[0], lw[1], lw[2], lw[3]};
+    const uint32_t gc[16] = {lw[4], lw[5], lw[6], lw[7], lw[8], lw[9], lw[10], lw[11],
+                             lw[12], lw[13], lw[14], lw[15], l9[0], l9[1], l9[2], l9[3]};
+    const uint32_t gd[8] = {l9[4], l9[5], l9[6], l9[7], l9[8], 0u, 0u, 0u};
+    tmem_st16(at + 16, gb);
+    tmem_st16(at + 32, gc);
+    tmem_st8(at + 48, gd);
+    tmem_wait_st();
+    tc_fence_before();
+}
+
+// Cotangent of the collocation points, c_j = lambda * ell_j(X), as the A row
+// of W5^T: words 0..3 = hi pairs (c_0, c_1) .. (c_6, c_7), words 4..7 = lo pairs.
+__device__ __forceinline__ void tile_cotangent(const Tile& T, float lam) {
+    uint32_t w[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        split_rn(__float_as_uint(lam * T.lb[2 * q]), __float_as_uint(lam * T.lb[2 * q + 1]), w[q], w[4 + q]);
+    }
+    tmem_st8(T.taddr + 64, w);
+    tmem_wait_st();
+    tc_fence_before();
+}
+
+// Normal of step i and the Lagrange basis at it, for any order of steps: the
+// block of four normals is redrawn whenever step i falls in another block.
+__device__ __forceinline__ void tile_rng_any(Tile& T, const SimArgs& a, int i, int& blk) {
+    if ((i >> 2) != blk) {
+        blk = i >> 2;
+        T.z4 = normal4(a.seed, 0u, static_cast<uint32_t>(T.s), T.q, static_cast<uint32_t>(blk));
+    }
+    lagrange_basis_m(pick4(T.z4, i & 3), a.gh, a.m, T.lb);
+}
+
+// OR of `v` over the 128 threads of named barrier `id` (also a barrier).
+__device__ __forceinline__ bool bar_or(int id, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, %2, 128, p;\nselp.u32 %0, 1, 0, q;\n}"
+        : "=r"(r)
+        : "r"(static_cast<uint32_t>(v)), "r"(id)
+        : "memory");
+    return r != 0;
+}
+
+template <int WG>
+__global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_kernel(const AdjTC A) {
+    constexpr int S = WG;
+    constexpr uint32_t kCols = (S * 256 <= 256) ? 256 : 512;
+    static_assert(S * 256 <= 512, "tensor memory holds 512 columns");
+    const SimArgs& a = A.s;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    unsigned char* sB = smem;
+    unsigned char* sBT = smem + kBBytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sBT + kBTBytes);   // d_ready[S], drain
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + S + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wg = warp >> 2, wq = warp & 3;
+    const int r = wq * 32 + lane;
+    const bool issuer = (wq == 0);
+
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < S; ++q) mbar_init(smem_u32(&bars[q]), 1);
+        mbar_init(smem_u32(&bars[S]), WG);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    stage_weights(sB, a.params, a.d_in, a.m);
+    stage_weights_T(sBT, a.params, a.d_in, a.m);
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    IssueConst C;
+    const uint32_t sB_u = smem_u32(sB);
+    C.db0 = sw128_desc(sB_u);
+    C.db1 = sw128_desc(sB_u + kB1Bytes);
+    C.db2 = sw128_desc(sB_u + kB1Bytes + kBHBytes);
+    C.db3 = sw128_desc(sB_u + kB1Bytes + 2 * kBHBytes);
+    C.db4 = sw128_desc(sB_u + kB1Bytes + 3 * kBHBytes);
+    IssueConstT CT;
+    const uint32_t sBT_u = smem_u32(sBT);
+    CT.db5 = sw128_desc(sBT_u);
+    CT.db4 = sw128_desc(sBT_u + kB5TBytes);
+    CT.db3 = sw128_desc(sBT_u + kB5TBytes + kBHTBytes);
+    CT.db2 = sw128_desc(sBT_u + kB5TBytes + 2 * kBHTBytes);
+    CT.db1 = sw128_desc(sBT_u + kB5TBytes + 3 * kBHTBytes);
+
+    Tile T;
+    T.d_tmem = tmem_base + static_cast<uint32_t>(wg * 256);
+    T.taddr = T.d_tmem + (static_cast<uint32_t>(wq * 32) << 16);
+    T.d_bar = smem_u32(&bars[wg]);
+    T.bar_id = 1 + wg;
+    T.dph = 0;
+    const uint32_t kMask0 = 128;   // mask of hidden layer l at 128 + 32 (l - 1)
+
+    const int64_t n_tiles = (a.total + kTile - 1) / kTile;
+    const int64_t tile_stride = static_cast<int64_t>(gridDim.x) * S;
+    const int p = a.p;
+    bool ok = true;
+    for (int64_t tile = static_cast<int64_t>(blockIdx.x) * S + wg; tile < n_tiles; tile += tile_stride) {
+        tile_begin(T, a, tile, r);
+        int blk = -1;
+        // ---- 1. forward sweep with checkpoints
+        for (int i = 0; i < a.n_steps; ++i) {
+            if (i % A.k == 0 && T.valid) A.ckpt[static_cast<int64_t>(i / A.k) * a.total + T.g] = T.Y;
+            if (ok) tile_features(T, a);
+            ok = tile_sync_issue(T, C, 0, ok, issuer);
+            if (!ok) break;
+            tile_rng_any(T, a, i, blk);
+#pragma unroll
+            for (int l = 1; l <= 4; ++l) {
+                const bool w = tile_wait(T, abort_flag, a.status);
+                if (w) tile_hidden(T);
+                ok = tile_sync_issue(T, C, l, w, issuer);
+                if (!ok) break;
+            }
+            if (!ok) break;
+            const bool w = tile_wait(T, abort_flag, a.status);
+            if (w) tile_out(T, a, i);
+            ok = bar_and(T.bar_id, w);
+            if (!ok) break;
+        }
+        if (!ok) break;
+        const float payoff = fmaxf(T.Y - A.K, 0.0f);
+        float lam = (T.valid && T.Y > A.K) ? 1.0f : 0.0f;
+        float gth[SL_MAX_DIN_TC - 2];
+#pragma unroll
+        for (int q = 0; q < SL_MAX_DIN_TC - 2; ++q) gth[q] = 0.0f;
+        // ---- 2-3. reverse sweep (skipped when every path of the tile is out of the money)
+        if (bar_or(T.bar_id, lam != 0.0f)) {
+            for (int c = A.n_ckpt - 1; ok && c >= 0; --c) {
+                const int i0 = c * A.k;
+                const int i1 = min(i0 + A.k, a.n_steps);
+                float Ys[kMaxCkptK];
+                Ys[0] = T.valid ? A.ckpt[static_cast<int64_t>(c) * a.total + T.g] : 0.0f;
+                // recompute Y_{i0+1} .. Y_{i1-1}
+                for (int i = i0; i < i1 - 1; ++i) {
+                    T.Y = Ys[i - i0];
+                    if (ok) tile_features(T, a);
+                    ok = tile_sync_issue(T, C, 0, ok, issuer);
+                    if (!ok) break;
+                    tile_rng_any(T, a, i, blk);
+#pragma unroll
+                    for (int l = 1; l <= 4; ++l) {
+                        const bool w = tile_wait(T, abort_flag, a.status);
+                        if (w) tile_hidden(T);
+                        ok = tile_sync_issue(T, C, l, w, issuer);
+                        if (!ok) break;
+                    }
+                    if (!ok) break;
+                    const bool w = tile_wait(T, abort_flag, a.status);
+                    if (w) tile_out(T, a, i);
+                    ok = bar_and(T.bar_id, w);
+                    if (!ok) break;
+                    Ys[i - i0 + 1] = T.Y;
+                }
+                for (int i = i1 - 1; ok && i >= i0; --i) {
+                    // a. mask pass: layers 1-4 at Y_i
+                    T.Y = Ys[i - i0];
+                    tile_features(T, a);
+                    ok = tile_sync_issue(T, C, 0, ok, issuer);
+                    if (!ok) break;
+                    tile_rng_any(T, a, i, blk);   // ell_j at this step's normal
+#pragma unroll
+                    for (int l = 1; l <= 4; ++l) {
+                        const bool w = tile_wait(T, abort_flag, a.status);
+                        if (w) tile_hidden_keep_mask(T, kMask0 + 32 * (l - 1));
+                        if (l < 4) {
+                            ok = tile_sync_issue(T, C, l, w, issuer);
+                        } else {
+                            ok = bar_and(T.bar_id, w);
+                        }
+                        if (!ok) break;
+                    }
+                    if (!ok) break;
+                    // b. backward chain
+                    tile_cotangent(T, lam);
+                    ok = tile_sync_issue_T(T, CT, 0, ok, issuer);
+                    if (!ok) break;
+#pragma unroll
+                    for (int lt = 1; lt <= 4; ++lt) {   // dh4 -> W4^T, dh3 -> W3^T, dh2 -> W2^T, dh1 -> W1^T
+                        const bool w = tile_wait(T, abort_flag, a.status);
+                        if (w) tile_backward_hidden(T, kMask0 + 32 * (4 - lt));
+                        ok = tile_sync_issue_T(T, CT, lt, w, issuer);
+                        if (!ok) break;
+                    }
+                    if (!ok) break;
+                    // c. d/d(features): lambda <- d/dY_i, g_theta += d/dtheta
+                    bool w = tile_wait(T, abort_flag, a.status);
+                    if (w) {
+                        tc_fence_after();
+                        uint32_t gf[8];
+                        tmem_ld8(T.taddr, gf);
+                        tmem_wait_ld();
+                        tc_fence_before();
+                        lam = __uint_as_float(gf[0]);
+#pragma unroll
+                        for (int q = 0; q < SL_MAX_DIN_TC - 2; ++q)
+                            if (q < p) gth[q] += __uint_as_float(gf[2 + q]);
+                    }
+                    ok = bar_and(T.bar_id, w);
+                }
+            }
+        }
+        if (!ok) break;
+        // ---- 4. per-path outputs (out-of-the-money paths: lambda = 0, g_theta = 0)
+        if (T.valid) {
+            A.pv[T.g] = payoff;
+            A.pv[a.total + T.g] = lam;
+            for (int q = 0; q < p; ++q) A.pv[static_cast<int64_t>(2 + q) * a.total + T.g] = gth[q];
+            if (!isfinite(lam) || !isfinite(payoff)) raise_status(a.status, SL_DEV_NONFINITE);
+        }
+    }
+    if (issuer) mma_commit_w(smem_u32(&bars[S]));
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) {
+        if (lane == 0) {
+            const uint64_t t0 = global_ns();
+            while (!mbar_try_wait(smem_u32(&bars[S]), 0)) {
+                if (global_ns() - t0 > kTimeoutNs) {
+                    raise_status(a.status, SL_DEV_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kCols)
+                     : "memory");
+    }
+}
+
+template <int WG>
+int launch_adj_tc(const AdjTC& A, cudaStream_t st) {
+    auto kern = tc_adjoint_kernel<WG>;
+    const size_t smem = 1024 + kBBytes + kBTBytes + (WG + 1) * 8 + 16;
+    int rc = cuda_error(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem)),
+                        "tc_adjoint attribute");
+    if (rc) return rc;
+    const int64_t n_tiles = (A.s.total + kTile - 1) / kTile;
+    int64_t grid = sm_count();
+    const int64_t need = (n_tiles + WG - 1) / WG;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    kern<<<static_cast<unsigned>(grid), 128 * WG, smem, st>>>(A);
+    return cuda_error(cudaGetLastError(), "tc_adjoint launch");
+}
+
+}  // namespace
+
+// Tensor-core adjoint: requires an MLP model with ReLU, d_in <= 7, m <= 8.
+int launch_tc_adjoint(const SimArgs& s, float K, int k, int n_ckpt, float* ckpt, float* pv, cudaStream_t st) {
+    if (s.d_in > SL_MAX_DIN_TC) return set_error(SL_ERR_UNSUPPORTED, "d_in=%d > %d", s.d_in, SL_MAX_DIN_TC);
+    if (k > kMaxCkptK) return set_error(SL_ERR_UNSUPPORTED, "ckpt_k=%d > %d", k, kMaxCkptK);
+    AdjTC A{};
+    A.s = s;
+    A.K = K;
+    A.k = k;
+    A.n_ckpt = n_ckpt;
+    A.ckpt = ckpt;
+    A.pv = pv;
+    return launch_adj_tc<2>(A, st);
+}
+
+}  // namespace sl
