@@ -16,8 +16,10 @@ scaling, no data-path collective.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -32,6 +34,33 @@ METRIC = "path-steps/s (7L online, BF16-TC vs FP32) at <=2e-3 rel err; EM label 
 UNIT = "path-steps/s"
 WORKLOAD = "GBM 7L online: 16 theta x 1e6 paths x 16 coarse steps, m=7, MLP 4->50x4->7 ReLU"
 ALG_FLOPS_PER_PATH_STEP = 2 * (4 * 50 + 3 * 50 * 50 + 50 * 7)   # 16,100 (biases excluded)
+
+# DRAM traffic of the sampler kernel on the default workload, from the committed ncu summary;
+# used only while the kernel's sources are those the counters were taken on.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "tc_7l_kernel_gbm_online.md")
+KERNEL_SOURCES = ("sl_tc.cu", "sl_tc_common.cuh", "sl_internal.cuh")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2302_05170_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """Bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum), or None when the summary
+    is missing or was taken on other kernel sources."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            text = fh.read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch: (\d+); kernel_source_sha256: ([0-9a-f]+)", text)
+    if not m or m.group(2) != kernel_source_hash():
+        return None
+    return int(m.group(1))
 
 
 def _peaks():
@@ -304,8 +333,9 @@ def main():
     if prec == sl.PREC_BF16:
         achieved = ALG_FLOPS_PER_PATH_STEP * path_steps / (k_ms * 1e-3) / 1e12
         peak = peaks["bf16_tflops_sustained"]
+        default_workload = (args.paths, n_steps, m) == (10 ** 6, 16, 7)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": recorded_traffic() if default_workload else None,
                 "peak_kind": "bf16 sustained, " + peak_src}
     else:
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -421,6 +451,27 @@ def main():
             secondary[key + "_result"] = ("value %.5f dY0 %.5f dtheta %s"
                                           % (v_a.item(), d0_a.item(), [round(x, 5) for x in dth_a[0].tolist()]))
         secondary["adjoint_workload"] = "GBM network, 1e6 paths x 64 steps, checkpoint every 8, call K=1"
+        # CIR adjoint on the trained CIR network (BF16 tcgen05 form): kappa=1, ybar=0.1, gamma=0.3,
+        # Y0=0.1, 1e6 paths x 64 steps of dt=0.25 (inside the label rows' dt range), checkpoint every 8;
+        # call K=1 lies far above the CIR range (every sensitivity is 0), K=ybar is the meaningful case
+        th_ca = torch.tensor([[1.0, 0.1, 0.3]], device=dev)
+        y0_ca = torch.tensor([0.1], device=dev)
+        ws_ca = torch.empty(sl.adjoint_workspace_size(n_a, 1, 64, 8, 3), dtype=torch.uint8, device=dev)
+        for Kc, key in ((1.0, "cir_adjoint_K1"), (0.1, "cir_adjoint_Kybar")):
+            run_ca = lambda: sl.seven_league_adjoint(sl.MODEL_MLP, net_c, th_ca, y0_ca, off_a, 16.0, 64, 7, 1, Kc,
+                                                     ckpt_k=8, ws=ws_ca, total_paths=n_a)
+            run_ca()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            v_c, d0_c, dth_c = run_ca()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            assert sl.workspace_status(ws_ca) == 0
+            secondary[key + "_path_steps_per_s"] = n_a * 64 / (e0.elapsed_time(e1) * 1e-3)
+            secondary[key + "_result"] = ("value %.6f dY0 %.5f dtheta %s"
+                                          % (v_c.item(), d0_c.item(), [round(x, 5) for x in dth_c[0].tolist()]))
+        secondary["cir_adjoint_workload"] = ("CIR network (BF16 tcgen05), kappa=1 ybar=0.1 gamma=0.3 Y0=0.1, "
+                                             "1e6 paths x 64 steps of dt=0.25, checkpoint every 8")
 
     # --- end to end through the C ABI with host buffers (pinned), copies timed
     h_theta = torch.as_tensor(w["theta"]).pin_memory()
