@@ -342,7 +342,8 @@ int model_p(int model) { return model == SL_MODEL_GBM_EXACT ? 2 : 3; }
 
 }  // namespace
 
-int launch_tc_adjoint(const SimArgs& s, float K, int k, int n_ckpt, float* ckpt, float* pv, cudaStream_t st);
+int launch_tc_adjoint(const SimArgs& s, float K, int k, int n_ckpt, float* ckpt, float* pv, float* yt,
+                      uint32_t* list, unsigned* count, cudaStream_t st);
 
 }  // namespace sl
 
@@ -356,8 +357,11 @@ size_t sl_adjoint_workspace_size(int64_t total_paths, int n_sets, int n_steps, i
     if (n_steps < 1) n_steps = 1;
     if (p < 0) p = 0;
     const int64_t n_ckpt = (n_steps + ckpt_k - 1) / ckpt_k;
-    return kStatusBytes + align256(static_cast<size_t>(n_ckpt * total_paths) * 4) +
+    // checkpoints (one spare row: the BF16 form's forward sweep also writes Y_T when k divides
+    // n_steps), per-path values, and for the BF16 form Y_T, the in-the-money list and its length
+    return kStatusBytes + align256(static_cast<size_t>((n_ckpt + 1) * total_paths) * 4) +
            align256(static_cast<size_t>((2 + p) * total_paths) * 4) +
+           2 * align256(static_cast<size_t>(total_paths) * 4) + 256 +
            set_moments_scratch_bytes(n_sets < 1 ? 1 : n_sets);
 }
 
@@ -421,16 +425,23 @@ int seven_league_adjoint(int model, const sl_net* net, const float* theta, int p
     A.n_ckpt = n_ckpt;
     size_t off = kStatusBytes;
     A.ckpt = reinterpret_cast<float*>(w + off);
-    off += align256(static_cast<size_t>(n_ckpt) * total_paths * 4);
+    off += align256(static_cast<size_t>(n_ckpt + 1) * total_paths * 4);
     A.pv = out_paths ? out_paths : reinterpret_cast<float*>(w + off);
     off += align256(static_cast<size_t>(2 + p) * total_paths * 4);
+    float* yt = reinterpret_cast<float*>(w + off);
+    off += align256(static_cast<size_t>(total_paths) * 4);
+    uint32_t* list = reinterpret_cast<uint32_t*>(w + off);
+    off += align256(static_cast<size_t>(total_paths) * 4);
+    unsigned* count = reinterpret_cast<unsigned*>(w + off);
+    off += 256;
     void* part = w + off;
     rc = cuda_error(cudaMemsetAsync(a.status, 0, kStatusBytes, st), "status clear");
     if (rc) return rc;
     if (total_paths > 0) {
         if (model == SL_MODEL_GBM_EXACT) rc = launch_adj<SL_MODEL_GBM_EXACT, 0>(A, st);
         else if (model == SL_MODEL_OU_EXACT) rc = launch_adj<SL_MODEL_OU_EXACT, 0>(A, st);
-        else if (net->prec == SL_PREC_BF16) rc = launch_tc_adjoint(a, K, ckpt_k, n_ckpt, A.ckpt, A.pv, st);
+        else if (net->prec == SL_PREC_BF16)
+            rc = launch_tc_adjoint(a, K, ckpt_k, n_ckpt, A.ckpt, A.pv, yt, list, count, st);
         else if (net->act == SL_ACT_SOFTPLUS) rc = launch_adj<SL_MODEL_MLP, SL_ACT_SOFTPLUS>(A, st);
         else rc = launch_adj<SL_MODEL_MLP, SL_ACT_RELU>(A, st);
         if (rc) return rc;

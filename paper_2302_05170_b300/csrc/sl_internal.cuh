@@ -177,6 +177,7 @@ struct SimArgs {
     uint64_t seed;
     float* out_YT;            // [total] or NULL
     float* out_grid;          // [(n_steps+1)][total] or NULL
+    int grid_k;               // >1: out_grid keeps only rows Y_0, Y_k, Y_2k, .. (row i/k), BF16 form only
     unsigned* status;         // device status word or NULL
     int m;                    // collocation points
     GHConst gh;

@@ -2,12 +2,15 @@
 // sensitivities of E[max(Y_T - K, 0)] with respect to Y0 and theta through
 // g_m and the network, with Y_i checkpointed every k steps.
 //
-// Per path tile (128 paths, one warpgroup, warp 0 issues the MMAs):
-//  1. forward sweep of the 7L sampler (same MMA chain and epilogues as the
-//     sampling kernel), writing Y_{ck} to the checkpoint buffer;
-//  2. lambda = 1{Y_T > K}; a tile whose paths are all out of the money stops;
-//  3. per segment (last first): recompute Y_{ck} .. Y_{ck+k-1} from the
-//     checkpoint; then per step i, from the segment's last to its first:
+// Three launches:
+//  1. forward: the BF16 sampler itself, with its path grid thinned to the
+//     checkpoint rows Y_0, Y_k, Y_2k, .. (the same paths as seven_league_simulate);
+//  2. itm_compact_kernel: f(Y_T) for every path, zero sensitivities for the
+//     out-of-the-money paths (Y_T <= K), and the list of in-the-money paths;
+//  3. tc_adjoint_reverse_kernel over that list only, 128 listed paths per tile
+//     (one warpgroup, warp 0 issues the MMAs), lambda = 1 at Y_T; per segment
+//     (last first): recompute Y_ck .. Y_ck+k-1 from the checkpoint; then per
+//     step i, from the segment's last to its first:
 //     a. mask pass: layers 1-4 at Y_i; the ReLU pattern of every hidden layer
 //        is kept in tensor memory (the packed BF16 "hi" words of the layer's
 //        output: non-zero exactly where the pre-activation is positive);
@@ -18,8 +21,7 @@
 //        tiles; the cotangents are split into BF16 hi + lo like the forward
 //        activations (A operand in tensor memory);
 //     c. lambda <- d/dY_i, g_theta += d/dtheta.
-//  4. per-path outputs (payoff, lambda, g_theta); per-set FP64 means by the
-//     shared deterministic reduction.
+//  Per-set FP64 means come from the shared deterministic reduction.
 //
 // Tensor memory per tile: 256 columns -- accumulator 0..63, A operand
 // 64..119, masks of hidden layers 1..4 at 128 + 32 (l-1) (25 words each).
@@ -39,10 +41,12 @@ constexpr int kBTBytes = kB5TBytes + 3 * kBHTBytes + kB1TBytes;
 struct AdjTC {
     SimArgs s;
     float K;
-    int k;          // checkpoint interval
-    int n_ckpt;
-    float* ckpt;    // [n_ckpt][total]
-    float* pv;      // [(2+p)][total]
+    int k;                  // checkpoint interval
+    int n_ckpt;             // checkpoints Y_0, Y_k, .., Y_(n_ckpt-1)k
+    const float* ckpt;      // [n_ckpt (+1)][total]
+    float* pv;              // [(2+p)][total]
+    const uint32_t* list;   // in-the-money paths
+    const unsigned* count;  // their number
 };
 
 // Transposed weights for the backward chain (BF16, 128B-swizzled, K-major):
@@ -205,19 +209,48 @@ __device__ __forceinline__ void tile_rng_any(Tile& T, const SimArgs& a, int i, i
     lagrange_basis_m(pick4(T.z4, i & 3), a.gh, a.m, T.lb);
 }
 
-// OR of `v` over the 128 threads of named barrier `id` (also a barrier).
-__device__ __forceinline__ bool bar_or(int id, bool v) {
-    uint32_t r;
-    asm volatile(
-        "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, %2, 128, p;\nselp.u32 %0, 1, 0, q;\n}"
-        : "=r"(r)
-        : "r"(static_cast<uint32_t>(v)), "r"(id)
-        : "memory");
-    return r != 0;
+// f(Y_T) for every path; zero sensitivities for the out-of-the-money paths;
+// the in-the-money paths (Y_T > K, where f'(Y_T) = 1) appended to `list`
+// (warp-aggregated; the order does not matter: every path's result depends on
+// its own row only).
+__global__ void itm_compact_kernel(const float* __restrict__ yt, int64_t total, float K, int p,
+                                   float* __restrict__ pv, uint32_t* __restrict__ list, unsigned* count) {
+    const int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    bool itm = false;
+    if (g < total) {
+        const float y = yt[g];
+        pv[g] = fmaxf(y - K, 0.0f);
+        itm = y > K;
+        if (!itm)
+            for (int q = 0; q < 1 + p; ++q) pv[static_cast<int64_t>(1 + q) * total + g] = 0.0f;
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, itm);
+    if (mask) {
+        const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+        unsigned base = 0;
+        if (lane == leader) base = atomicAdd(count, static_cast<unsigned>(__popc(mask)));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (itm) list[base + __popc(mask & ((1u << lane) - 1u))] = static_cast<uint32_t>(g);
+    }
+}
+
+// Row r of a reverse tile: listed path `g` (or an idle row past the end of the list).
+__device__ __forceinline__ void tile_begin_listed(Tile& T, const SimArgs& a, int64_t g, bool valid) {
+    T.g = g;
+    T.valid = valid;
+    T.s = owning_set(a.offsets, a.n_sets, g);
+    T.q = static_cast<uint32_t>(g - __ldg(a.offsets + T.s));
+    const float* th = a.theta + static_cast<int64_t>(T.s) * a.p;
+    T.feat[0] = 0.0f;
+    T.feat[1] = a.dt;
+#pragma unroll
+    for (int k = 0; k < SL_MAX_DIN_TC - 2; ++k) T.feat[2 + k] = (k < a.p) ? __ldg(th + k) : 0.0f;
+    T.Y = 0.0f;
+    T.z4 = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 template <int WG>
-__global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_kernel(const AdjTC A) {
+__global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const AdjTC A) {
     constexpr int S = WG;
     constexpr uint32_t kCols = (S * 256 <= 256) ? 256 : 512;
     static_assert(S * 256 <= 512, "tensor memory holds 512 columns");
@@ -280,122 +313,99 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_kernel(const AdjTC A) 
     T.dph = 0;
     const uint32_t kMask0 = 128;   // mask of hidden layer l at 128 + 32 (l - 1)
 
-    const int64_t n_tiles = (a.total + kTile - 1) / kTile;
+    const int64_t n_list = static_cast<int64_t>(*A.count);
+    const int64_t n_tiles = (n_list + kTile - 1) / kTile;
     const int64_t tile_stride = static_cast<int64_t>(gridDim.x) * S;
     const int p = a.p;
     bool ok = true;
     for (int64_t tile = static_cast<int64_t>(blockIdx.x) * S + wg; tile < n_tiles; tile += tile_stride) {
-        tile_begin(T, a, tile, r);
+        const int64_t li = tile * kTile + r;
+        const bool valid = li < n_list;
+        const int64_t g = A.list[valid ? li : n_list - 1];
+        tile_begin_listed(T, a, g, valid);
         int blk = -1;
-        // ---- 1. forward sweep with checkpoints
-        for (int i = 0; i < a.n_steps; ++i) {
-            if (i % A.k == 0 && T.valid) A.ckpt[static_cast<int64_t>(i / A.k) * a.total + T.g] = T.Y;
-            if (ok) tile_features(T, a);
-            ok = tile_sync_issue(T, C, 0, ok, issuer);
-            if (!ok) break;
-            tile_rng_any(T, a, i, blk);
-#pragma unroll
-            for (int l = 1; l <= 4; ++l) {
-                const bool w = tile_wait(T, abort_flag, a.status);
-                if (w) tile_hidden(T);
-                ok = tile_sync_issue(T, C, l, w, issuer);
-                if (!ok) break;
-            }
-            if (!ok) break;
-            const bool w = tile_wait(T, abort_flag, a.status);
-            if (w) tile_out(T, a, i);
-            ok = bar_and(T.bar_id, w);
-            if (!ok) break;
-        }
-        if (!ok) break;
-        const float payoff = fmaxf(T.Y - A.K, 0.0f);
-        float lam = (T.valid && T.Y > A.K) ? 1.0f : 0.0f;
+        float lam = valid ? 1.0f : 0.0f;
         float gth[SL_MAX_DIN_TC - 2];
 #pragma unroll
         for (int q = 0; q < SL_MAX_DIN_TC - 2; ++q) gth[q] = 0.0f;
-        // ---- 2-3. reverse sweep (skipped when every path of the tile is out of the money)
-        if (bar_or(T.bar_id, lam != 0.0f)) {
-            for (int c = A.n_ckpt - 1; ok && c >= 0; --c) {
-                const int i0 = c * A.k;
-                const int i1 = min(i0 + A.k, a.n_steps);
-                float Ys[kMaxCkptK];
-                Ys[0] = T.valid ? A.ckpt[static_cast<int64_t>(c) * a.total + T.g] : 0.0f;
-                // recompute Y_{i0+1} .. Y_{i1-1}
-                for (int i = i0; i < i1 - 1; ++i) {
-                    T.Y = Ys[i - i0];
-                    if (ok) tile_features(T, a);
-                    ok = tile_sync_issue(T, C, 0, ok, issuer);
-                    if (!ok) break;
-                    tile_rng_any(T, a, i, blk);
+        for (int c = A.n_ckpt - 1; ok && c >= 0; --c) {
+            const int i0 = c * A.k;
+            const int i1 = min(i0 + A.k, a.n_steps);
+            float Ys[kMaxCkptK];
+            Ys[0] = A.ckpt[static_cast<int64_t>(c) * a.total + g];
+            // recompute Y_{i0+1} .. Y_{i1-1}
+            for (int i = i0; i < i1 - 1; ++i) {
+                T.Y = Ys[i - i0];
+                tile_features(T, a);
+                ok = tile_sync_issue(T, C, 0, ok, issuer);
+                if (!ok) break;
+                tile_rng_any(T, a, i, blk);
 #pragma unroll
-                    for (int l = 1; l <= 4; ++l) {
-                        const bool w = tile_wait(T, abort_flag, a.status);
-                        if (w) tile_hidden(T);
-                        ok = tile_sync_issue(T, C, l, w, issuer);
-                        if (!ok) break;
-                    }
-                    if (!ok) break;
+                for (int l = 1; l <= 4; ++l) {
                     const bool w = tile_wait(T, abort_flag, a.status);
-                    if (w) tile_out(T, a, i);
-                    ok = bar_and(T.bar_id, w);
+                    if (w) tile_hidden(T);
+                    ok = tile_sync_issue(T, C, l, w, issuer);
                     if (!ok) break;
-                    Ys[i - i0 + 1] = T.Y;
                 }
-                for (int i = i1 - 1; ok && i >= i0; --i) {
-                    // a. mask pass: layers 1-4 at Y_i
-                    T.Y = Ys[i - i0];
-                    tile_features(T, a);
-                    ok = tile_sync_issue(T, C, 0, ok, issuer);
-                    if (!ok) break;
-                    tile_rng_any(T, a, i, blk);   // ell_j at this step's normal
+                if (!ok) break;
+                const bool w = tile_wait(T, abort_flag, a.status);
+                if (w) tile_out(T, a, i);
+                ok = bar_and(T.bar_id, w);
+                if (!ok) break;
+                Ys[i - i0 + 1] = T.Y;
+            }
+            for (int i = i1 - 1; ok && i >= i0; --i) {
+                // a. mask pass: layers 1-4 at Y_i
+                T.Y = Ys[i - i0];
+                tile_features(T, a);
+                ok = tile_sync_issue(T, C, 0, ok, issuer);
+                if (!ok) break;
+                tile_rng_any(T, a, i, blk);   // ell_j at this step's normal
 #pragma unroll
-                    for (int l = 1; l <= 4; ++l) {
-                        const bool w = tile_wait(T, abort_flag, a.status);
-                        if (w) tile_hidden_keep_mask(T, kMask0 + 32 * (l - 1));
-                        if (l < 4) {
-                            ok = tile_sync_issue(T, C, l, w, issuer);
-                        } else {
-                            ok = bar_and(T.bar_id, w);
-                        }
-                        if (!ok) break;
+                for (int l = 1; l <= 4; ++l) {
+                    const bool w = tile_wait(T, abort_flag, a.status);
+                    if (w) tile_hidden_keep_mask(T, kMask0 + 32 * (l - 1));
+                    if (l < 4) {
+                        ok = tile_sync_issue(T, C, l, w, issuer);
+                    } else {
+                        ok = bar_and(T.bar_id, w);
                     }
                     if (!ok) break;
-                    // b. backward chain
-                    tile_cotangent(T, lam);
-                    ok = tile_sync_issue_T(T, CT, 0, ok, issuer);
-                    if (!ok) break;
-#pragma unroll
-                    for (int lt = 1; lt <= 4; ++lt) {   // dh4 -> W4^T, dh3 -> W3^T, dh2 -> W2^T, dh1 -> W1^T
-                        const bool w = tile_wait(T, abort_flag, a.status);
-                        if (w) tile_backward_hidden(T, kMask0 + 32 * (4 - lt));
-                        ok = tile_sync_issue_T(T, CT, lt, w, issuer);
-                        if (!ok) break;
-                    }
-                    if (!ok) break;
-                    // c. d/d(features): lambda <- d/dY_i, g_theta += d/dtheta
-                    bool w = tile_wait(T, abort_flag, a.status);
-                    if (w) {
-                        tc_fence_after();
-                        uint32_t gf[8];
-                        tmem_ld8(T.taddr, gf);
-                        tmem_wait_ld();
-                        tc_fence_before();
-                        lam = __uint_as_float(gf[0]);
-#pragma unroll
-                        for (int q = 0; q < SL_MAX_DIN_TC - 2; ++q)
-                            if (q < p) gth[q] += __uint_as_float(gf[2 + q]);
-                    }
-                    ok = bar_and(T.bar_id, w);
                 }
+                if (!ok) break;
+                // b. backward chain
+                tile_cotangent(T, lam);
+                ok = tile_sync_issue_T(T, CT, 0, ok, issuer);
+                if (!ok) break;
+#pragma unroll
+                for (int lt = 1; lt <= 4; ++lt) {   // dh4 -> W4^T, dh3 -> W3^T, dh2 -> W2^T, dh1 -> W1^T
+                    const bool w = tile_wait(T, abort_flag, a.status);
+                    if (w) tile_backward_hidden(T, kMask0 + 32 * (4 - lt));
+                    ok = tile_sync_issue_T(T, CT, lt, w, issuer);
+                    if (!ok) break;
+                }
+                if (!ok) break;
+                // c. d/d(features): lambda <- d/dY_i, g_theta += d/dtheta
+                const bool w = tile_wait(T, abort_flag, a.status);
+                if (w) {
+                    tc_fence_after();
+                    uint32_t gf[8];
+                    tmem_ld8(T.taddr, gf);
+                    tmem_wait_ld();
+                    tc_fence_before();
+                    lam = __uint_as_float(gf[0]);
+#pragma unroll
+                    for (int q = 0; q < SL_MAX_DIN_TC - 2; ++q)
+                        if (q < p) gth[q] += __uint_as_float(gf[2 + q]);
+                }
+                ok = bar_and(T.bar_id, w);
             }
         }
         if (!ok) break;
-        // ---- 4. per-path outputs (out-of-the-money paths: lambda = 0, g_theta = 0)
-        if (T.valid) {
-            A.pv[T.g] = payoff;
-            A.pv[a.total + T.g] = lam;
-            for (int q = 0; q < p; ++q) A.pv[static_cast<int64_t>(2 + q) * a.total + T.g] = gth[q];
-            if (!isfinite(lam) || !isfinite(payoff)) raise_status(a.status, SL_DEV_NONFINITE);
+        if (valid) {
+            A.pv[a.total + g] = lam;
+            for (int q = 0; q < p; ++q) A.pv[static_cast<int64_t>(2 + q) * a.total + g] = gth[q];
+            if (!isfinite(lam)) raise_status(a.status, SL_DEV_NONFINITE);
         }
     }
     if (issuer) mma_commit_w(smem_u32(&bars[S]));
@@ -419,16 +429,18 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_kernel(const AdjTC A) 
 }
 
 template <int WG>
-int launch_adj_tc(const AdjTC& A, cudaStream_t st) {
-    auto kern = tc_adjoint_kernel<WG>;
+int launch_reverse(const AdjTC& A, cudaStream_t st) {
+    auto kern = tc_adjoint_reverse_kernel<WG>;
     const size_t smem = 1024 + kBBytes + kBTBytes + (WG + 1) * 8 + 16;
     int rc = cuda_error(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(smem)),
                         "tc_adjoint attribute");
     if (rc) return rc;
-    const int64_t n_tiles = (A.s.total + kTile - 1) / kTile;
+    // The list's length is known on the device only: one persistent CTA per SM
+    // (at most as many as the paths could fill); CTAs without a tile exit.
+    const int64_t max_tiles = (A.s.total + kTile - 1) / kTile;
     int64_t grid = sm_count();
-    const int64_t need = (n_tiles + WG - 1) / WG;
+    const int64_t need = (max_tiles + WG - 1) / WG;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     kern<<<static_cast<unsigned>(grid), 128 * WG, smem, st>>>(A);
@@ -438,17 +450,40 @@ int launch_adj_tc(const AdjTC& A, cudaStream_t st) {
 }  // namespace
 
 // Tensor-core adjoint: requires an MLP model with ReLU, d_in <= 7, m <= 8.
-int launch_tc_adjoint(const SimArgs& s, float K, int k, int n_ckpt, float* ckpt, float* pv, cudaStream_t st) {
+// ckpt: [n_ckpt + 1][total] (the sampler writes rows 0 .. n_steps / k); yt:
+// [total]; list: [total]; count: one word.
+int launch_tc_adjoint(const SimArgs& s, float K, int k, int n_ckpt, float* ckpt, float* pv, float* yt,
+                      uint32_t* list, unsigned* count, cudaStream_t st) {
     if (s.d_in > SL_MAX_DIN_TC) return set_error(SL_ERR_UNSUPPORTED, "d_in=%d > %d", s.d_in, SL_MAX_DIN_TC);
     if (k > kMaxCkptK) return set_error(SL_ERR_UNSUPPORTED, "ckpt_k=%d > %d", k, kMaxCkptK);
+    if (s.total > static_cast<int64_t>(UINT32_MAX)) return set_error(SL_ERR_UNSUPPORTED, "total_paths >= 2^32");
+    // 1. forward: the sampler, keeping Y_0, Y_k, Y_2k, ..
+    SimArgs f = s;
+    f.out_YT = yt;
+    f.out_grid = ckpt;
+    f.grid_k = k;
+    int rc = launch_tc_7l(s.m, f, st);
+    if (rc) return rc;
+    // 2. payoff of every path, list of the in-the-money ones
+    rc = cuda_error(cudaMemsetAsync(count, 0, sizeof(unsigned), st), "count clear");
+    if (rc) return rc;
+    const unsigned blocks = static_cast<unsigned>((s.total + 255) / 256);
+    itm_compact_kernel<<<blocks, 256, 0, st>>>(yt, s.total, K, s.p, pv, list, count);
+    rc = cuda_error(cudaGetLastError(), "itm_compact launch");
+    if (rc) return rc;
+    // 3. reverse sweep over the listed paths
     AdjTC A{};
     A.s = s;
+    A.s.out_YT = nullptr;
+    A.s.out_grid = nullptr;
     A.K = K;
     A.k = k;
     A.n_ckpt = n_ckpt;
     A.ckpt = ckpt;
     A.pv = pv;
-    return launch_adj_tc<2>(A, st);
+    A.list = list;
+    A.count = count;
+    return launch_reverse<2>(A, st);
 }
 
 }  // namespace sl

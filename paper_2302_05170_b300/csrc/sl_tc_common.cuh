@@ -438,7 +438,11 @@ __device__ __forceinline__ void tile_out(Tile& T, const SimArgs& a, int i) {
 #pragma unroll
     for (int j = SL_MAX_M - 1; j >= 0; --j) acc = fmaf(__uint_as_float(yv[j]), T.lb[j], acc);
     T.Y = acc;
-    if (a.out_grid && T.valid) a.out_grid[static_cast<int64_t>(i + 1) * a.total + T.g] = T.Y;
+    if (a.out_grid && T.valid) {
+        const int next = i + 1;
+        if (a.grid_k <= 1) a.out_grid[static_cast<int64_t>(next) * a.total + T.g] = T.Y;
+        else if (next % a.grid_k == 0) a.out_grid[static_cast<int64_t>(next / a.grid_k) * a.total + T.g] = T.Y;
+    }
 }
 
 __device__ __forceinline__ void tile_end(const Tile& T, const SimArgs& a) {
