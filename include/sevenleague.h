@@ -251,7 +251,9 @@ size_t sl_em_labels_noalloc_max_samples(void);
  * Pathwise sensitivities (adjoint) of E[f(Y_T)], f(Y) = max(Y - K, 0).
  * ---------------------------------------------------------------------- */
 
-/* Bytes of workspace seven_league_adjoint needs. */
+/* Bytes of workspace seven_league_adjoint needs: the status word, ceil(n_steps /
+ * ckpt_k) + 1 checkpoint rows of total_paths FP32, the per-path values, Y_T and
+ * the in-the-money path list (BF16 form), and the per-set reduction scratch. */
 size_t sl_adjoint_workspace_size(int64_t total_paths, int n_sets, int n_steps, int ckpt_k, int p);
 
 /*
@@ -268,10 +270,13 @@ size_t sl_adjoint_workspace_size(int64_t total_paths, int n_sets, int n_steps, i
  * seed_grad: device FP64 [n_sets] upstream factors (NULL = 1), for use as the
  * backward of an autograd function.  out_paths: device FP32 [(2+p)][total]
  * per-path (f, df/dY0, df/dtheta_0..) or NULL (kept in the workspace).
- * Network forms: net->prec = SL_PREC_FP32 runs the FP32 CUDA-core form;
- * SL_PREC_BF16 (ReLU, d_in <= SL_MAX_DIN_TC) runs the tcgen05 form, which
- * samples the same paths as the BF16 sampler and back-propagates through the
- * same BF16 weights (hi + lo BF16 cotangents, FP32 accumulation).
+ * Network forms: net->prec = SL_PREC_FP32 runs the FP32 CUDA-core form (one
+ * launch). SL_PREC_BF16 (ReLU, d_in <= SL_MAX_DIN_TC) runs the tcgen05 form in
+ * three launches on `stream`: the BF16 sampler (the same paths as
+ * seven_league_simulate_batched) keeping the checkpoint rows, a compaction of
+ * the in-the-money paths, and a reverse sweep over those paths only that
+ * back-propagates through the same BF16 weights (hi + lo BF16 cotangents, FP32
+ * accumulation). total_paths < 2^32 for the BF16 form.
  */
 int seven_league_adjoint(int model, const sl_net* net, const float* theta, int p, const float* Y0,
                          const int64_t* path_offsets, int n_sets, int64_t total_paths, float T,
