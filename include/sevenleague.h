@@ -127,6 +127,16 @@ int sl_quantile_ranks(int m, int64_t n, int64_t* ranks);
  * receives the raw SL_DEV_* bits. */
 int sl_workspace_status(const void* ws, void* stream, uint32_t* bits);
 
+/*
+ * Self-test of the bounded waits (a library facility; the paper has no
+ * counterpart).  Clears the status word of `ws` (device, >= 256 bytes) and
+ * launches one warp that waits, with the kernels' own bounded mbarrier wait,
+ * on a barrier nothing arrives on; after about one second the wait gives up
+ * and sets SL_DEV_TIMEOUT, and the kernel returns.  sl_workspace_status then
+ * reports SL_ERR_TIMEOUT; the context stays usable.
+ */
+int sl_selftest_wait_timeout(void* ws, size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------------------------------
  * Online stage (Algorithm I, steps 2-8).
  * ---------------------------------------------------------------------- */

@@ -28,6 +28,7 @@ ACT_RELU, ACT_SOFTPLUS = 0, 1
 PREC_FP32, PREC_BF16 = 0, 1
 PAYOFF_CALL = 0
 WIDTH, N_HIDDEN, MIN_M, MAX_M = 50, 4, 2, 8
+SL_DEV_NONFINITE, SL_DEV_OFFSETS, SL_DEV_TIMEOUT = 0x1, 0x2, 0x4   # device status bits
 _STATUS_NAMES = {1: "SL_ERR_ARG", 2: "SL_ERR_UNSUPPORTED", 3: "SL_ERR_WORKSPACE",
                  4: "SL_ERR_CUDA", 5: "SL_ERR_DEVICE", 6: "SL_ERR_TIMEOUT"}
 
@@ -41,6 +42,7 @@ EXPORTED = [
     "sl_tc_get_pipeline", "sl_train_workspace_size",
     "sl_mlp_forward", "sl_mse_grad", "sl_adam_step", "sl_train", "sl_adjoint_workspace_size",
     "seven_league_adjoint", "em_collocation_labels_noalloc", "sl_em_labels_noalloc_max_samples",
+    "sl_selftest_wait_timeout",
 ]
 
 
@@ -106,6 +108,7 @@ def load(path: str = LIB_PATH):
     L.sl_adjoint_workspace_size.restype = _sz
     L.seven_league_adjoint.argtypes = [_i, ctypes.POINTER(sl_net), _vp, _i, _vp, _vp, _i, _i64, _f, _i, _i,
                                        _u64, _i, _f, _i, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
+    L.sl_selftest_wait_timeout.argtypes = [_vp, _sz, _vp]
     L.em_collocation_labels_noalloc.argtypes = [_i, _vp, _vp, _vp, _i, _i64, _i, _i, _u64, _vp, _vp]
     L.sl_em_labels_noalloc_max_samples.restype = _sz
     L.sl_tc_set_pipeline.argtypes = [_i]
@@ -196,6 +199,17 @@ def workspace_status(ws, stream=None):
     if rc not in (SL_OK, SL_ERR_DEVICE, SL_ERR_TIMEOUT):
         _check(rc)
     return int(bits.value)
+
+
+def selftest_wait_timeout(ws=None, stream=None):
+    """Runs the bounded-wait self-test on the status word of `ws` (allocated if None) and
+    returns the workspace (read it with workspace_status)."""
+    torch = _torch()
+    L = load()
+    if ws is None:
+        ws = _workspace(256, torch.device("cuda"))
+    _check(L.sl_selftest_wait_timeout(_ptr(ws), ws.numel(), _stream(stream)))
+    return ws
 
 
 def tc_set_slots(slots):

@@ -244,6 +244,7 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_simt_kernel(const AdjArgs
             if (i % A.k == 0) A.ckpt[static_cast<int64_t>(i / A.k) * a.total + g] = Y;
             Y = step_fwd<MODEL, ACT>(a, net, hb, nt, f, E, Y, nc.get(a, s, q, i));
         }
+        if (!isfinite(Y)) raise_status(a.status, SL_DEV_NONFINITE);
         const float payoff = fmaxf(Y - A.K, 0.0f);
         float lam = Y > A.K ? 1.0f : 0.0f;
         float gth[DS - 2];

@@ -48,3 +48,47 @@ def train_gbm_online_network(n_rows=1 << 15, n_steps=40_000, dts=(0.125, 0.25, 0
     on labels for theta in [0,0.2]x[0.1,0.5], Y_i log-uniform on [0.25,4] and dt in `dts`."""
     th, yi, dt = W.gbm_training_rows(n_rows, seed=2, dts=dts)
     return train_network(0, th, yi, dt, 7, n_steps=n_steps, device=device)
+
+
+# --- training state on disk (weights + Adam moments + step counter) for resume -------------
+STATE_VERSION = 1
+
+
+def save_training_state(path, params, adam_m, adam_v, t, d_in, m, act=0):
+    """Writes an .npz blob: header int64 [version, d_in, m, width, n_hidden, act, t] and the
+    flat FP32 arrays params, adam_m, adam_v (layout of sl_n_params: per layer W[out][in], b)."""
+    import numpy as _np
+
+    arrs = [_np.ascontiguousarray(_np.asarray(x.detach().cpu() if hasattr(x, "detach") else x,
+                                              dtype=_np.float32)) for x in (params, adam_m, adam_v)]
+    n = W.n_params(d_in, m)
+    if any(a.shape != (n,) for a in arrs):
+        raise ValueError("state arrays must have shape (%d,)" % n)
+    header = _np.array([STATE_VERSION, d_in, m, W.WIDTH, W.N_HIDDEN, act, int(t)], dtype=_np.int64)
+    with open(path, "wb") as fh:
+        _np.savez(fh, header=header, params=arrs[0], adam_m=arrs[1], adam_v=arrs[2])
+
+
+def load_training_state(path, device=None):
+    """Reads save_training_state's blob; checks the header against the arrays.  Returns a dict
+    with params, adam_m, adam_v (numpy, or torch tensors on `device`), t, d_in, m, act."""
+    import numpy as _np
+
+    with _np.load(path) as z:
+        header = z["header"]
+        if header.shape != (7,) or int(header[0]) != STATE_VERSION:
+            raise ValueError("not a training state (version %s)" % (header[:1],))
+        _, d_in, m, width, n_hidden, act, t = (int(v) for v in header)
+        if (width, n_hidden) != (W.WIDTH, W.N_HIDDEN):
+            raise ValueError("network shape %dx%d != %dx%d" % (n_hidden, width, W.N_HIDDEN, W.WIDTH))
+        n = W.n_params(d_in, m)
+        out = {k: z[k].astype(_np.float32) for k in ("params", "adam_m", "adam_v")}
+    for k, a in out.items():
+        if a.shape != (n,):
+            raise ValueError("%s has shape %s, header says (%d,)" % (k, a.shape, n))
+    if device is not None:
+        import torch
+
+        out = {k: torch.as_tensor(a, device=device) for k, a in out.items()}
+    out.update(t=t, d_in=d_in, m=m, act=act)
+    return out

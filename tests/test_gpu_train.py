@@ -139,3 +139,27 @@ def test_train_gbm_and_gain(sl, orc):
 
 def stats_norm_cdf(x):
     return 0.5 * math.erfc(-x / math.sqrt(2.0))
+
+
+def test_resume_from_saved_state(sl, orc, tmp_path):
+    """Training 2 x 50 Adam steps with a save/load of (weights, moments, step) in between gives
+    bit-identical weights to 100 uninterrupted steps (Adam and the minibatch order are
+    deterministic)."""
+    from paper_2302_05170_b300 import pipeline
+    th, yi, dt = W.gbm_training_rows(512, seed=9)
+    feats = torch.as_tensor(np.concatenate([yi[:, None], dt[:, None], th], 1).astype(np.float32), device="cuda")
+    labels = torch.as_tensor(np.random.default_rng(1).normal(1.0, 0.2, (512, 7)).astype(np.float32), device="cuda")
+    rows = torch.as_tensor(W.minibatch_rows(512, 128, 100, seed=2), device="cuda")
+    P0 = torch.as_tensor(W.xavier_params(4, 7, seed=0), device="cuda")
+
+    P, am, av = P0.clone(), torch.zeros_like(P0), torch.zeros_like(P0)
+    sl.train(P, 4, 7, am, av, 0, feats, labels, rows, 128, lr=1e-3)
+    straight = P.cpu().numpy()
+
+    P, am, av = P0.clone(), torch.zeros_like(P0), torch.zeros_like(P0)
+    sl.train(P, 4, 7, am, av, 0, feats, labels, rows[:50], 128, lr=1e-3)
+    pipeline.save_training_state(tmp_path / "s.npz", P, am, av, 50, 4, 7)
+    st = pipeline.load_training_state(tmp_path / "s.npz", device="cuda")
+    P, am, av = st["params"], st["adam_m"], st["adam_v"]
+    sl.train(P, 4, 7, am, av, st["t"], feats, labels, rows[50:], 128, lr=1e-3)
+    assert np.array_equal(P.cpu().numpy(), straight)
