@@ -394,9 +394,16 @@ def main():
         feats_c = torch.cat([yid[:, None], dtd[:, None], thd], 1).contiguous()
         P_c = torch.as_tensor(W.xavier_params(5, 7, seed=0), device=dev)
         am_c, av_c = torch.zeros_like(P_c), torch.zeros_like(P_c)
+        rows_all = [torch.as_tensor(W.minibatch_rows(1024, 1024, 1000, seed=40 + c), device=dev) for c in range(10)]
+        t_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        t_ev[0].record(stream)
         for c in range(10):
-            rows_c = torch.as_tensor(W.minibatch_rows(1024, 1024, 1000, seed=40 + c), device=dev)
-            sl.train(P_c, 5, 7, am_c, av_c, 1000 * c, feats_c, lab, rows_c, 1024, lr=1e-3 * 0.01 ** (c / 9))
+            sl.train(P_c, 5, 7, am_c, av_c, 1000 * c, feats_c, lab, rows_all[c], 1024, lr=1e-3 * 0.01 ** (c / 9))
+        t_ev[1].record(stream)
+        torch.cuda.synchronize()
+        secondary["train_adam_steps_per_s"] = 10000 / (t_ev[0].elapsed_time(t_ev[1]) * 1e-3)
+        secondary["train_workload"] = ("CIR network 5->50x4->7, batch 1024 of 1024 label rows, 10000 Adam steps "
+                                       "(forward, MSE back-propagation, deterministic reduction, update)")
         cb = W.cir_batched()
         tot_c = int(cb["offsets"][-1])
         net_c = sl.make_net(P_c, 5, 7, prec=prec)
