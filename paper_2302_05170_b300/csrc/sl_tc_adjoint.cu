@@ -9,11 +9,12 @@
 //     out-of-the-money paths (Y_T <= K), and the list of in-the-money paths;
 //  3. tc_adjoint_reverse_kernel over that list only, 128 listed paths per tile
 //     (one warpgroup, warp 0 issues the MMAs), lambda = 1 at Y_T; per segment
-//     (last first): recompute Y_ck .. Y_ck+k-1 from the checkpoint; then per
-//     step i, from the segment's last to its first:
-//     a. mask pass: layers 1-4 at Y_i; the ReLU pattern of every hidden layer
-//        is kept in tensor memory (the packed BF16 "hi" words of the layer's
-//        output: non-zero exactly where the pre-activation is positive);
+//     (last first), in blocks of at most 8 steps (last first):
+//     a. a forward pass over the block from its first state (the checkpoint,
+//        or for a segment longer than 8 steps a state recomputed first) that
+//        records the ReLU pattern of every hidden layer at every step as bits
+//        in shared memory (pre-activation > 0);
+//     then per step i of the block, from its last to its first:
 //     b. backward chain with c_j = lambda * ell_j(X_i) (the cotangent of the
 //        collocation points: d Y_{i+1} / d y_j = ell_j(X_i)):
 //        dh4 = W5^T c, dz_l = dh_l masked, dh_{l-1} = W_l^T dz_l, ...,
@@ -23,8 +24,9 @@
 //     c. lambda <- d/dY_i, g_theta += d/dtheta.
 //  Per-set FP64 means come from the shared deterministic reduction.
 //
-// Tensor memory per tile: 256 columns -- accumulator 0..63, A operand
-// 64..119, masks of hidden layers 1..4 at 128 + 32 (l-1) (25 words each).
+// Tensor memory per tile: 128 columns -- accumulator 0..63, A operand 64..119.
+// Shared memory per tile: the block's ReLU patterns, 8 steps x 4 layers x 2 words
+// per path (32 KB).
 #include "sl_tc_common.cuh"
 
 namespace sl {
@@ -114,21 +116,35 @@ __device__ __forceinline__ bool tile_sync_issue_T(const Tile& T, const IssueCons
     return ok;
 }
 
-// Forward hidden epilogue that also keeps the layer's ReLU pattern: the packed
-// hi words 0..24 of the next A row go to the mask columns `mcol` as well.
-__device__ __forceinline__ void tile_hidden_keep_mask(const Tile& T, uint32_t mcol) {
+// Steps of a segment whose ReLU patterns are recorded at once (per tile: 8 steps x 4
+// hidden layers x 2 words x 128 rows in shared memory).
+constexpr int kMaskSteps = 8;
+constexpr int kMaskWordsPerTile = kMaskSteps * 4 * 2 * kTile;
+
+// Hidden epilogue of a recorded forward step: the sampler's epilogue (ReLU, BF16 hi + lo,
+// next A row) plus the layer's ReLU pattern as bits -- bit j of word 0 for neuron j < 32,
+// bit j of word 1 for neuron 32 + j -- stored to mrow[0] and mrow[kTile].
+__device__ __forceinline__ void tile_hidden_rec(const Tile& T, uint32_t* mrow) {
     tc_fence_after();
     uint32_t v[32], v2[16], u[8];
     tmem_ld32(T.taddr, v);
     tmem_ld16(T.taddr + 32, v2);
     tmem_ld8(T.taddr + 48, u);
     tmem_wait_ld();
+    uint32_t m0 = 0u, m1 = 0u;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) m0 |= (static_cast<int32_t>(v[j]) > 0) ? (1u << j) : 0u;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) m1 |= (static_cast<int32_t>(v2[j]) > 0) ? (1u << j) : 0u;
+    m1 |= (static_cast<int32_t>(u[0]) > 0) ? (1u << 16) : 0u;
+    m1 |= (static_cast<int32_t>(u[1]) > 0) ? (1u << 17) : 0u;
+    mrow[0] = m0;
+    mrow[kTile] = m1;
     const uint32_t at = T.taddr + 64;
     uint32_t hw[16], lw[16];
 #pragma unroll
     for (int i2 = 0; i2 < 16; ++i2) split_relu(v[2 * i2], v[2 * i2 + 1], hw[i2], lw[i2]);
     tmem_st16(at, hw);
-    tmem_st16(T.taddr + mcol, hw);
     uint32_t h9[9], l9[9];
 #pragma unroll
     for (int i2 = 0; i2 < 9; ++i2)
@@ -138,33 +154,28 @@ __device__ __forceinline__ void tile_hidden_keep_mask(const Tile& T, uint32_t mc
     const uint32_t gc[16] = {lw[4], lw[5], lw[6], lw[7], lw[8], lw[9], lw[10], lw[11],
                              lw[12], lw[13], lw[14], lw[15], l9[0], l9[1], l9[2], l9[3]};
     const uint32_t gd[8] = {l9[4], l9[5], l9[6], l9[7], l9[8], 0u, 0u, 0u};
-    const uint32_t gm[16] = {h9[0], h9[1], h9[2], h9[3], h9[4], h9[5], h9[6], h9[7], h9[8], 0u, 0u, 0u,
-                             0u, 0u, 0u, 0u};
     tmem_st16(at + 16, gb);
     tmem_st16(at + 32, gc);
     tmem_st8(at + 48, gd);
-    tmem_st16(T.taddr + mcol + 16, gm);
     tmem_wait_st();
     tc_fence_before();
 }
 
-// Backward epilogue: dh (accumulator columns 0..49) masked by the ReLU pattern
-// kept at `mcol`, split into BF16 hi + lo (no ReLU: cotangents have either
-// sign) and written as the next A row (hi 0..24, 25..27 = 0, lo 28..52).
-__device__ __forceinline__ void tile_backward_hidden(const Tile& T, uint32_t mcol) {
+// Backward epilogue: dh (accumulator columns 0..49) masked by the recorded ReLU pattern
+// (m0: neurons 0..31, m1: neurons 32..49), split into BF16 hi + lo (no ReLU: cotangents
+// have either sign) and written as the next A row (hi 0..24, 25..27 = 0, lo 28..52).
+__device__ __forceinline__ void tile_backward_bits(const Tile& T, uint32_t m0, uint32_t m1) {
     tc_fence_after();
-    uint32_t v[32], v2[16], u[8], mk[16], mk2[16];
+    uint32_t v[32], v2[16], u[8];
     tmem_ld32(T.taddr, v);
     tmem_ld16(T.taddr + 32, v2);
     tmem_ld8(T.taddr + 48, u);
-    tmem_ld16(T.taddr + mcol, mk);
-    tmem_ld16(T.taddr + mcol + 16, mk2);
     tmem_wait_ld();
     const uint32_t at = T.taddr + 64;
     uint32_t hw[16], lw[16];
 #pragma unroll
     for (int i2 = 0; i2 < 16; ++i2)
-        split_rn((mk[i2] & 0x0000FFFFu) ? v[2 * i2] : 0u, (mk[i2] & 0xFFFF0000u) ? v[2 * i2 + 1] : 0u, hw[i2],
+        split_rn((m0 >> (2 * i2)) & 1u ? v[2 * i2] : 0u, (m0 >> (2 * i2 + 1)) & 1u ? v[2 * i2 + 1] : 0u, hw[i2],
                  lw[i2]);
     tmem_st16(at, hw);
     uint32_t h9[9], l9[9];
@@ -172,7 +183,7 @@ __device__ __forceinline__ void tile_backward_hidden(const Tile& T, uint32_t mco
     for (int i2 = 0; i2 < 9; ++i2) {
         const uint32_t ra = (i2 < 8) ? v2[2 * i2] : u[0];
         const uint32_t rb = (i2 < 8) ? v2[2 * i2 + 1] : u[1];
-        split_rn((mk2[i2] & 0x0000FFFFu) ? ra : 0u, (mk2[i2] & 0xFFFF0000u) ? rb : 0u, h9[i2], l9[i2]);
+        split_rn((m1 >> (2 * i2)) & 1u ? ra : 0u, (m1 >> (2 * i2 + 1)) & 1u ? rb : 0u, h9[i2], l9[i2]);
     }
     const uint32_t gb[16] = {h9[0], h9[1], h9[2], h9[3], h9[4], h9[5], h9[6], h9[7],
                              h9[8], 0u, 0u, 0u, lw[0], lw[1], lw[2], lw[3]};
@@ -252,15 +263,16 @@ __device__ __forceinline__ void tile_begin_listed(Tile& T, const SimArgs& a, int
 template <int WG>
 __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const AdjTC A) {
     constexpr int S = WG;
-    constexpr uint32_t kCols = (S * 256 <= 256) ? 256 : 512;
-    static_assert(S * 256 <= 512, "tensor memory holds 512 columns");
+    constexpr uint32_t kCols = (S * 128 <= 128) ? 128 : (S * 128 <= 256) ? 256 : 512;
+    static_assert(S * 128 <= 512, "tensor memory holds 512 columns");
     const SimArgs& a = A.s;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     unsigned char* sB = smem;
     unsigned char* sBT = smem + kBBytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sBT + kBTBytes);   // d_ready[S], drain
+    uint32_t* masks = reinterpret_cast<uint32_t*>(sBT + kBTBytes);     // [S][kMaskSteps][4][2][128]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(masks + S * kMaskWordsPerTile);   // d_ready[S], drain
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + S + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -306,12 +318,12 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
     CT.db1 = sw128_desc(sBT_u + kB5TBytes + 3 * kBHTBytes);
 
     Tile T;
-    T.d_tmem = tmem_base + static_cast<uint32_t>(wg * 256);
+    T.d_tmem = tmem_base + static_cast<uint32_t>(wg * 128);
     T.taddr = T.d_tmem + (static_cast<uint32_t>(wq * 32) << 16);
     T.d_bar = smem_u32(&bars[wg]);
     T.bar_id = 1 + wg;
     T.dph = 0;
-    const uint32_t kMask0 = 128;   // mask of hidden layer l at 128 + 32 (l - 1)
+    uint32_t* tmask = masks + wg * kMaskWordsPerTile + r;   // word (step, layer l, half h) at ((step*4 + l-1)*2 + h)*128
 
     const int64_t n_list = static_cast<int64_t>(*A.count);
     const int64_t n_tiles = (n_list + kTile - 1) / kTile;
@@ -333,72 +345,83 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
             const int i1 = min(i0 + A.k, a.n_steps);
             float Ys[kMaxCkptK];
             Ys[0] = A.ckpt[static_cast<int64_t>(c) * a.total + g];
-            // recompute Y_{i0+1} .. Y_{i1-1}
-            for (int i = i0; i < i1 - 1; ++i) {
-                T.Y = Ys[i - i0];
-                tile_features(T, a);
-                ok = tile_sync_issue(T, C, 0, ok, issuer);
-                if (!ok) break;
-                tile_rng_any(T, a, i, blk);
-#pragma unroll
-                for (int l = 1; l <= 4; ++l) {
-                    const bool w = tile_wait(T, abort_flag, a.status);
-                    if (w) tile_hidden(T);
-                    ok = tile_sync_issue(T, C, l, w, issuer);
+            if (i1 - i0 > kMaskSteps) {
+                // a long segment: recompute its states first (Y_{i0+1} .. Y_{i1-1})
+                for (int i = i0; i < i1 - 1; ++i) {
+                    T.Y = Ys[i - i0];
+                    tile_features(T, a);
+                    ok = tile_sync_issue(T, C, 0, ok, issuer);
                     if (!ok) break;
-                }
-                if (!ok) break;
-                const bool w = tile_wait(T, abort_flag, a.status);
-                if (w) tile_out(T, a, i);
-                ok = bar_and(T.bar_id, w);
-                if (!ok) break;
-                Ys[i - i0 + 1] = T.Y;
-            }
-            for (int i = i1 - 1; ok && i >= i0; --i) {
-                // a. mask pass: layers 1-4 at Y_i
-                T.Y = Ys[i - i0];
-                tile_features(T, a);
-                ok = tile_sync_issue(T, C, 0, ok, issuer);
-                if (!ok) break;
-                tile_rng_any(T, a, i, blk);   // ell_j at this step's normal
+                    tile_rng_any(T, a, i, blk);
 #pragma unroll
-                for (int l = 1; l <= 4; ++l) {
-                    const bool w = tile_wait(T, abort_flag, a.status);
-                    if (w) tile_hidden_keep_mask(T, kMask0 + 32 * (l - 1));
-                    if (l < 4) {
+                    for (int l = 1; l <= 4; ++l) {
+                        const bool w = tile_wait(T, abort_flag, a.status);
+                        if (w) tile_hidden(T);
                         ok = tile_sync_issue(T, C, l, w, issuer);
-                    } else {
-                        ok = bar_and(T.bar_id, w);
+                        if (!ok) break;
                     }
                     if (!ok) break;
-                }
-                if (!ok) break;
-                // b. backward chain
-                tile_cotangent(T, lam);
-                ok = tile_sync_issue_T(T, CT, 0, ok, issuer);
-                if (!ok) break;
-#pragma unroll
-                for (int lt = 1; lt <= 4; ++lt) {   // dh4 -> W4^T, dh3 -> W3^T, dh2 -> W2^T, dh1 -> W1^T
                     const bool w = tile_wait(T, abort_flag, a.status);
-                    if (w) tile_backward_hidden(T, kMask0 + 32 * (4 - lt));
-                    ok = tile_sync_issue_T(T, CT, lt, w, issuer);
+                    if (w) tile_out(T, a, i);
+                    ok = bar_and(T.bar_id, w);
+                    if (!ok) break;
+                    Ys[i - i0 + 1] = T.Y;
+                }
+            }
+            // blocks of at most kMaskSteps steps, last first: a forward pass over the block that
+            // records every hidden layer's ReLU pattern, then the reverse steps of the block
+            for (int j1 = i1; ok && j1 > i0;) {
+                const int j0 = max(i0, j1 - kMaskSteps);
+                T.Y = Ys[j0 - i0];
+                for (int i = j0; i < j1; ++i) {
+                    tile_features(T, a);
+                    ok = tile_sync_issue(T, C, 0, ok, issuer);
+                    if (!ok) break;
+                    tile_rng_any(T, a, i, blk);
+#pragma unroll
+                    for (int l = 1; l <= 4; ++l) {
+                        const bool w = tile_wait(T, abort_flag, a.status);
+                        if (w) tile_hidden_rec(T, tmask + ((i - j0) * 4 + (l - 1)) * 2 * kTile);
+                        ok = tile_sync_issue(T, C, l, w, issuer);
+                        if (!ok) break;
+                    }
+                    if (!ok) break;
+                    const bool w = tile_wait(T, abort_flag, a.status);
+                    if (w) tile_out(T, a, i);
+                    ok = bar_and(T.bar_id, w);
                     if (!ok) break;
                 }
-                if (!ok) break;
-                // c. d/d(features): lambda <- d/dY_i, g_theta += d/dtheta
-                const bool w = tile_wait(T, abort_flag, a.status);
-                if (w) {
-                    tc_fence_after();
-                    uint32_t gf[8];
-                    tmem_ld8(T.taddr, gf);
-                    tmem_wait_ld();
-                    tc_fence_before();
-                    lam = __uint_as_float(gf[0]);
+                for (int i = j1 - 1; ok && i >= j0; --i) {
+                    // backward chain with c_j = lambda * ell_j(X_i)
+                    tile_rng_any(T, a, i, blk);
+                    tile_cotangent(T, lam);
+                    ok = tile_sync_issue_T(T, CT, 0, ok, issuer);
+                    if (!ok) break;
 #pragma unroll
-                    for (int q = 0; q < SL_MAX_DIN_TC - 2; ++q)
-                        if (q < p) gth[q] += __uint_as_float(gf[2 + q]);
+                    for (int lt = 1; lt <= 4; ++lt) {   // dh4 -> W4^T, dh3 -> W3^T, dh2 -> W2^T, dh1 -> W1^T
+                        const bool w = tile_wait(T, abort_flag, a.status);
+                        const uint32_t* mr = tmask + ((i - j0) * 4 + (4 - lt)) * 2 * kTile;
+                        if (w) tile_backward_bits(T, mr[0], mr[kTile]);
+                        ok = tile_sync_issue_T(T, CT, lt, w, issuer);
+                        if (!ok) break;
+                    }
+                    if (!ok) break;
+                    // d/d(features): lambda <- d/dY_i, g_theta += d/dtheta
+                    const bool w = tile_wait(T, abort_flag, a.status);
+                    if (w) {
+                        tc_fence_after();
+                        uint32_t gf[8];
+                        tmem_ld8(T.taddr, gf);
+                        tmem_wait_ld();
+                        tc_fence_before();
+                        lam = __uint_as_float(gf[0]);
+#pragma unroll
+                        for (int q = 0; q < SL_MAX_DIN_TC - 2; ++q)
+                            if (q < p) gth[q] += __uint_as_float(gf[2 + q]);
+                    }
+                    ok = bar_and(T.bar_id, w);
                 }
-                ok = bar_and(T.bar_id, w);
+                j1 = j0;
             }
         }
         if (!ok) break;
@@ -431,7 +454,7 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
 template <int WG>
 int launch_reverse(const AdjTC& A, cudaStream_t st) {
     auto kern = tc_adjoint_reverse_kernel<WG>;
-    const size_t smem = 1024 + kBBytes + kBTBytes + (WG + 1) * 8 + 16;
+    const size_t smem = 1024 + kBBytes + kBTBytes + static_cast<size_t>(WG) * kMaskWordsPerTile * 4 + (WG + 1) * 8 + 16;
     int rc = cuda_error(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(smem)),
                         "tc_adjoint attribute");
@@ -483,7 +506,7 @@ int launch_tc_adjoint(const SimArgs& s, float K, int k, int n_ckpt, float* ckpt,
     A.pv = pv;
     A.list = list;
     A.count = count;
-    return launch_reverse<2>(A, st);
+    return launch_reverse<3>(A, st);
 }
 
 }  // namespace sl
