@@ -17,8 +17,8 @@ namespace sl {
 namespace {
 
 constexpr int W = SL_WIDTH;
-constexpr int kRows = 16;              // minibatch rows per CTA
-constexpr int kThreads = 256;
+constexpr int kRows = 8;               // minibatch rows per CTA
+constexpr int kThreads = 512;
 constexpr int kMaxParams = W * SL_MAX_DIN + W + 3 * (W * W + W) + SL_MAX_M * W + SL_MAX_M;
 
 struct Layer {
