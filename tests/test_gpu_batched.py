@@ -8,6 +8,8 @@ counts in one persistent launch, replayed from a captured CUDA graph.
 * The CIR batched workload's shape (4096 sets, log-uniform counts) against the FP64
   oracle on sampled paths of sampled sets, including the smallest and largest sets.
 * Degenerate batches: every set empty (nothing to do, status clean, means 0), one path.
+* Maximum sizes: a set of 2^31 + 129 paths (indices past int32) in both forms, and
+  SL_MAX_SETS = 2^24 parameter sets in one launch.
 """
 import numpy as np
 import pytest
@@ -135,3 +137,51 @@ def test_long_horizon_bf16(sl, orc):
     mx = max_abs_normals(orc, 3, 0, st, q, 128)
     ok, *info = gate(rel_err(yt, want, 1.0), mx, 2e-3)
     assert ok, info
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_more_than_2_31_paths(sl, orc, prec):
+    """One set of 2^31 + 129 paths (flat and in-set path indices past the int32 range), 1 step:
+    sampled paths including the last ones agree with the oracle; the set mean is finite."""
+    n = (1 << 31) + 129
+    P = W.xavier_params(4, 7, seed=8)
+    net = sl.make_net(_dev(P), 4, 7, prec=prec)
+    th = W.gbm_online_thetas(1)
+    off = W.offsets_from_counts([n])
+    yt = torch.empty(n, dtype=torch.float32, device="cuda")
+    mean = torch.empty(1, dtype=torch.float64, device="cuda")
+    ws = sl.seven_league_simulate_batched(sl.MODEL_MLP, net, _dev(th), _dev([1.0]), _dev(off, torch.int64), 1.0, 1,
+                                          7, 2, out_YT=yt, out_mean=mean)
+    assert sl.workspace_status(ws) == 0
+    idx = np.concatenate([np.arange(0, 64), np.arange((1 << 31) - 64, (1 << 31) + 64), np.arange(n - 64, n)])
+    Pw = (W.bf16_round(P) if prec else P).astype(np.float64)
+    want = orc.seven_league_paths(0, Pw, th, [1.0], off, 1.0, 1, 7, 2, d_in=4, idx=idx)
+    got = yt[torch.as_tensor(idx, device="cuda")].cpu().numpy()
+    assert np.all(rel_err(got, want, 1.0) <= (2e-3 if prec else 1e-5))
+    assert np.isfinite(mean.item())
+    del yt
+
+
+def test_max_sets(sl, orc):
+    """SL_MAX_SETS (2^24) parameter sets with 0 or 1 path each, 2 steps, BF16 form."""
+    n_sets = 1 << 24
+    rng = np.random.default_rng(9)
+    counts = rng.integers(0, 2, n_sets)
+    off = W.offsets_from_counts(counts)
+    th = rng.uniform([0.0, 0.1], [0.2, 0.5], (n_sets, 2)).astype(np.float32)
+    P = W.xavier_params(4, 7, seed=9)
+    net = sl.make_net(_dev(P), 4, 7, prec=sl.PREC_BF16)
+    total = int(off[-1])
+    yt = torch.empty(total, dtype=torch.float32, device="cuda")
+    mean = torch.empty(n_sets, dtype=torch.float64, device="cuda")
+    ws = sl.seven_league_simulate_batched(sl.MODEL_MLP, net, _dev(th), _dev(np.ones(n_sets)), _dev(off, torch.int64),
+                                          1.0, 2, 7, 4, out_YT=yt, out_mean=mean)
+    assert sl.workspace_status(ws) == 0
+    sets = np.concatenate([np.nonzero(counts)[0][:50], np.nonzero(counts)[0][-50:]])
+    idx = off[sets]
+    want = orc.seven_league_paths(0, W.bf16_round(P).astype(np.float64), th, np.ones(n_sets), off, 1.0, 2, 7, 4,
+                                  d_in=4, idx=idx)
+    got = yt.cpu().numpy()[idx]
+    assert np.all(rel_err(got, want, 1.0) <= 2e-3)
+    m = mean.cpu().numpy()
+    assert np.array_equal(m[sets], got.astype(np.float64)) and np.all(m[counts == 0] == 0)
