@@ -72,29 +72,11 @@ __device__ __forceinline__ float pick4(const float4& v, int i) {
     return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
-// g_m(X) through (x_j, y_j): first (modified-Lagrange) barycentric form
-// ell(X) sum_j bary_j y_j / (X - x_j), evaluated without division as
-// sum_j y_j bary_j prod_{k<j}(X-x_k) prod_{k>j}(X-x_k).  Stable when X lies
-// outside [x_0, x_{m-1}] (the second form cancels there).
-template <int M>
-__device__ __forceinline__ float lagrange_eval(const float (&y)[M], float X, const GHConst& gh) {
-    float d[M], pre[M];
-#pragma unroll
-    for (int j = 0; j < M; ++j) d[j] = X - gh.x[j];
-    pre[0] = 1.0f;
-#pragma unroll
-    for (int j = 1; j < M; ++j) pre[j] = pre[j - 1] * d[j - 1];
-    float acc = 0.0f, suf = 1.0f;
-#pragma unroll
-    for (int j = M - 1; j >= 0; --j) {
-        acc = fmaf(y[j] * gh.bary[j], pre[j] * suf, acc);
-        suf *= d[j];
-    }
-    return acc;
-}
-
-// Same map for a runtime m <= SL_MAX_M: the unused nodes contribute a factor 1
-// to every product and a zero term (their barycentric weights are 0).
+// g_m(X) through (x_j, y_j) for a runtime m <= SL_MAX_M: first (modified-Lagrange)
+// barycentric form ell(X) sum_j bary_j y_j / (X - x_j), evaluated without division as
+// sum_j y_j bary_j prod_{k<j}(X-x_k) prod_{k>j}(X-x_k).  Stable when X lies outside
+// [x_0, x_{m-1}] (the second form cancels there).  The unused nodes j >= m contribute a
+// factor 1 to every product and a zero term (their barycentric weights are 0).
 __device__ __forceinline__ float lagrange_eval_m(const float (&y)[SL_MAX_M], float X,
                                                  const GHConst& gh, int m) {
     float d[SL_MAX_M], pre[SL_MAX_M];
@@ -124,23 +106,6 @@ __device__ __forceinline__ void lagrange_basis_m(float X, const GHConst& gh, int
     float suf = 1.0f;
 #pragma unroll
     for (int j = SL_MAX_M - 1; j >= 0; --j) {
-        l[j] = gh.bary[j] * (pre[j] * suf);
-        suf *= d[j];
-    }
-}
-
-// The Lagrange basis values ell_j(X) (for the adjoint: d g_m / d y_j).
-template <int M>
-__device__ __forceinline__ void lagrange_basis(float X, const GHConst& gh, float (&l)[M]) {
-    float d[M], pre[M];
-#pragma unroll
-    for (int j = 0; j < M; ++j) d[j] = X - gh.x[j];
-    pre[0] = 1.0f;
-#pragma unroll
-    for (int j = 1; j < M; ++j) pre[j] = pre[j - 1] * d[j - 1];
-    float suf = 1.0f;
-#pragma unroll
-    for (int j = M - 1; j >= 0; --j) {
         l[j] = gh.bary[j] * (pre[j] * suf);
         suf *= d[j];
     }
