@@ -479,6 +479,35 @@ def main():
                                           % (v_c.item(), d0_c.item(), [round(x, 5) for x in dth_c[0].tolist()]))
         secondary["cir_adjoint_workload"] = ("CIR network (BF16 tcgen05), kappa=1 ybar=0.1 gamma=0.3 Y0=0.1, "
                                              "1e6 paths x 64 steps of dt=0.25, checkpoint every 8")
+        # the paper's own experiment (Table 6.1's path counts): OU, m = 5, trained network;
+        # time per 7L run of 16 steps (T = 2) in both forms, and the pathwise error at 2e5 paths
+        # against Eq. (6.6) on the same normals (exact-collocation OU model)
+        P_ou, _, _ = pipeline.train_ou_network(n_rows=1 << 14, n_steps=20000, device=dev)
+        th_ou, y0_ou = torch.tensor([[0.5, 0.3, 1.0]], device=dev), torch.tensor([1.5], device=dev)
+        ou_ms = {}
+        for pr, key in ((sl.PREC_BF16, "bf16"), (sl.PREC_FP32, "fp32")):
+            net_ou = sl.make_net(P_ou, 5, 5, prec=pr)
+            for n_ou in (1000, 50000, 100000, 200000):
+                off_ou = torch.as_tensor(W.offsets_from_counts([n_ou]), device=dev)
+                yt_ou = torch.empty(n_ou, dtype=f32, device=dev)
+                ws_ou = torch.empty(sl.simulate_workspace_size(n_ou, 1), dtype=torch.uint8, device=dev)
+                run_ou = lambda: sl.seven_league_simulate_batched(sl.MODEL_MLP, net_ou, th_ou, y0_ou, off_ou, 2.0, 16,
+                                                                  5, 3, out_YT=yt_ou, ws=ws_ou, total_paths=n_ou)
+                run_ou()
+                torch.cuda.synchronize()
+                e0.record(stream)
+                for _ in range(10):
+                    run_ou()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ou_ms["%s_%d" % (key, n_ou)] = round(e0.elapsed_time(e1) / 10, 4)
+            yt_ex = torch.empty(200000, dtype=f32, device=dev)
+            sl.seven_league_simulate_batched(sl.MODEL_OU_EXACT, None, th_ou, y0_ou, off_ou, 2.0, 16, 5, 3,
+                                             out_YT=yt_ex, total_paths=200000)
+            secondary["ou_pathwise_err_" + key] = float((yt_ou - yt_ex).abs().mean().item())
+        secondary["ou_table61_ms_per_run"] = ou_ms
+        secondary["ou_table61_workload"] = ("OU (Ybar 0.5, sigma 0.3, lambda 1, Y0 1.5), m=5, trained 5->50x4->5 ReLU "
+                                            "network, T=2 in 16 steps; paths 1e3/5e4/1e5/2e5 as in Table 6.1")
 
     # --- end to end through the C ABI with host buffers (pinned), copies timed.  Every step copies
     # its inputs host -> device, runs the sampler and copies Y_T and the set moments back; the steps

@@ -50,6 +50,13 @@ def train_gbm_online_network(n_rows=1 << 15, n_steps=40_000, dts=(0.125, 0.25, 0
     return train_network(0, th, yi, dt, 7, n_steps=n_steps, device=device)
 
 
+def train_ou_network(n_rows=1 << 14, n_steps=20_000, m=5, dts=(0.125, 0.25, 0.5, 1.0), device="cuda"):
+    """The OU network of the paper's experiment (Eq. 6.5; d_in = 5: Y, dt, Ybar, sigma, lambda;
+    m = 5 collocation points), trained on labels for the box of workloads.ou_training_rows."""
+    th, yi, dt = W.ou_training_rows(n_rows, dts=dts)
+    return train_network(1, th, yi, dt, m, n_steps=n_steps, device=device)
+
+
 # --- training state on disk (weights + Adam moments + step counter) for resume -------------
 STATE_VERSION = 1
 

@@ -119,6 +119,19 @@ def gbm_training_rows(n_rows: int, seed: int = 2, dt: float = 0.125, dts=None):
     return (np.stack([mu, sg], 1).astype(np.float32), yi.astype(np.float32), dtv.astype(np.float32))
 
 
+def ou_training_rows(n_rows: int, seed: int = 12, dts=(0.125, 0.25, 0.5, 1.0)):
+    """Training rows (theta=(Ybar, sigma, lambda), Y_i, dt) for the OU network of the
+    paper's experiment (Eq. 6.5): Ybar ~ U[0,1], sigma ~ U[0.1,0.5], lambda ~ U[0.5,2],
+    Y_i ~ U[-1,2], dt drawn uniformly from `dts`."""
+    rng = np.random.default_rng(seed)
+    yb = rng.uniform(0.0, 1.0, n_rows)
+    sg = rng.uniform(0.1, 0.5, n_rows)
+    lam = rng.uniform(0.5, 2.0, n_rows)
+    yi = rng.uniform(-1.0, 2.0, n_rows)
+    dtv = rng.choice(np.asarray(dts, np.float64), n_rows)
+    return (np.stack([yb, sg, lam], 1).astype(np.float32), yi.astype(np.float32), dtv.astype(np.float32))
+
+
 def cir_label_rows(n_rows: int = 1024, seed: int = 3):
     """CIR_LABELS rows: theta=(kappa, ybar, gamma), Y_i, dt uniform in their boxes."""
     rng = np.random.default_rng(seed)

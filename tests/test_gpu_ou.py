@@ -1,0 +1,90 @@
+"""The paper's own experiment (the Ornstein-Uhlenbeck process, Eq. 6.5, with m = 5
+collocation points and a trained network) against the exact solution Eq. (6.6).
+
+* The trained network against the exact OU collocation map
+  y_j = e^{-lambda dt} Y + Ybar (1 - e^{-lambda dt}) + sigma s(dt) x_j on a grid.
+* Pathwise error of the trained 7L scheme against the exact solution driven by the scheme's
+  own normals (the exact-collocation OU model, which is pathwise Eq. 6.6), at dt = 0.125,
+  0.5 and 1 (T = 2): small at every step size, and not growing with it (the paper's claim).
+* Weak error of Var(Y_T): Euler-Maruyama's grows with the step (at lambda dt = 1 its variance
+  is sigma^2 dt instead of sigma^2 (1 - e^{-2 lambda T}) / (2 lambda)); the 7L scheme's does not.
+* Both network forms (FP32 CUDA cores, BF16 tensor cores) meet the same bounds.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2302_05170_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+YB, SG, LAM, Y0, T, M = 0.5, 0.3, 1.0, 1.5, 2.0, 5
+
+
+def _dev(a, dtype=torch.float32):
+    return torch.as_tensor(np.asarray(a), dtype=dtype, device="cuda")
+
+
+def _run(sl, model, net, n, n_steps, seed):
+    off = _dev(W.offsets_from_counts([n]), torch.int64)
+    yt = torch.empty(n, device="cuda")
+    ws = sl.seven_league_simulate_batched(model, net, _dev([[YB, SG, LAM]]), _dev([Y0]), off, T, n_steps, M, seed,
+                                          out_YT=yt)
+    assert sl.workspace_status(ws) == 0
+    return yt.cpu().numpy().astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def ou_net(sl):
+    from paper_2302_05170_b300 import pipeline
+    P, losses, _ = pipeline.train_ou_network(n_rows=1 << 14, n_steps=20000)
+    assert losses[-500:].mean() < 0.02 * losses[:20].mean()
+    return P
+
+
+def test_trained_map_vs_exact(sl, orc, ou_net):
+    x, _, _ = sl.gauss_hermite(M)
+    net = sl.make_net(ou_net, 5, M)
+    gy, gyb, gsg, glam, gdt = np.meshgrid(np.linspace(-0.5, 1.5, 5), np.linspace(0.2, 0.8, 3),
+                                          np.linspace(0.15, 0.45, 3), np.linspace(0.6, 1.8, 3), [0.125, 0.5, 1.0])
+    G = np.stack([gy.ravel(), gdt.ravel(), gyb.ravel(), gsg.ravel(), glam.ravel()], 1).astype(np.float32)
+    yh = sl.mlp_forward(net, _dev(G)).cpu().numpy().astype(np.float64)
+    Y, dt, yb, sg, lam = (G[:, k:k + 1].astype(np.float64) for k in range(5))
+    e1 = np.exp(-lam * dt)
+    ex = e1 * Y + yb * (1 - e1) + sg * np.sqrt((1 - e1 ** 2) / (2 * lam)) * x[None, :]
+    err = np.abs(yh - ex).max()
+    print("max |H - exact OU map| on the grid:", err)
+    assert err < 0.05
+
+
+def test_pathwise_error_does_not_grow_with_step(sl, orc, ou_net):
+    n, seed = 20000, 13
+    errs, var7, var_em = {}, {}, {}
+    exact_var = SG * SG * (1 - math.exp(-2 * LAM * T)) / (2 * LAM)
+    for n_steps in (16, 4, 2):
+        ref = _run(sl, sl.MODEL_OU_EXACT, None, n, n_steps, seed)           # Eq. (6.6) on the 7L normals
+        row = {}
+        for name, prec in (("fp32", sl.PREC_FP32), ("bf16", sl.PREC_BF16)):
+            y = _run(sl, sl.MODEL_MLP, sl.make_net(ou_net, 5, M, prec=prec), n, n_steps, seed)
+            row[name] = np.abs(y - ref).mean()
+            if name == "fp32":
+                var7[n_steps] = abs(y.var() - ref.var()) / exact_var
+        errs[n_steps] = row
+        em = sl.em_terminal(1, _dev([[YB, SG, LAM]]), _dev([Y0]), _dev([T]), n, n_steps, seed)
+        var_em[n_steps] = abs(em.cpu().numpy()[0].astype(np.float64).var() - exact_var) / exact_var
+    print("pathwise mean |7L - exact|:", errs)
+    print("relative variance error, 7L (vs the exact solution on the same normals):", var7)
+    print("relative variance error, Euler-Maruyama (vs the exact variance):", var_em)
+    # both forms: small at every step size and not growing with it (the BF16 weights perturb the
+    # learned map by about 2^-9 per weight, an error of the size of the map's own, so each form
+    # is held to the bound separately rather than to the other form)
+    for form in ("fp32", "bf16"):
+        for k in (16, 4, 2):
+            assert errs[k][form] < 0.02 * Y0, (form, k)
+        assert errs[2][form] <= 1.5 * errs[16][form], form
+    # Euler-Maruyama's variance error grows with the step; the 7L scheme's stays small
+    assert var_em[2] > 0.5 and var_em[2] > 5 * var_em[16]
+    for k in (16, 4, 2):
+        assert var7[k] < 0.05
