@@ -369,6 +369,21 @@ def main():
             secondary["bf16_vs_fp32_max_rel_diff"] = float(((a64 - b64).abs() / (b64.abs() + 1.0)).max())
         except sl.SLError as e:
             secondary["other_form_error"] = str(e)
+        if prec == sl.PREC_BF16:
+            # the same workload with the paper's Softplus activation in the tensor-core form
+            # (log(1 + e^z) on the fast exponent/logarithm unit in the epilogue)
+            net_sp = sl.make_net(P, 4, 7, act=sl.ACT_SOFTPLUS, prec=sl.PREC_BF16)
+            yt_sp = torch.empty_like(yt)
+            step(out_yt=yt_sp, net_=net_sp)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                step(out_yt=yt_sp, net_=net_sp)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            secondary["softplus_bf16_path_steps_per_s"] = path_steps / (e0.elapsed_time(e1) / 3 * 1e-3)
+            del yt_sp
         # offline stage: EM label samples/s on the CIR labels workload
         th, yi, dtr = W.cir_label_rows(1024)
         thd, yid, dtd = (torch.as_tensor(a, device=dev) for a in (th, yi, dtr))

@@ -77,7 +77,8 @@ enum { SL_ACT_RELU = 0, SL_ACT_SOFTPLUS = 1 };
 /* Arithmetic of the network in the online sampler */
 enum { SL_PREC_FP32 = 0,        /* FP32 CUDA-core form */
        SL_PREC_BF16 = 1 };      /* tcgen05 BF16 tensor cores, FP32 accumulate, BF16 weights,
-                                   activations split hi+lo in BF16 (ReLU only) */
+                                   activations split hi+lo in BF16; d_in <= SL_MAX_DIN_TC;
+                                   ReLU or Softplus in the sampler, ReLU in the adjoint */
 enum { SL_PAYOFF_CALL = 0 };    /* f(Y_T) = max(Y_T - K, 0) */
 
 /*

@@ -22,8 +22,6 @@ int check_net(const sl_net* net, int m, int p) {
     if (net->prec != SL_PREC_FP32 && net->prec != SL_PREC_BF16)
         return set_error(SL_ERR_ARG, "prec=%d", net->prec);
     if (net->prec == SL_PREC_BF16) {
-        if (net->act != SL_ACT_RELU)
-            return set_error(SL_ERR_UNSUPPORTED, "BF16 tensor-core form supports ReLU only");
         if (net->d_in > SL_MAX_DIN_TC)
             return set_error(SL_ERR_UNSUPPORTED, "BF16 tensor-core form needs d_in <= %d", SL_MAX_DIN_TC);
     }

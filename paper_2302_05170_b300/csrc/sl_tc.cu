@@ -45,7 +45,7 @@ using namespace tc;
 // tiles' MMAs.  With TPW = 2 the warpgroup alternates between its two tiles
 // layer by layer, so one tile's epilogue runs while the other tile's MMAs run
 // ("ping-pong"); with TPW = 1 the overlap comes only from other warpgroups.
-template <int WG, int TPW>
+template <int WG, int TPW, int ACT>
 __global__ void __launch_bounds__(128 * WG, 1) tc_7l_kernel(const SimArgs a) {
     constexpr int S = WG * TPW;
     constexpr uint32_t kCols = (S * 128 <= 128) ? 128 : (S * 128 <= 256) ? 256 : 512;
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_7l_kernel(const SimArgs a) {
 #pragma unroll
                 for (int j = 0; j < TPW; ++j) {
                     const bool w = tile_wait(T[j], abort_flag, a.status);
-                    if (w) tile_hidden(T[j]);
+                    if (w) tile_hidden_act<ACT>(T[j]);
                     ok = tile_sync_issue(T[j], C, l, w, issuer);
                     if (!ok) break;
                 }
@@ -177,10 +177,10 @@ size_t tc_smem_bytes() {
     return 1024 + kBBytes + (WG * TPW + 1) * 8 + 16;
 }
 
-template <int WG, int TPW>
+template <int WG, int TPW, int ACT = SL_ACT_RELU>
 int launch_cfg(const SimArgs& a, cudaStream_t st) {
     constexpr int S = WG * TPW;
-    auto kern = tc_7l_kernel<WG, TPW>;
+    auto kern = tc_7l_kernel<WG, TPW, ACT>;
     const size_t smem = tc_smem_bytes<WG, TPW>();
     int rc = cuda_error(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(smem)),
@@ -203,6 +203,13 @@ int g_tpw = 1;     // tiles per warpgroup (sl_tc_set_pipeline)
 int launch_tc_7l(int m, const SimArgs& a, cudaStream_t st) {
     (void)m;
     if (a.d_in > SL_MAX_DIN_TC) return set_error(SL_ERR_UNSUPPORTED, "d_in=%d > %d", a.d_in, SL_MAX_DIN_TC);
+    if (a.act == SL_ACT_SOFTPLUS) {   // one tile per warpgroup
+        switch (g_slots) {
+            case 2: return launch_cfg<2, 1, SL_ACT_SOFTPLUS>(a, st);
+            case 3: return launch_cfg<3, 1, SL_ACT_SOFTPLUS>(a, st);
+            default: return launch_cfg<4, 1, SL_ACT_SOFTPLUS>(a, st);
+        }
+    }
     if (g_tpw == 2) return (g_slots == 2) ? launch_cfg<1, 2>(a, st) : launch_cfg<2, 2>(a, st);
     switch (g_slots) {
         case 2: return launch_cfg<2, 1>(a, st);

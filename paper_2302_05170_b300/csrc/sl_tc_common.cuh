@@ -229,17 +229,36 @@ __device__ __forceinline__ void split_relu(uint32_t a, uint32_t b, uint32_t& hw,
     sub_f32x2(a, b, hw << 16, hw & 0xFFFF0000u, la, lb);
     lw = pack_relu(la, lb);
 }
+// Softplus log(1 + e^x) = max(x, 0) + log(1 + e^{-|x|}) on the fast exponent/logarithm
+// unit.  e^{-|x|} lies in (0, 1], so the logarithm's argument lies in (1, 2]; its absolute
+// error stays near 1e-7, far below what the BF16 hi + lo split keeps of the result.
+__device__ __forceinline__ float softplus_fast(float x) {
+    return fmaxf(x, 0.0f) + __logf(1.0f + __expf(-fabsf(x)));
+}
 __device__ __forceinline__ uint32_t pack_rn(float lo_elem, float hi_elem) {
     uint32_t d;
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi_elem), "f"(lo_elem));
     return d;
 }
+// Activation of a pair as BF16 hi + lo: ReLU (fused into the conversions) or Softplus.
+template <int ACT>
+__device__ __forceinline__ void split_act(uint32_t a, uint32_t b, uint32_t& hw, uint32_t& lw);
+
 // x as BF16 hi + lo for a pair (a, b), no ReLU (cotangents have either sign).
 __device__ __forceinline__ void split_rn(uint32_t a, uint32_t b, uint32_t& hw, uint32_t& lw) {
     asm("cvt.rz.bf16x2.f32 %0, %1, %2;" : "=r"(hw) : "f"(__uint_as_float(b)), "f"(__uint_as_float(a)));
     float la, lb;
     sub_f32x2(a, b, hw << 16, hw & 0xFFFF0000u, la, lb);
     lw = pack_rn(la, lb);
+}
+template <>
+__device__ __forceinline__ void split_act<SL_ACT_RELU>(uint32_t a, uint32_t b, uint32_t& hw, uint32_t& lw) {
+    split_relu(a, b, hw, lw);
+}
+template <>
+__device__ __forceinline__ void split_act<SL_ACT_SOFTPLUS>(uint32_t a, uint32_t b, uint32_t& hw, uint32_t& lw) {
+    split_rn(__float_as_uint(softplus_fast(__uint_as_float(a))), __float_as_uint(softplus_fast(__uint_as_float(b))),
+             hw, lw);
 }
 
 // Byte offset of 16-byte chunk `c` (0..7) of row `r` inside a 128B-swizzled atom.
@@ -394,10 +413,11 @@ __device__ __forceinline__ bool tile_wait(Tile& T, volatile int* abort_flag, uns
     return __all_sync(0xffffffffu, w);
 }
 
-// Hidden-layer epilogue: accumulator row -> ReLU -> BF16 hi + lo -> next A row.
+// Hidden-layer epilogue: accumulator row -> activation -> BF16 hi + lo -> next A row.
 // A row (BF16 words): hi 0..24 (columns 0..49), word 25 = {1.0, 0} (bias unit),
 // 26..27 = 0, lo 28..52, 53..55 = 0.
-__device__ __forceinline__ void tile_hidden(const Tile& T) {
+template <int ACT>
+__device__ __forceinline__ void tile_hidden_act(const Tile& T) {
     tc_fence_after();
     uint32_t v[32], v2[16], u[8];
     tmem_ld32(T.taddr, v);
@@ -408,12 +428,12 @@ __device__ __forceinline__ void tile_hidden(const Tile& T) {
     uint32_t hw[16], lw[16];
 #pragma unroll
     for (int i2 = 0; i2 < 16; ++i2)     // columns 0..31 -> hi words 0..15, lo words 28..43
-        split_relu(v[2 * i2], v[2 * i2 + 1], hw[i2], lw[i2]);
+        split_act<ACT>(v[2 * i2], v[2 * i2 + 1], hw[i2], lw[i2]);
     tmem_st16(at, hw);
     uint32_t h9[9], l9[9];
 #pragma unroll
     for (int i2 = 0; i2 < 9; ++i2)      // columns 32..49 -> hi words 16..24, lo words 44..52
-        split_relu((i2 < 8) ? v2[2 * i2] : u[0], (i2 < 8) ? v2[2 * i2 + 1] : u[1], h9[i2], l9[i2]);
+        split_act<ACT>((i2 < 8) ? v2[2 * i2] : u[0], (i2 < 8) ? v2[2 * i2 + 1] : u[1], h9[i2], l9[i2]);
     const uint32_t gb[16] = {h9[0], h9[1], h9[2], h9[3], h9[4], h9[5], h9[6], h9[7],
                              h9[8], 0x00003F80u, 0u, 0u, lw[0], lw[1], lw[2], lw[3]};
     const uint32_t gc[16] = {lw[4], lw[5], lw[6], lw[7], lw[8], lw[9], lw[10], lw[11],
@@ -425,6 +445,8 @@ __device__ __forceinline__ void tile_hidden(const Tile& T) {
     tmem_wait_st();
     tc_fence_before();
 }
+
+__device__ __forceinline__ void tile_hidden(const Tile& T) { tile_hidden_act<SL_ACT_RELU>(T); }
 
 // Output layer: collocation points y_j, then Y_{i+1} = g_m(X) = sum_j y_j ell_j(X)
 // (Algorithm I steps 5-6).

@@ -139,3 +139,28 @@ def test_full_size_gbm_online_sampled(sl, orc):
     want = _oracle(orc, w["params"], 4, 7, w["theta"], w["Y0"], off, w["T"], w["n_steps"], w["seed"], idx=idx)
     _check(orc, yt[idx], want, off, w["seed"], w["n_steps"], idx=idx)
     assert np.all(np.isfinite(yt))
+
+
+@pytest.mark.parametrize("slots", [4, 3, 2])
+def test_softplus(sl, orc, slots):
+    """Softplus (the paper's activation) in the tensor-core form: log(1 + e^z) on the fast
+    exponent/logarithm unit, then the same BF16 hi + lo split; against the FP64 oracle's
+    Softplus network with the same BF16 weights."""
+    P = W.xavier_params(5, 7, seed=12)
+    th = np.random.default_rng(3).uniform(0.05, 0.4, (3, 3)).astype(np.float32)
+    off = W.offsets_from_counts([3000, 129, 4000])
+    y0 = np.array([1.0, 0.5, 1.5], np.float32)
+    old = (sl.tc_get_slots(), sl.tc_get_pipeline())
+    try:
+        _set_cfg(sl, slots, 1)
+        net = sl.make_net(_dev(P), 5, 7, act=sl.ACT_SOFTPLUS, prec=sl.PREC_BF16)
+        total = int(off[-1])
+        yt = torch.full((total,), float("nan"), dtype=torch.float32, device="cuda")
+        ws = sl.seven_league_simulate_batched(sl.MODEL_MLP, net, _dev(th), _dev(y0), _dev(off, torch.int64), 2.0, 16,
+                                              7, 4, out_YT=yt)
+        assert sl.workspace_status(ws) == 0
+    finally:
+        _set_cfg(sl, *old)
+    want = orc.seven_league_paths(0, W.bf16_round(P).astype(np.float64), th, y0, off, 2.0, 16, 7, 4, d_in=5,
+                                  act=orc.ACT_SOFTPLUS)
+    _check(orc, yt.cpu().numpy(), want, off, 4, 16)
