@@ -82,13 +82,17 @@ class ClockSampler:
         self.rows, self.proc, self.bus_id = [], None, bus_id
 
     def __enter__(self):
-        cmd = ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits", "-lms", "200"]
+        cmd = ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits", "-lms", "25"]
         if self.bus_id:
             cmd[1:1] = ["-i", self.bus_id]
         try:
             self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.time()
+            while not self.rows and time.time() - t0 < 5.0:   # sampling has started before the region
+                time.sleep(0.005)
+            self.rows.clear()
         except OSError:
             self.proc = None
         return self
@@ -99,6 +103,10 @@ class ClockSampler:
 
     def __exit__(self, *a):
         if self.proc:
+            n = len(self.rows)
+            t0 = time.time()
+            while len(self.rows) <= n and time.time() - t0 < 1.0:   # one sample after the region ends
+                time.sleep(0.005)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
