@@ -153,22 +153,32 @@ grad_partial_kernel(const float* __restrict__ P, int d_in, int m, int act,
     }
 }
 
-// Sum the partials of every parameter (CTA order) into grad, and optionally
-// apply Adam; block 0 also sums the partial losses.
-__global__ void reduce_adam_kernel(const float* __restrict__ part, const float* __restrict__ loss_part,
-                                   int n_parts, int n_params, float* __restrict__ grad,
-                                   float* __restrict__ loss_out, float* __restrict__ params,
-                                   float* __restrict__ am, float* __restrict__ av, float lr,
-                                   float b1, float b2, float eps, float c1, float c2) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0 && loss_out) {
+// Sum the partials of every parameter into grad, and optionally apply Adam; block 0
+// also sums the partial losses.  A block takes kRedParams parameters; kRedSplit
+// threads per parameter add the partials c = c0, c0 + kRedSplit, .. in order and the
+// kRedSplit sub-sums are added in a fixed order (deterministic).
+constexpr int kRedParams = 64, kRedSplit = 4, kRedThreads = kRedParams * kRedSplit;
+
+__global__ void __launch_bounds__(kRedThreads)
+reduce_adam_kernel(const float* __restrict__ part, const float* __restrict__ loss_part, int n_parts,
+                   int n_params, float* __restrict__ grad, float* __restrict__ loss_out,
+                   float* __restrict__ params, float* __restrict__ am, float* __restrict__ av, float lr,
+                   float b1, float b2, float eps, float c1, float c2) {
+    __shared__ float sub[kRedSplit][kRedParams];
+    const int pl = threadIdx.x % kRedParams, c0 = threadIdx.x / kRedParams;
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * kRedParams + pl;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && loss_out) {
         float t = 0.0f;
         for (int c = 0; c < n_parts; ++c) t += loss_part[c];
         *loss_out = t;
     }
-    if (i >= n_params) return;
-    float gsum = 0.0f;
-    for (int c = 0; c < n_parts; ++c) gsum += part[static_cast<int64_t>(c) * n_params + i];
+    float s = 0.0f;
+    if (i < n_params)
+        for (int c = c0; c < n_parts; c += kRedSplit) s += part[static_cast<int64_t>(c) * n_params + i];
+    sub[c0][pl] = s;
+    __syncthreads();
+    if (c0 != 0 || i >= n_params) return;
+    const float gsum = ((sub[0][pl] + sub[1][pl]) + sub[2][pl]) + sub[3][pl];
     if (grad) grad[i] = gsum;
     if (params) {
         const float mi = b1 * am[i] + (1.0f - b1) * gsum;
@@ -178,6 +188,8 @@ __global__ void reduce_adam_kernel(const float* __restrict__ part, const float* 
         params[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
     }
 }
+
+unsigned reduce_blocks(int64_t n_params) { return static_cast<unsigned>((n_params + kRedParams - 1) / kRedParams); }
 
 // FP32 batched forward pass, one thread per row.
 __global__ void __launch_bounds__(kThreads)
@@ -287,7 +299,7 @@ int sl_mse_grad(const sl_net* net, const float* feats, const float* labels, cons
                      &part, &lp, &nc);
     if (rc) return rc;
     const int np = static_cast<int>(sl_n_params(net->d_in, net->m));
-    reduce_adam_kernel<<<(np + 255) / 256, 256, 0, st>>>(part, lp, nc, np, grad, loss, nullptr, nullptr,
+    reduce_adam_kernel<<<reduce_blocks(np), kRedThreads, 0, st>>>(part, lp, nc, np, grad, loss, nullptr, nullptr,
                                                          nullptr, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
     return cuda_error(cudaGetLastError(), "reduce launch");
 }
@@ -300,7 +312,7 @@ int sl_adam_step(float* params, float* adam_m, float* adam_v, const float* grad,
     const float c1 = static_cast<float>(1.0 / (1.0 - pow(static_cast<double>(b1), static_cast<double>(t))));
     const float c2 = static_cast<float>(1.0 / (1.0 - pow(static_cast<double>(b2), static_cast<double>(t))));
     // one "partial" = the gradient itself
-    reduce_adam_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+    reduce_adam_kernel<<<reduce_blocks(n), kRedThreads, 0, static_cast<cudaStream_t>(stream)>>>(
         grad, grad, 1, static_cast<int>(n), nullptr, nullptr, params, adam_m, adam_v, lr, b1, b2, eps, c1, c2);
     return cuda_error(cudaGetLastError(), "adam launch");
 }
@@ -326,7 +338,7 @@ int sl_train(float* params, int d_in, int m, int act, float* adam_m, float* adam
         const double t = static_cast<double>(t0 + b + 1);
         const float c1 = static_cast<float>(1.0 / (1.0 - pow(static_cast<double>(b1), t)));
         const float c2 = static_cast<float>(1.0 / (1.0 - pow(static_cast<double>(b2), t)));
-        reduce_adam_kernel<<<(np + 255) / 256, 256, 0, st>>>(part, lp, nc, np, nullptr,
+        reduce_adam_kernel<<<reduce_blocks(np), kRedThreads, 0, st>>>(part, lp, nc, np, nullptr,
                                                              losses ? losses + b : nullptr, params,
                                                              adam_m, adam_v, lr, b1, b2, eps, c1, c2);
         rc = cuda_error(cudaGetLastError(), "reduce_adam launch");
