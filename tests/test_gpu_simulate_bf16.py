@@ -70,7 +70,7 @@ def test_gbm_small(sl, orc):
     _check(orc, yt, want, w["offsets"], w["seed"], w["n_steps"])
 
 
-@pytest.mark.parametrize("m,d_in", [(2, 3), (5, 4), (7, 4), (7, 5), (8, 7)])
+@pytest.mark.parametrize("m,d_in", [(2, 3), (5, 4), (7, 4), (7, 5), (8, 7), (3, 2), (6, 6)])
 def test_ragged_batched_grid(sl, orc, m, d_in):
     P = W.xavier_params(d_in, m, seed=m + d_in)
     rng = np.random.default_rng(m)
