@@ -371,6 +371,11 @@ def main():
             o_ms = e0.elapsed_time(e1) / 3
             key = "fp32_simt" if other == sl.PREC_FP32 else "bf16_tc"
             secondary[key + "_path_steps_per_s"] = path_steps / (o_ms * 1e-3)
+            if other == sl.PREC_FP32:   # the FP32 form against its own roofline (FP32 FMA lanes)
+                sms = torch.cuda.get_device_properties(dev).multi_processor_count
+                fp32_peak = sms * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+                secondary["fp32_simt_roofline_frac"] = (ALG_FLOPS_PER_PATH_STEP * path_steps / (o_ms * 1e-3) / 1e12
+                                                        / fp32_peak)
             secondary["bf16_over_fp32"] = (value / (path_steps / (o_ms * 1e-3))) if other == sl.PREC_FP32 else \
                 (path_steps / (o_ms * 1e-3)) / value
             a64, b64 = yt.double(), yt_o.double()
