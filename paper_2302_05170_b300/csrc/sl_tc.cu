@@ -9,13 +9,13 @@
 // 128 paths.  Warpgroup t (warps 4t..4t+3, TMEM lanes 32*(warp%4)..) owns
 // slot t: its warp 0 issues the slot's tcgen05.mma (one elected lane), with B
 // (weights) in shared memory through 128-byte-swizzled K-major descriptors, A
-// (activations) in tensor memory (or shared memory) and FP32 accumulators in
-// tensor memory; all four warps are the slot's epilogue: each thread reads the
-// accumulator row of its path with
-// tcgen05.ld, applies ReLU, splits every activation h into BF16 hi + lo
-// (hi = h truncated to BF16, lo = BF16(h - hi)), and writes the next A tile.
-// While one slot's MMAs run, the other slots' epilogues, Philox normals and
-// g_m evaluations run, so tensor pipe and CUDA cores overlap.
+// (activations) and FP32 accumulators in tensor memory; all four warps are the
+// slot's epilogue: each thread reads the accumulator row of its path with
+// tcgen05.ld, applies the activation (ReLU fused into the BF16 conversions, or
+// Softplus), splits every activation h into BF16 hi + lo (hi = h truncated to
+// BF16, lo = BF16(h - hi)), and writes the next A tile.  Several slots keep
+// independent MMA groups in the tensor pipe at once; the Philox normals and the
+// Lagrange basis of a step are computed while the step's first MMA runs.
 //
 // Numerics: weights and biases are rounded to BF16 (nearest, ties to even);
 // the network's inputs and activations carry ~16 significant bits through the
