@@ -97,6 +97,13 @@ def _declare(L):
     L.orc_em_labels.argtypes = [_c_int, _d, _d, _d, _c_int, _c_int, _c_i64, _c_int, _c_int, _c_u64,
                                 _d, _c_int]
     L.orc_em_labels.restype = _c_int
+    L.orc_cdc_conditional_points.argtypes = [_c_int, _d, _d, _c_dbl, _d]
+    L.orc_cdc_tables.argtypes = [_c_int, _d, _d, _c_int, _c_int, _c_int, _c_int, _d, _c_int, _d, _c_int,
+                                 _c_dbl, _c_int, _c_int, _d, _d]
+    L.orc_cdc_tables.restype = _c_int
+    L.orc_cdc_paths.argtypes = [_c_int, _d, _d, _c_int, _c_int, _c_int, _c_int, _d, _c_int, _d, _i64,
+                                _c_int, _c_dbl, _c_int, _c_int, _c_u64, _i64, _c_i64, _d, _d, _c_int]
+    L.orc_cdc_paths.restype = _c_int
 
 
 def _p(a, ct):
@@ -298,3 +305,53 @@ def em_labels(sde, theta, Yi, dt, n_paths, n_fine, m, seed, row0=0, n_rows=None,
     if rc:
         raise ValueError("orc_em_labels failed")
     return out
+
+
+# --- the 7L-CDC variant (global interpolation in Y through marginal collocation points) ----
+def cdc_conditional_points(z, C, Y):
+    """yhat_j = sum_k C[k, j] L_k(Y), L_k the Lagrange basis through the nodes z (row 0
+    when all nodes coincide)."""
+    zz = _f64(z)
+    m = zz.shape[0]
+    CC = _f64(C).reshape(m, m)
+    out = np.zeros(m)
+    lib().orc_cdc_conditional_points(m, _p(zz, _d), _p(CC, _d), float(Y), _p(out, _d))
+    return out
+
+
+def cdc_tables(model, P, theta, Y0, T, n_steps, m, Pm=None, d_in=3, act=ACT_RELU, width=WIDTH,
+               n_hidden=N_HIDDEN):
+    """Marginal nodes z [n_sets, n_steps, m] and conditional points at them
+    C [n_sets, n_steps, m (node k), m (point j)]."""
+    y0 = _f64(Y0).reshape(-1)
+    n_sets = y0.shape[0]
+    th = _f64(theta).reshape(n_sets, -1)
+    Pp = _f64(P) if P is not None else np.zeros(1)
+    Pmp = _f64(Pm) if Pm is not None else None
+    z = np.zeros((n_sets, n_steps, m))
+    C = np.zeros((n_sets, n_steps, m, m))
+    rc = lib().orc_cdc_tables(model, _p(Pp, _d), _p(Pmp, _d), d_in, width, n_hidden, act, _p(th, _d),
+                              th.shape[1], _p(y0, _d), n_sets, float(T), n_steps, m, _p(z, _d), _p(C, _d))
+    if rc:
+        raise ValueError("orc_cdc_tables failed")
+    return z, C
+
+
+def cdc_paths(model, P, theta, Y0, offsets, T, n_steps, m, seed, Pm=None, idx=None, d_in=3,
+              act=ACT_RELU, grid=False, threads=0, width=WIDTH, n_hidden=N_HIDDEN):
+    """Y_T (and optionally the grid) of selected flat paths of the 7L-CDC chain."""
+    o, n_sets = _offsets(offsets)
+    th = _f64(theta).reshape(n_sets, -1)
+    Pp = _f64(P) if P is not None else np.zeros(1)
+    Pmp = _f64(Pm) if Pm is not None else None
+    y0 = _f64(Y0).reshape(n_sets)
+    ix = None if idx is None else _i64a(idx)
+    n = int(o[-1]) if ix is None else ix.shape[0]
+    out = np.zeros(n)
+    gr = np.zeros((n, n_steps + 1)) if grid else None
+    rc = lib().orc_cdc_paths(model, _p(Pp, _d), _p(Pmp, _d), d_in, width, n_hidden, act, _p(th, _d),
+                             th.shape[1], _p(y0, _d), _p(o, _i64), n_sets, float(T), n_steps, m, seed,
+                             _p(ix, _i64), n, _p(out, _d), _p(gr, _d), threads)
+    if rc:
+        raise ValueError("orc_cdc_paths failed")
+    return (out, gr) if grid else out

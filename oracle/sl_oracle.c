@@ -17,7 +17,10 @@
  * interpolation identities, closed-form moments of the exact-collocation GBM
  * chain, pathwise exactness of the exact-collocation OU chain, exact moment
  * recursions of Euler-Maruyama, brute-force order statistics, central finite
- * differences for every derivative, and closed-form Black-Scholes values.
+ * differences for every derivative, and closed-form Black-Scholes values;
+ * the 7L-CDC variant against polynomial reproduction, scipy's exact marginal
+ * and conditional quantiles, and the 7L chain wherever the conditional map is
+ * affine in Y (tests/test_oracle_cdc.py).
  * No function in this file is "parity unpinned".
  */
 #include <math.h>
@@ -719,5 +722,113 @@ int orc_em_labels(int sde, const double* theta, const double* Yi, const double* 
         orc_order_statistics(buf, off, 1, ranks, m, labels + (int64_t)r * m);
     }
     free(buf);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * The 7L-CDC variant (the remark after Algorithm I and the discussion of
+ * Table 6.1): step 3 of Algorithm I -- the network evaluated for every path --
+ * is replaced by a global interpolation built from a few network evaluations
+ * per parameter set and time step.  The paper describes the variant in outline
+ * only; the reading taken here:
+ *
+ *  - Marginal collocation points of Y at t_i = i dt (i >= 1): z_k = G_k(Y0,
+ *    t_i, theta), k = 0..m-1, the collocation map at the same Gauss-Hermite
+ *    abscissae x_k over the horizon t_i from the deterministic start Y0 (the
+ *    law of Y_{t_i} given Y_0 is the marginal law).  G is the marginal network
+ *    (features [Y0, t_i, theta]) or, for the exact models, the exact map with
+ *    dt replaced by t_i.  At i = 0 the marginal is the point mass at Y0.
+ *  - Conditional collocation points at the marginal nodes:
+ *    C[k][j] = H_j(z_k, dt, theta) (m network evaluations).
+ *  - Per path at Y_i: yhat_j = sum_k C[k][j] L_k(Y_i), the Lagrange
+ *    interpolation in Y through the nodes z_k (the "global interpolation");
+ *    then Y_{i+1} = g_m(X_{i+1}) through (x_j, yhat_j), with the same normals
+ *    as the 7L scheme (tag 0).
+ *  - If the marginal nodes all coincide (i = 0, or a degenerate law) every
+ *    path sits at that point and yhat_j = C[0][j].
+ * With a conditional map that is a polynomial of degree <= m-1 in Y (the
+ * exact GBM and OU maps are linear in Y) the interpolation in Y is exact and
+ * the 7L-CDC chain equals the 7L chain.
+ * ---------------------------------------------------------------------- */
+
+/* yhat_j = sum_k C[k*m + j] L_k(Y), L_k the Lagrange basis through z (plain
+ * definition); all z equal: yhat = row 0. */
+void orc_cdc_conditional_points(int m, const double* z, const double* C, double Y, double* yhat) {
+    int same = 1;
+    for (int k = 1; k < m; ++k)
+        if (z[k] != z[0]) same = 0;
+    for (int j = 0; j < m; ++j) yhat[j] = same ? C[j] : 0.0;
+    if (same) return;
+    for (int k = 0; k < m; ++k) {
+        double L = 1.0;
+        for (int l = 0; l < m; ++l)
+            if (l != k) L *= (Y - z[l]) / (z[k] - z[l]);
+        for (int j = 0; j < m; ++j) yhat[j] += C[k * m + j] * L;
+    }
+}
+
+/* Tables of every (set s, step i): z[(s*n_steps + i)*m + k] and
+ * C[((s*n_steps + i)*m + k)*m + j].  Pm: the marginal network's parameters
+ * (the same shape as P; NULL: P itself). */
+int orc_cdc_tables(int model, const double* P, const double* Pm, int d_in, int width, int n_hidden,
+                   int act, const double* theta, int p, const double* Y0, int n_sets, double T,
+                   int n_steps, int m, double* z, double* C) {
+    double xn[64], wn[64];
+    if (orc_gauss_hermite(m, xn, wn) != 0) return 1;
+    orc_net N = {model, d_in, width, n_hidden, act, m, p, P, xn};
+    orc_net NM = {model, d_in, width, n_hidden, act, m, p, Pm ? Pm : P, xn};
+    double dt = T / (double)n_steps;
+    for (int s = 0; s < n_sets; ++s) {
+        const double* th = theta + (int64_t)s * p;
+        for (int i = 0; i < n_steps; ++i) {
+            double* zi = z + ((int64_t)s * n_steps + i) * m;
+            double* Ci = C + ((int64_t)s * n_steps + i) * m * m;
+            if (i == 0) {
+                for (int k = 0; k < m; ++k) zi[k] = Y0[s];
+            } else {
+                collocation(&NM, Y0[s], i * dt, th, zi, NULL);
+            }
+            for (int k = 0; k < m; ++k) collocation(&N, zi[k], dt, th, Ci + k * m, NULL);
+        }
+    }
+    return 0;
+}
+
+/* Y_T (and optionally the grid) of selected flat paths of a batched 7L-CDC
+ * call; arguments as orc_7l_paths plus the marginal network Pm. */
+int orc_cdc_paths(int model, const double* P, const double* Pm, int d_in, int width, int n_hidden,
+                  int act, const double* theta, int p, const double* Y0, const int64_t* offsets,
+                  int n_sets, double T, int n_steps, int m, uint64_t seed, const int64_t* idx,
+                  int64_t n_idx, double* out_YT, double* out_grid, int n_threads) {
+    double xn[64], wn[64];
+    if (orc_gauss_hermite(m, xn, wn) != 0) return 1;
+    size_t nt = (size_t)n_sets * n_steps;
+    double* z = (double*)malloc(sizeof(double) * nt * m + 1);
+    double* C = (double*)malloc(sizeof(double) * nt * m * m + 1);
+    if (!z || !C) { free(z); free(C); return 1; }
+    int rc = orc_cdc_tables(model, P, Pm, d_in, width, n_hidden, act, theta, p, Y0, n_sets, T,
+                            n_steps, m, z, C);
+    if (rc) { free(z); free(C); return rc; }
+    set_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < n_idx; ++k) {
+        int64_t g = idx ? idx[k] : k;
+        int s = owning_set(offsets, n_sets, g);
+        uint32_t q = (uint32_t)(g - offsets[s]);
+        double* grid = out_grid ? out_grid + k * (int64_t)(n_steps + 1) : NULL;
+        double Y = Y0[s];
+        if (grid) grid[0] = Y;
+        for (int i = 0; i < n_steps; ++i) {
+            double yhat[ORC_MAX_W];
+            size_t r = (size_t)s * n_steps + i;
+            orc_cdc_conditional_points(m, z + r * m, C + r * m * m, Y, yhat);
+            double X = orc_normal(seed, ORC_TAG_7L, (uint32_t)s, q, (uint32_t)i);
+            Y = orc_lagrange(m, xn, yhat, X);
+            if (grid) grid[i + 1] = Y;
+        }
+        out_YT[k] = Y;
+    }
+    free(z);
+    free(C);
     return 0;
 }
