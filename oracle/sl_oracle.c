@@ -741,7 +741,8 @@ int orc_em_labels(int sde, const double* theta, const double* Yi, const double* 
  *  - Conditional collocation points at the marginal nodes:
  *    C[k][j] = H_j(z_k, dt, theta) (m network evaluations).
  *  - Per path at Y_i: yhat_j = sum_k C[k][j] L_k(Y_i), the Lagrange
- *    interpolation in Y through the nodes z_k (the "global interpolation");
+ *    interpolation in Y through the nodes z_k (the "global interpolation"),
+ *    continued linearly beyond the outermost nodes (orc_cdc_conditional_points);
  *    then Y_{i+1} = g_m(X_{i+1}) through (x_j, yhat_j), with the same normals
  *    as the 7L scheme (tag 0).
  *  - If the marginal nodes all coincide (i = 0, or a degenerate law) every
@@ -751,14 +752,40 @@ int orc_em_labels(int sde, const double* theta, const double* Yi, const double* 
  * the 7L-CDC chain equals the 7L chain.
  * ---------------------------------------------------------------------- */
 
-/* yhat_j = sum_k C[k*m + j] L_k(Y), L_k the Lagrange basis through z (plain
- * definition); all z equal: yhat = row 0. */
+/* yhat_j at Y from the conditional points C[k*m + j] at the marginal nodes z_k:
+ *  - all z_k equal: row 0;
+ *  - Y inside [min z, max z]: sum_k C[k][j] L_k(Y), L_k the Lagrange basis
+ *    through the z_k (plain definition);
+ *  - Y beyond the outermost node on one side: the straight line through that
+ *    node and the next one on the same side (a polynomial of degree m-1 grows
+ *    without bound away from its nodes; the line agrees with the polynomial at
+ *    the outermost node, and both are exact for maps affine in Y). */
 void orc_cdc_conditional_points(int m, const double* z, const double* C, double Y, double* yhat) {
     int same = 1;
     for (int k = 1; k < m; ++k)
         if (z[k] != z[0]) same = 0;
-    for (int j = 0; j < m; ++j) yhat[j] = same ? C[j] : 0.0;
-    if (same) return;
+    if (same) {
+        for (int j = 0; j < m; ++j) yhat[j] = C[j];
+        return;
+    }
+    /* the two smallest and the two largest nodes (ties keep the lower index) */
+    int lo = 0, hi = 0;
+    for (int k = 1; k < m; ++k) {
+        if (z[k] < z[lo]) lo = k;
+        if (z[k] > z[hi]) hi = k;
+    }
+    int lo2 = -1, hi2 = -1;
+    for (int k = 0; k < m; ++k) {
+        if (k != lo && (lo2 < 0 || z[k] < z[lo2])) lo2 = k;
+        if (k != hi && (hi2 < 0 || z[k] > z[hi2])) hi2 = k;
+    }
+    if (Y < z[lo] || Y > z[hi]) {
+        int a = Y < z[lo] ? lo : hi, b = Y < z[lo] ? lo2 : hi2;
+        for (int j = 0; j < m; ++j)
+            yhat[j] = C[a * m + j] + (Y - z[a]) * (C[b * m + j] - C[a * m + j]) / (z[b] - z[a]);
+        return;
+    }
+    for (int j = 0; j < m; ++j) yhat[j] = 0.0;
     for (int k = 0; k < m; ++k) {
         double L = 1.0;
         for (int l = 0; l < m; ++l)

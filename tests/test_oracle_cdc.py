@@ -2,9 +2,11 @@
 network of Algorithm I step 3 replaced by an interpolation in Y through the marginal
 collocation points).
 
-* The interpolation in Y reproduces every polynomial of degree <= m-1 (values checked with
-  numpy's polyval, inside and outside the nodes), returns row k at Y = z_k, and returns
-  row 0 when all nodes coincide.
+* The interpolation in Y reproduces every polynomial of degree <= m-1 inside the nodes' hull
+  (values checked with numpy's polyval), returns row k at Y = z_k, returns row 0 when all
+  nodes coincide; beyond the outermost nodes it is a straight line in Y (zero second
+  differences) that meets the interpolant at the outermost node and has the slope of the two
+  outermost nodes; maps affine in Y are reproduced everywhere, nodes in any order.
 * Marginal nodes of the exact models are the exact quantiles of Y_{t_i} at levels Phi(x_k):
   scipy's lognormal (GBM) and normal (OU, Eq. 6.6) quantile functions at numpy's
   Gauss-Hermite nodes; the conditional points at the nodes are the exact conditional
@@ -31,13 +33,34 @@ def test_interpolation_in_y_reproduces_polynomials(orc, m):
     z = np.sort(rng.uniform(-2.0, 3.0, m))
     coef = rng.normal(size=(m, m))                 # point j is the polynomial coef[j] (degree m-1)
     C = np.array([[np.polyval(coef[j], zk) for j in range(m)] for zk in z])
-    for Y in np.concatenate([rng.uniform(-2.0, 3.0, 20), [-3.5, 4.2], z]):
+    for Y in np.concatenate([rng.uniform(z[0], z[-1], 20), z]):
         got = orc.cdc_conditional_points(z, C, Y)
         want = np.array([np.polyval(coef[j], Y) for j in range(m)])
         assert np.allclose(got, want, rtol=1e-9, atol=1e-9 * np.abs(want).max()), Y
     for k in range(m):
         assert np.array_equal(orc.cdc_conditional_points(z, C, z[k]), C[k])
     assert np.array_equal(orc.cdc_conditional_points(np.full(m, 0.7), C, 5.0), C[0])
+
+
+@pytest.mark.parametrize("m", [2, 5, 8])
+def test_continuation_beyond_the_nodes(orc, m):
+    rng = np.random.default_rng(10 + m)
+    z = rng.permutation(np.sort(rng.uniform(-1.0, 2.0, m)))          # nodes in no particular order
+    coef = rng.normal(size=(m, 3))                                    # quadratic points
+    C = np.array([[np.polyval(coef[j], zk) for j in range(m)] for zk in z])
+    zs = np.sort(z)
+    for edge, inner, side in ((zs[0], zs[1], -1.0), (zs[-1], zs[-2], 1.0)):
+        Ys = edge + side * np.array([1e-9, 0.5, 1.0, 1.5, 40.0])
+        v = np.array([orc.cdc_conditional_points(z, C, Y) for Y in Ys])
+        at_edge = orc.cdc_conditional_points(z, C, edge)
+        assert np.allclose(v[0], at_edge, atol=1e-7)                    # continuous at the node
+        assert np.allclose(v[1] - 2 * v[2] + v[3], 0.0, atol=1e-9)      # straight line
+        slope = (at_edge - orc.cdc_conditional_points(z, C, inner)) / (edge - inner)
+        assert np.allclose((v[4] - at_edge) / (Ys[4] - edge), slope, rtol=1e-9)
+    lin = rng.normal(size=(m, 2))                                     # affine points: exact everywhere
+    CL = np.array([[lin[j, 0] + lin[j, 1] * zk for j in range(m)] for zk in z])
+    for Y in (-50.0, -1.3, 0.4, 2.7, 60.0):
+        assert np.allclose(orc.cdc_conditional_points(z, CL, Y), lin[:, 0] + lin[:, 1] * Y, rtol=1e-12, atol=1e-12)
 
 
 def test_interpolation_in_y_is_not_exact_beyond_degree(orc):
