@@ -192,6 +192,57 @@ int sl_tc_set_pipeline(int tiles_per_warpgroup);
 int sl_tc_get_pipeline(void);
 
 /* ------------------------------------------------------------------------
+ * The 7L-CDC variant (timed beside the 7L scheme in Table 6.1; the remark
+ * after Algorithm I): step 3's network evaluation per path is replaced by a
+ * global interpolation built from a few network evaluations per parameter
+ * set and step.  The paper gives the variant in outline; this library reads
+ * it as follows.  For set s and step i (t_i = i dt, dt = T / n_steps):
+ *   - marginal collocation points z_k = G_k(Y0[s], t_i, theta_s), k < m: the
+ *     collocation map over the horizon t_i from the deterministic start
+ *     (features [Y0, t_i, theta]); G = marg_net (NULL: net) for SL_MODEL_MLP,
+ *     the exact map for the exact models.  At i = 0, z_k = Y0[s];
+ *   - conditional points at the nodes C[k][j] = H_j(z_k, dt, theta_s);
+ *   - a path at Y_i takes yhat_j = sum_k C[k][j] L_k(Y_i), L_k the Lagrange
+ *     basis in Y through the z_k, while min z <= Y_i <= max z; beyond the
+ *     outermost node on a side, the line through the two outermost nodes on
+ *     that side (degree m-1 extrapolation grows without bound); yhat = C[0]
+ *     when all z_k coincide, as at i = 0.  Then Y_{i+1} = g_m(X) through
+ *     (x_j, yhat_j), with the normals of the 7L sampler (tag 0).
+ * With a conditional map that is affine in Y (the exact GBM and OU maps) the
+ * chain equals the 7L chain.  The network evaluations ((m + 1) per set and
+ * step) run in FP32 on CUDA cores whatever net->prec says; the paths run in
+ * FP32.
+ * ---------------------------------------------------------------------- */
+
+/* Bytes of workspace seven_league_cdc_simulate_batched needs. */
+size_t sl_cdc_workspace_size(int64_t total_paths, int n_sets, int n_steps);
+
+/*
+ * Batched 7L-CDC sampler.  Arguments, outputs and errors as
+ * seven_league_simulate_batched, plus marg_net (SL_MODEL_MLP only; NULL = use
+ * net; same d_in and m as net, its own activation).  The workspace holds, at
+ * byte offset 256, the tables of the call: FP32 [n_sets][n_steps][192] with,
+ * per (set, step): [0,8) z (the marginal nodes, zero beyond m); [8,16) w
+ * (their barycentric weights 1/prod_{l!=k}(z_k - z_l), computed in FP64 from
+ * the FP32 nodes; all zero when the nodes coincide); [16,80) C[8][8] (row k =
+ * the conditional points at z_k, zero beyond m); [80,88) S_lo and [88,96)
+ * S_hi, the slopes (C[b][j] - C[a][j]) / (z_b - z_a) of the lines through the
+ * two smallest and the two largest nodes (ties to the lower index; FP64,
+ * rounded once; 0 if the two nodes coincide); [96,104) C_lo and [104,112)
+ * C_hi, the rows of the smallest and the largest node; [112] z_lo, [113]
+ * z_hi; [114,120) zero; [120,128) a copy of C[0]; [128,192) Cw[8][8] =
+ * w_k b_j C[k][j] (b_j the barycentric weights of the Gauss-Hermite points,
+ * FP64 product rounded once; zero when the nodes coincide).  Nodes that
+ * coincide only in part give non-finite paths (SL_DEV_NONFINITE).
+ */
+int seven_league_cdc_simulate_batched(int model, const sl_net* net, const sl_net* marg_net,
+                                      const float* theta, int p, const float* Y0,
+                                      const int64_t* path_offsets, int n_sets, int64_t total_paths,
+                                      float T, int n_steps, int m, uint64_t seed, float* out_YT,
+                                      float* out_grid, double* out_mean, double* out_var, void* ws,
+                                      size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
  * Offline stage (Algorithm I, step 1).
  * ---------------------------------------------------------------------- */
 

@@ -42,7 +42,7 @@ EXPORTED = [
     "sl_tc_get_pipeline", "sl_train_workspace_size",
     "sl_mlp_forward", "sl_mse_grad", "sl_adam_step", "sl_train", "sl_adjoint_workspace_size",
     "seven_league_adjoint", "em_collocation_labels_noalloc", "sl_em_labels_noalloc_max_samples",
-    "sl_selftest_wait_timeout",
+    "sl_selftest_wait_timeout", "sl_cdc_workspace_size", "seven_league_cdc_simulate_batched",
 ]
 
 
@@ -109,6 +109,11 @@ def load(path: str = LIB_PATH):
     L.seven_league_adjoint.argtypes = [_i, ctypes.POINTER(sl_net), _vp, _i, _vp, _vp, _i, _i64, _f, _i, _i,
                                        _u64, _i, _f, _i, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
     L.sl_selftest_wait_timeout.argtypes = [_vp, _sz, _vp]
+    L.sl_cdc_workspace_size.argtypes = [_i64, _i, _i]
+    L.sl_cdc_workspace_size.restype = _sz
+    L.seven_league_cdc_simulate_batched.argtypes = [
+        _i, ctypes.POINTER(sl_net), ctypes.POINTER(sl_net), _vp, _i, _vp, _vp, _i, _i64, _f, _i, _i, _u64,
+        _vp, _vp, _vp, _vp, _vp, _sz, _vp]
     L.em_collocation_labels_noalloc.argtypes = [_i, _vp, _vp, _vp, _i, _i64, _i, _i, _u64, _vp, _vp]
     L.sl_em_labels_noalloc_max_samples.restype = _sz
     L.sl_tc_set_pipeline.argtypes = [_i]
@@ -270,6 +275,43 @@ def seven_league_simulate(model, theta, Y0, T, n_steps, m, weights, n_paths, see
                                    float(Y0), float(T), n_steps, m, netp, int(n_paths), seed,
                                    _ptr(out, torch.float32, "out"), _stream(stream)))
     return out
+
+
+CDC_TABLE_FLOATS = 192  # per (set, step): z | w | C | S_lo | S_hi | C_lo | C_hi | z_lo, z_hi | C[0] | Cw
+
+
+def cdc_workspace_size(total_paths, n_sets, n_steps):
+    return int(load().sl_cdc_workspace_size(total_paths, n_sets, n_steps))
+
+
+def seven_league_cdc_simulate_batched(model, net, theta, Y0, path_offsets, T, n_steps, m, seed,
+                                      marg_net=None, out_YT=None, out_grid=None, out_mean=None,
+                                      out_var=None, ws=None, total_paths=None, stream=None):
+    """Batched 7L-CDC sampler (see include/sevenleague.h); marg_net None = net.
+    Returns the workspace used (status word first, then the tables)."""
+    torch = _torch()
+    L = load()
+    n_sets = path_offsets.numel() - 1
+    p = theta.shape[1] if theta.dim() == 2 else theta.numel() // max(n_sets, 1)
+    if total_paths is None:
+        total_paths = int(path_offsets[-1].item())
+    if ws is None:
+        ws = _workspace(L.sl_cdc_workspace_size(total_paths, n_sets, n_steps), theta.device)
+    netp = ctypes.byref(net) if net is not None else None
+    mnetp = ctypes.byref(marg_net) if marg_net is not None else None
+    _check(L.seven_league_cdc_simulate_batched(
+        model, netp, mnetp, _ptr(theta, torch.float32, "theta"), p, _ptr(Y0, torch.float32, "Y0"),
+        _ptr(path_offsets, torch.int64, "path_offsets"), n_sets, int(total_paths), float(T),
+        n_steps, m, seed, _ptr(out_YT, torch.float32, "out_YT"),
+        _ptr(out_grid, torch.float32, "out_grid"), _ptr(out_mean, torch.float64, "out_mean"),
+        _ptr(out_var, torch.float64, "out_var"), _ptr(ws), ws.numel(), _stream(stream)))
+    return ws
+
+
+def cdc_tables(ws, n_sets, n_steps):
+    """View of the tables a 7L-CDC call left in its workspace: FP32 [n_sets, n_steps, 192]."""
+    n = n_sets * n_steps * CDC_TABLE_FLOATS
+    return ws[256:256 + 4 * n].view(_torch().float32).view(n_sets, n_steps, CDC_TABLE_FLOATS)
 
 
 def adjoint_workspace_size(total_paths, n_sets, n_steps, ckpt_k, p):

@@ -1,0 +1,562 @@
+// sl_cdc.cu -- the 7L-CDC online sampler: Algorithm I with the per-path network
+// of step 3 replaced by a global interpolation (the variant timed beside the 7L
+// scheme in Table 6.1).
+//
+// Reading: at t_i = i dt the marginal collocation points of Y are
+// z_k = G_k(Y0, t_i, theta) (the collocation map over the horizon t_i from the
+// deterministic start; G is the marginal network or the exact map), the
+// conditional points at those nodes are C[k][j] = H_j(z_k, dt, theta), and a path
+// at Y_i takes yhat_j = sum_k C[k][j] L_k(Y_i) (Lagrange in Y through the z_k)
+// inside the nodes' hull and the line through the two outermost nodes beyond it,
+// then Y_{i+1} = g_m(X) through (x_j, yhat_j).  At i = 0 (and whenever the nodes
+// coincide) every path sits at z_0 and yhat = C[0].
+//
+// Two phases.  (1) Tables: for every (set, step) the m + 1 network evaluations,
+// in FP32 on CUDA cores (weights staged in shared memory, one evaluation per
+// thread), plus the barycentric weights of the z_k in FP64; 768 bytes per
+// (set, step), with the continuation lines beyond the hull.  (2) Paths: one thread per path for the whole time loop, the
+// state and the normals in registers; the table of the path's (set, step) is
+// read through the L1 cache (the lanes of a warp share a set, so a load is one
+// broadcast).  Phase 2 has no network and no tensor-core work: per path-step it
+// is a Philox normal, two Lagrange bases of m nodes and an m x m contraction,
+// all FP32 ALU work.
+#include <math.h>
+
+#include "sl_check.cuh"
+#include "sl_internal.cuh"
+#include "sl_simt_net.cuh"
+
+namespace sl {
+namespace {
+
+using namespace simt;
+
+// Table of one (set, step), floats: z[8] | w[8] | C[8][8] | S_lo[8] | S_hi[8] |
+// C_lo[8] | C_hi[8] | z_lo, z_hi, pad | C[0] | Cw[8][8].  Below the smallest node z_lo
+// the points are C_lo + (Y - z_lo) S_lo (the line through the two smallest nodes),
+// above z_hi likewise with the two largest.  Cw[k][j] = w_k b_j C[k][j] (b_j the
+// barycentric weights of the Gauss-Hermite points) folds both interpolations'
+// weights into the table: inside the hull
+//   Y_{i+1} = sum_k P_k(Y) sum_j Cw[k][j] Q_j(X),
+// P_k(Y) = prod_{l!=k} (Y - z_l), Q_j(X) = prod_{l!=j} (X - x_l).
+constexpr int kTabFloats = 192;
+constexpr int kSlo = 80, kShi = 88, kClo = 96, kChi = 104, kZlo = 112, kRow0 = 120, kCw = 128;
+constexpr int kTabThreads = 128;
+constexpr int kPathThreads = 256;
+
+struct CdcArgs {
+    const float* params;       // conditional network (FP32) or NULL (exact models)
+    const float* mparams;      // marginal network
+    int d_in, act, mact;
+    const float* theta;
+    int p;
+    const float* Y0;
+    int n_sets;
+    int n_steps;
+    float dt;
+    int m;
+    float* tab;                // [n_sets][n_steps][kTabFloats]
+    GHConst gh;
+};
+
+// Collocation points of the exact models over the horizon h from Y:
+// GBM y_j = Y exp((mu - sigma^2/2) h + sigma sqrt(h) x_j); OU (Eq. 6.6) restarted at Y.
+template <int MODEL>
+__device__ __forceinline__ void exact_map(const float* th, float Y, float h, const GHConst& gh, int m,
+                                          float (&y)[SL_MAX_M]) {
+    if (MODEL == SL_MODEL_GBM_EXACT) {
+        const float mu = __ldg(th), sg = __ldg(th + 1);
+        const float am = (mu - 0.5f * sg * sg) * h, bm = sg * sqrtf(h);
+#pragma unroll
+        for (int j = 0; j < SL_MAX_M; ++j) y[j] = (j < m) ? Y * expf(fmaf(bm, gh.x[j], am)) : 0.0f;
+    } else {
+        const float yb = __ldg(th), sg = __ldg(th + 1), lam = __ldg(th + 2);
+        const float c1 = expf(-lam * h);
+        const float sd = sg * sqrtf(-expm1f(-2.0f * lam * h) / (2.0f * lam));
+        const float c0 = yb * (-expm1f(-lam * h));
+#pragma unroll
+        for (int j = 0; j < SL_MAX_M; ++j) y[j] = (j < m) ? fmaf(sd, gh.x[j], fmaf(c1, Y, c0)) : 0.0f;
+    }
+}
+
+template <int MODEL, int ACT>
+__device__ __forceinline__ void eval_map(const SmemNet& net, float* act, const float* th, int p, float Y,
+                                         float h, const GHConst& gh, int m, float (&y)[SL_MAX_M]) {
+    if (MODEL == SL_MODEL_MLP) {
+        float f[DS];
+#pragma unroll
+        for (int k = 0; k < DS; ++k) f[k] = 0.0f;
+        f[0] = Y;
+        f[1] = h;
+        for (int k = 0; k < p && k < DS - 2; ++k) f[2 + k] = __ldg(th + k);
+        mlp_forward<ACT>(net, act, blockDim.x, f, y);
+#pragma unroll
+        for (int j = 0; j < SL_MAX_M; ++j)
+            if (j >= m) y[j] = 0.0f;
+    } else {
+        exact_map<MODEL>(th, Y, h, gh, m, y);
+    }
+}
+
+// Phase 1a: marginal nodes z and their barycentric weights w (FP64 products of
+// the FP32 node differences, rounded once); w = 0 marks coinciding nodes.
+template <int MODEL, int ACT>
+__global__ void __launch_bounds__(kTabThreads) cdc_marginal_kernel(const CdcArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemNet& net = *reinterpret_cast<SmemNet*>(smem_raw);
+    float* act = reinterpret_cast<float*>(smem_raw + sizeof(SmemNet)) + threadIdx.x;
+    if (MODEL == SL_MODEL_MLP) {
+        stage_net(net, a.mparams, a.d_in, a.m);
+        __syncthreads();
+    }
+    const int m = a.m;
+    const int64_t n = static_cast<int64_t>(a.n_sets) * a.n_steps;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    // no barrier inside the loop: mlp_forward touches only this thread's column of `act`
+    for (int64_t u = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; u < n; u += stride) {
+        const int s = static_cast<int>(u / a.n_steps), i = static_cast<int>(u % a.n_steps);
+        const float y0 = __ldg(a.Y0 + s);
+        float z[SL_MAX_M];
+        if (i == 0) {
+#pragma unroll
+            for (int k = 0; k < SL_MAX_M; ++k) z[k] = (k < m) ? y0 : 0.0f;
+        } else {
+            eval_map<MODEL, ACT>(net, act, a.theta + static_cast<int64_t>(s) * a.p, a.p, y0,
+                                 static_cast<float>(i) * a.dt, a.gh, m, z);
+        }
+        bool same = true;
+        for (int k = 1; k < m; ++k) same = same && (z[k] == z[0]);
+        float* t = a.tab + u * kTabFloats;
+#pragma unroll
+        for (int k = 0; k < SL_MAX_M; ++k) {
+            double prod = 1.0;
+            for (int l = 0; l < m; ++l)
+                if (l != k) prod *= static_cast<double>(z[k]) - static_cast<double>(z[l]);
+            t[k] = z[k];
+            t[8 + k] = (k < m && !same) ? static_cast<float>(1.0 / prod) : 0.0f;
+        }
+    }
+}
+
+// Phase 1b: conditional points C[k][j] = H_j(z_k, dt, theta) (rows k >= m zero).
+template <int MODEL, int ACT>
+__global__ void __launch_bounds__(kTabThreads) cdc_conditional_kernel(const CdcArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemNet& net = *reinterpret_cast<SmemNet*>(smem_raw);
+    float* act = reinterpret_cast<float*>(smem_raw + sizeof(SmemNet)) + threadIdx.x;
+    if (MODEL == SL_MODEL_MLP) {
+        stage_net(net, a.params, a.d_in, a.m);
+        __syncthreads();
+    }
+    const int m = a.m;
+    const int64_t n = static_cast<int64_t>(a.n_sets) * a.n_steps * SL_MAX_M;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int64_t u = v / SL_MAX_M;
+        const int k = static_cast<int>(v % SL_MAX_M);
+        const int s = static_cast<int>(u / a.n_steps);
+        float* t = a.tab + u * kTabFloats;
+        float y[SL_MAX_M];
+        if (k < m) {
+            eval_map<MODEL, ACT>(net, act, a.theta + static_cast<int64_t>(s) * a.p, a.p, t[k], a.dt, a.gh,
+                                 m, y);
+        } else {
+#pragma unroll
+            for (int j = 0; j < SL_MAX_M; ++j) y[j] = 0.0f;
+        }
+        float4* row = reinterpret_cast<float4*>(t + 16 + k * 8);
+        row[0] = make_float4(y[0], y[1], y[2], y[3]);
+        row[1] = make_float4(y[4], y[5], y[6], y[7]);
+    }
+}
+
+// Phase 1c: the continuation lines beyond the outermost nodes.  The two smallest
+// (largest) nodes, ties to the lower index; slopes (C[b][j] - C[a][j]) / (z_b - z_a)
+// in FP64 from the FP32 entries, rounded once (0 where the two nodes coincide: the
+// table is then degenerate, w = 0, or already non-finite through w).
+__global__ void __launch_bounds__(kTabThreads) cdc_edge_kernel(float* __restrict__ tab, int64_t n, int m,
+                                                                const GHConst gh) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t u = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; u < n; u += stride) {
+        float* t = tab + u * kTabFloats;
+        int lo = 0, hi = 0;
+        for (int k = 1; k < m; ++k) {
+            if (t[k] < t[lo]) lo = k;
+            if (t[k] > t[hi]) hi = k;
+        }
+        int lo2 = -1, hi2 = -1;
+        for (int k = 0; k < m; ++k) {
+            if (k != lo && (lo2 < 0 || t[k] < t[lo2])) lo2 = k;
+            if (k != hi && (hi2 < 0 || t[k] > t[hi2])) hi2 = k;
+        }
+        const double dlo = static_cast<double>(t[lo2]) - t[lo], dhi = static_cast<double>(t[hi2]) - t[hi];
+        for (int j = 0; j < SL_MAX_M; ++j) {
+            const float clo = t[16 + lo * 8 + j], chi = t[16 + hi * 8 + j];
+            t[kClo + j] = clo;
+            t[kChi + j] = chi;
+            t[kSlo + j] = (j < m && dlo != 0.0)
+                              ? static_cast<float>((static_cast<double>(t[16 + lo2 * 8 + j]) - clo) / dlo) : 0.0f;
+            t[kShi + j] = (j < m && dhi != 0.0)
+                              ? static_cast<float>((static_cast<double>(t[16 + hi2 * 8 + j]) - chi) / dhi) : 0.0f;
+        }
+        t[kZlo] = t[lo];
+        t[kZlo + 1] = t[hi];
+        for (int k = kZlo + 2; k < kRow0; ++k) t[k] = 0.0f;
+        for (int j = 0; j < SL_MAX_M; ++j) t[kRow0 + j] = t[16 + j];
+        // Cw[k][j] = w_k b_j C[k][j]: w_k again in FP64 from the FP32 nodes (0 when the
+        // nodes coincide, like the stored w)
+        const bool live = t[8] != 0.0f;
+        for (int k = 0; k < SL_MAX_M; ++k) {
+            double wk = 0.0;
+            if (live && k < m) {
+                double prod = 1.0;
+                for (int l = 0; l < m; ++l)
+                    if (l != k) prod *= static_cast<double>(t[k]) - static_cast<double>(t[l]);
+                wk = 1.0 / prod;
+            }
+            for (int j = 0; j < SL_MAX_M; ++j)
+                t[kCw + 8 * k + j] = (j < m) ? static_cast<float>(wk * gh.bary[j] * t[16 + 8 * k + j]) : 0.0f;
+        }
+    }
+}
+
+// P_k(X) = prod_{l != k} (X - n_l) for k < M (prefix and suffix products).
+template <int M>
+__device__ __forceinline__ void prod_except(float X, const float (&nd)[8], float (&P)[M]) {
+    float d[M], pre[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) d[k] = X - nd[k];
+    pre[0] = 1.0f;
+#pragma unroll
+    for (int k = 1; k < M; ++k) pre[k] = pre[k - 1] * d[k - 1];
+    float suf = 1.0f;
+#pragma unroll
+    for (int k = M - 1; k >= 0; --k) {
+        P[k] = pre[k] * suf;
+        suf *= d[k];
+    }
+}
+
+__device__ __forceinline__ void load8(const float* p, float (&v)[8]) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+    const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
+// One step of NP paths of the same (set, step) table t: Y[p] <- g_m(X[p]) through the
+// conditional points at Y[p].  The table is loaded once for all NP paths.
+template <int M, int NP>
+__device__ __forceinline__ void cdc_step(const float* __restrict__ t, float (&Y)[NP], const float (&X)[NP],
+                                         const float (&gx)[8], const float (&gb)[8]) {
+    float Q[NP][M];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) prod_except<M>(X[p], gx, Q[p]);
+    const float4 w4 = __ldg(reinterpret_cast<const float4*>(t + 8));
+    const float2 edge = __ldg(reinterpret_cast<const float2*>(t + kZlo));
+    float row[8];
+    if (w4.x == 0.0f) {                      // coinciding nodes: every path at z_0
+        load8(t + kRow0, row);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            float y = 0.0f;
+#pragma unroll
+            for (int j = 0; j < M; ++j) y = fmaf(row[j] * gb[j], Q[p][j], y);
+            Y[p] = y;
+        }
+        return;
+    }
+    bool out[NP];
+    bool any_out = false;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        out[p] = Y[p] < edge.x || Y[p] > edge.y;
+        any_out = any_out || out[p];
+    }
+    float zn[8];
+    load8(t, zn);
+    float P[NP][M], acc[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        prod_except<M>(Y[p], zn, P[p]);
+        acc[p] = 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        load8(t + kCw + 8 * k, row);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            float v = 0.0f;
+#pragma unroll
+            for (int j = 0; j < M; ++j) v = fmaf(row[j], Q[p][j], v);
+            acc[p] = fmaf(P[p][k], v, acc[p]);
+        }
+    }
+    float ynew[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) ynew[p] = acc[p];
+    if (any_out) {                           // beyond the hull: the outer line
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            if (!out[p]) continue;
+            const bool below = Y[p] < edge.x;
+            float sl[8];
+            load8(t + (below ? kClo : kChi), row);
+            load8(t + (below ? kSlo : kShi), sl);
+            const float dY = Y[p] - (below ? edge.x : edge.y);
+            float y = 0.0f;
+#pragma unroll
+            for (int j = 0; j < M; ++j) y = fmaf(fmaf(dY, sl[j], row[j]) * gb[j], Q[p][j], y);
+            ynew[p] = y;
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) Y[p] = ynew[p];
+}
+
+// The whole time loop of NP paths of one set s (path indices q[p] within the set, flat
+// indices g[p]; write[p] false for a padding lane).
+template <int M, int NP>
+__device__ __forceinline__ void cdc_paths(const SimArgs& a, const float* __restrict__ ts, int s,
+                                          const int64_t (&q)[NP], const int64_t (&g)[NP], const bool (&write)[NP],
+                                          const float (&gx)[8], const float (&gb)[8]) {
+    float Y[NP], X[NP];
+    float4 z4[NP];
+    const float y0 = __ldg(a.Y0 + s);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        Y[p] = y0;
+        if (a.out_grid && write[p]) a.out_grid[g[p]] = y0;
+    }
+    for (int i = 0; i < a.n_steps; ++i) {
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            if ((i & 3) == 0)
+                z4[p] = normal4(a.seed, 0u, static_cast<uint32_t>(s), static_cast<uint32_t>(q[p]),
+                                static_cast<uint32_t>(i >> 2));
+            X[p] = pick4(z4[p], i & 3);
+        }
+        cdc_step<M, NP>(ts + static_cast<int64_t>(i) * kTabFloats, Y, X, gx, gb);
+        if (a.out_grid) {
+#pragma unroll
+            for (int p = 0; p < NP; ++p)
+                if (write[p]) a.out_grid[static_cast<int64_t>(i + 1) * a.total + g[p]] = Y[p];
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        if (!write[p]) continue;
+        if (a.out_YT) a.out_YT[g[p]] = Y[p];
+        if (!isfinite(Y[p])) raise_status(a.status, SL_DEV_NONFINITE);
+    }
+}
+
+// Phase 2: the paths.  Each thread takes kPair neighbouring flat paths; when they
+// belong to one set (all but the pairs that straddle a set boundary) they share the
+// table loads of every step.
+constexpr int kPair = 2;
+
+template <int M>
+__global__ void __launch_bounds__(kPathThreads) cdc_path_kernel(const SimArgs a, const float* __restrict__ tab) {
+    float gx[8], gb[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        gx[j] = j < M ? a.gh.x[j] : 0.0f;
+        gb[j] = j < M ? a.gh.bary[j] : 0.0f;
+    }
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x * kPair;
+    for (int64_t g0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) * kPair; g0 < a.total;
+         g0 += stride) {
+        int s[kPair];
+        int64_t q[kPair], g[kPair];
+        bool write[kPair];
+        bool same = true;
+#pragma unroll
+        for (int p = 0; p < kPair; ++p) {
+            write[p] = g0 + p < a.total;
+            g[p] = write[p] ? g0 + p : g0;
+            s[p] = a.offsets ? owning_set(a.offsets, a.n_sets, g[p]) : 0;
+            q[p] = a.offsets ? g[p] - __ldg(a.offsets + s[p]) : g[p];
+            same = same && s[p] == s[0];
+        }
+        if (same) {
+            cdc_paths<M, kPair>(a, tab + static_cast<int64_t>(s[0]) * a.n_steps * kTabFloats, s[0], q, g, write,
+                                gx, gb);
+        } else {
+#pragma unroll
+            for (int p = 0; p < kPair; ++p) {
+                const int64_t q1[1] = {q[p]}, g1[1] = {g[p]};
+                const bool w1[1] = {write[p]};
+                cdc_paths<M, 1>(a, tab + static_cast<int64_t>(s[p]) * a.n_steps * kTabFloats, s[p], q1, g1, w1,
+                                gx, gb);
+            }
+        }
+    }
+}
+
+template <int MODEL, int ACT>
+int launch_tables(const CdcArgs& c, int mact, cudaStream_t st) {
+    const size_t smem = (MODEL == SL_MODEL_MLP)
+                            ? sizeof(SmemNet) + static_cast<size_t>(W) * kTabThreads * sizeof(float)
+                            : 0;
+    const int64_t n1 = static_cast<int64_t>(c.n_sets) * c.n_steps;
+    const int64_t cap = static_cast<int64_t>(sm_count()) * 8;
+    auto blocks = [&](int64_t n) {
+        int64_t b = (n + kTabThreads - 1) / kTabThreads;
+        return static_cast<unsigned>(b < 1 ? 1 : (b > cap ? cap : b));
+    };
+    // the marginal network may use another activation than the conditional one
+    auto km = (mact == SL_ACT_SOFTPLUS) ? cdc_marginal_kernel<MODEL, SL_ACT_SOFTPLUS>
+                                        : cdc_marginal_kernel<MODEL, SL_ACT_RELU>;
+    auto kc = cdc_conditional_kernel<MODEL, ACT>;
+    int rc = cuda_error(cudaFuncSetAttribute(km, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
+                        "cdc_marginal attribute");
+    if (rc) return rc;
+    rc = cuda_error(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
+                    "cdc_conditional attribute");
+    if (rc) return rc;
+    km<<<blocks(n1), kTabThreads, smem, st>>>(c);
+    rc = cuda_error(cudaGetLastError(), "cdc_marginal launch");
+    if (rc) return rc;
+    kc<<<blocks(n1 * SL_MAX_M), kTabThreads, smem, st>>>(c);
+    rc = cuda_error(cudaGetLastError(), "cdc_conditional launch");
+    if (rc) return rc;
+    cdc_edge_kernel<<<blocks(n1), kTabThreads, 0, st>>>(c.tab, n1, c.m, c.gh);
+    return cuda_error(cudaGetLastError(), "cdc_edge launch");
+}
+
+template <int M>
+int launch_paths_m(const SimArgs& a, const float* tab, cudaStream_t st) {
+    auto kern = cdc_path_kernel<M>;
+    int per_sm = 0;
+    int rc = cuda_error(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPathThreads, 0),
+                        "cdc_path occupancy");
+    if (rc) return rc;
+    const int64_t need = (a.total + static_cast<int64_t>(kPathThreads) * kPair - 1) / (static_cast<int64_t>(kPathThreads) * kPair);
+    int64_t blocks = static_cast<int64_t>(sm_count()) * (per_sm > 0 ? per_sm : 1);
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    kern<<<static_cast<unsigned>(blocks), kPathThreads, 0, st>>>(a, tab);
+    return cuda_error(cudaGetLastError(), "cdc_path launch");
+}
+
+int launch_paths(const SimArgs& a, const float* tab, cudaStream_t st) {
+    switch (a.m) {
+        case 2: return launch_paths_m<2>(a, tab, st);
+        case 3: return launch_paths_m<3>(a, tab, st);
+        case 4: return launch_paths_m<4>(a, tab, st);
+        case 5: return launch_paths_m<5>(a, tab, st);
+        case 6: return launch_paths_m<6>(a, tab, st);
+        case 7: return launch_paths_m<7>(a, tab, st);
+        default: return launch_paths_m<8>(a, tab, st);
+    }
+}
+
+size_t table_bytes(int n_sets, int n_steps) {
+    return align256(static_cast<size_t>(n_sets) * static_cast<size_t>(n_steps) * kTabFloats * sizeof(float));
+}
+
+}  // namespace
+}  // namespace sl
+
+using namespace sl;
+
+extern "C" {
+
+size_t sl_cdc_workspace_size(int64_t total_paths, int n_sets, int n_steps) {
+    if (total_paths < 0) total_paths = 0;
+    if (n_sets < 1) n_sets = 1;
+    if (n_steps < 1) n_steps = 1;
+    return kStatusBytes + table_bytes(n_sets, n_steps) +
+           align256(static_cast<size_t>(total_paths) * sizeof(float)) + set_moments_scratch_bytes(n_sets);
+}
+
+int seven_league_cdc_simulate_batched(int model, const sl_net* net, const sl_net* marg_net,
+                                      const float* theta, int p, const float* Y0,
+                                      const int64_t* path_offsets, int n_sets, int64_t total_paths,
+                                      float T, int n_steps, int m, uint64_t seed, float* out_YT,
+                                      float* out_grid, double* out_mean, double* out_var, void* ws,
+                                      size_t ws_bytes, void* stream) {
+    int rc = check_common(model, net, theta, p, T, n_steps, m);
+    if (rc) return rc;
+    if (model == SL_MODEL_MLP && marg_net) {
+        rc = check_net(marg_net, m, p);
+        if (rc) return rc;
+    }
+    if (n_sets < 1 || n_sets > SL_MAX_SETS) return set_error(SL_ERR_ARG, "n_sets=%d", n_sets);
+    if (total_paths < 0) return set_error(SL_ERR_ARG, "total_paths < 0");
+    if (total_paths > (int64_t(1) << 40)) return set_error(SL_ERR_UNSUPPORTED, "total_paths too large");
+    if (!Y0 || !path_offsets) return set_error(SL_ERR_ARG, "Y0 / path_offsets == NULL");
+    if (!out_YT && !out_grid && !out_mean && !out_var) return set_error(SL_ERR_ARG, "no output requested");
+    if (!ws) return set_error(SL_ERR_WORKSPACE, "ws == NULL");
+    const bool moments = out_mean || out_var;
+    const size_t tbytes = table_bytes(n_sets, n_steps);
+    const size_t need = kStatusBytes + tbytes +
+                        ((moments && !out_YT) ? align256(static_cast<size_t>(total_paths) * 4) : 0) +
+                        (moments ? set_moments_scratch_bytes(n_sets) : 0);
+    if (ws_bytes < need) return set_error(SL_ERR_WORKSPACE, "workspace %zu bytes < %zu required", ws_bytes, need);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned char* w = static_cast<unsigned char*>(ws);
+    unsigned* status = reinterpret_cast<unsigned*>(w);
+    size_t off = kStatusBytes;
+    float* tab = reinterpret_cast<float*>(w + off);
+    off += tbytes;
+    float* yt = out_YT;
+    if (moments && !out_YT) {
+        yt = reinterpret_cast<float*>(w + off);
+        off += align256(static_cast<size_t>(total_paths) * 4);
+    }
+    void* part = w + off;
+
+    CdcArgs c{};
+    const sl_net* mn = (model == SL_MODEL_MLP) ? (marg_net ? marg_net : net) : nullptr;
+    if (model == SL_MODEL_MLP) {
+        c.params = net->params;
+        c.mparams = mn->params;
+        c.d_in = net->d_in;
+        c.act = net->act;
+        c.mact = mn->act;
+    }
+    c.theta = theta;
+    c.p = p;
+    c.Y0 = Y0;
+    c.n_sets = n_sets;
+    c.n_steps = n_steps;
+    c.dt = T / static_cast<float>(n_steps);
+    c.m = m;
+    c.tab = tab;
+    rc = make_gh_const(m, &c.gh);
+    if (rc) return rc;
+
+    SimArgs a{};
+    a.theta = theta;
+    a.p = p;
+    a.Y0 = Y0;
+    a.offsets = path_offsets;
+    a.n_sets = n_sets;
+    a.total = total_paths;
+    a.dt = c.dt;
+    a.n_steps = n_steps;
+    a.seed = seed;
+    a.out_YT = yt;
+    a.out_grid = out_grid;
+    a.status = status;
+    a.m = m;
+    a.gh = c.gh;
+
+    rc = cuda_error(cudaMemsetAsync(status, 0, kStatusBytes, st), "status clear");
+    if (rc) return rc;
+    if (model == SL_MODEL_GBM_EXACT) rc = launch_tables<SL_MODEL_GBM_EXACT, 0>(c, 0, st);
+    else if (model == SL_MODEL_OU_EXACT) rc = launch_tables<SL_MODEL_OU_EXACT, 0>(c, 0, st);
+    else if (c.act == SL_ACT_SOFTPLUS) rc = launch_tables<SL_MODEL_MLP, SL_ACT_SOFTPLUS>(c, c.mact, st);
+    else rc = launch_tables<SL_MODEL_MLP, SL_ACT_RELU>(c, c.mact, st);
+    if (rc) return rc;
+    if (total_paths > 0) {
+        rc = launch_paths(a, tab, st);
+        if (rc) return rc;
+    }
+    if (moments) return launch_set_moments(yt, path_offsets, n_sets, total_paths, out_mean, out_var, part, st);
+    return SL_OK;
+}
+
+}  // extern "C"

@@ -17,41 +17,6 @@ namespace {
 
 using namespace simt;
 
-// The network H: features f -> collocation points y (Eq. 6.4).  The inputs of
-// a layer live in registers; its outputs go to the thread's column of `act`
-// (element k at act[k * nt], conflict-free across a warp) and are reloaded as
-// the next layer's inputs.
-template <int ACT>
-__device__ __forceinline__ void mlp_forward(const SmemNet& s, float* act, int nt,
-                                            const float (&f)[DS], float (&y)[SL_MAX_M]) {
-#pragma unroll 2
-    for (int o = 0; o < W; ++o) {
-        const float4 a = *reinterpret_cast<const float4*>(s.W1 + o * DS);
-        const float4 b = *reinterpret_cast<const float4*>(s.W1 + o * DS + 4);
-        float acc = s.b1[o];
-        acc = fmaf(a.x, f[0], acc);
-        acc = fmaf(a.y, f[1], acc);
-        acc = fmaf(a.z, f[2], acc);
-        acc = fmaf(a.w, f[3], acc);
-        acc = fmaf(b.x, f[4], acc);
-        acc = fmaf(b.y, f[5], acc);
-        acc = fmaf(b.z, f[6], acc);
-        acc = fmaf(b.w, f[7], acc);
-        act[o * nt] = activation<ACT>(acc);
-    }
-    float h[W];
-    for (int l = 0; l < 3; ++l) {
-#pragma unroll
-        for (int k = 0; k < W; ++k) h[k] = act[k * nt];
-#pragma unroll 2
-        for (int o = 0; o < W; ++o) act[o * nt] = activation<ACT>(dot50(s.Wh[l] + o * WS, h, s.bh[l][o]));
-    }
-#pragma unroll
-    for (int k = 0; k < W; ++k) h[k] = act[k * nt];
-#pragma unroll
-    for (int o = 0; o < SL_MAX_M; ++o) y[o] = dot50(s.W5 + o * WS, h, s.b5[o]);
-}
-
 // MODEL: SL_MODEL_MLP / GBM_EXACT / OU_EXACT.
 template <int MODEL, int ACT>
 __global__ void __launch_bounds__(256) simt_7l_kernel(const SimArgs a) {

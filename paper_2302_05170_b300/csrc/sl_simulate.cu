@@ -3,11 +3,12 @@
 // form or the BF16 tcgen05 form, and the FP64 per-set moments.
 #include <math.h>
 
+#include "sl_check.cuh"
 #include "sl_internal.cuh"
 
 using namespace sl;
 
-namespace {
+namespace sl {
 
 int model_p(int model) { return model == SL_MODEL_GBM_EXACT ? 2 : 3; }
 
@@ -42,6 +43,10 @@ int check_common(int model, const sl_net* net, const float* theta, int p, float 
         return set_error(SL_ERR_ARG, "model %d needs p=%d, got %d", model, model_p(model), p);
     return SL_OK;
 }
+
+}  // namespace sl
+
+namespace {
 
 int dispatch(int model, const sl_net* net, int m, const SimArgs& a, cudaStream_t st) {
     if (model == SL_MODEL_MLP && net->prec == SL_PREC_BF16) return launch_tc_7l(m, a, st);

@@ -58,6 +58,40 @@ def xavier_params(d_in: int, m: int, seed: int = 0, width: int = WIDTH,
     return np.concatenate(parts).astype(np.float32)
 
 
+def near_affine_params(d_in: int, m: int, a: float = 0.2, b: float = 0.3, eps: float = 0.02,
+                       seed: int = 0, shift: float = 1.5) -> np.ndarray:
+    """A network whose outputs look like collocation points, for the 7L-CDC variant (whose
+    marginal points an untrained network leaves unordered or nearly coincident).
+
+    Before the perturbation it computes y_j = Y + x_j (a + b dt) exactly (x_j the ascending
+    Gauss-Hermite points of N(0,1), from numpy) while every feature exceeds -shift: hidden
+    units u < d_in carry feature u + shift through every layer (on the linear side of the
+    ReLU), the other units are zero, and the output layer undoes the shift.  A small shift
+    keeps the output from being a difference of large terms (FP32 evaluations stay accurate).  Then eps times Xavier-uniform
+    weights (seed) are added to every weight, so some units switch and the map is no
+    longer affine.
+    """
+    from numpy.polynomial import hermite_e
+
+    x = hermite_e.hermegauss(m)[0]
+    parts = []
+    for li, (fo, fi) in enumerate(layer_shapes(d_in, m)):
+        Wl = np.zeros((fo, fi))
+        bl = np.zeros(fo)
+        if li < N_HIDDEN:
+            for u in range(d_in):
+                Wl[u, u] = 1.0
+            if li == 0:
+                bl[:d_in] = shift
+        else:
+            Wl[:, 0] = 1.0
+            Wl[:, 1] = b * x
+            bl[:] = a * x - shift * (1.0 + b * x)
+        parts += [Wl.ravel(), bl]
+    P = np.concatenate(parts)
+    return (P + eps * xavier_params(d_in, m, seed=seed).astype(np.float64)).astype(np.float32)
+
+
 def split_params(P: np.ndarray, d_in: int, m: int, width: int = WIDTH, n_hidden: int = N_HIDDEN):
     """Views [(W, b), ...] of a flat parameter array."""
     out, o = [], 0

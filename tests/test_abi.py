@@ -153,6 +153,43 @@ def test_host_argument_checks(lib):
     assert L.sl_segmented_select(fake, fake, 3, neg, 2, fake, fake, 256, None) == sl.SL_ERR_ARG
 
 
+def test_cdc_argument_checks(lib):
+    L = lib
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: every call below is rejected first
+    net = sl.sl_net(0x1000, 3, 5, sl.ACT_RELU, sl.PREC_FP32)
+    base = dict(model=sl.MODEL_MLP, net=ctypes.byref(net), mnet=None, theta=fake, p=1, Y0=fake, off=fake,
+                n_sets=1, total=10, T=1.0, n_steps=2, m=5, seed=1, yt=fake, grid=None, mean=None,
+                var=None, ws=fake, ws_bytes=256, stream=None)
+
+    def call(**kw):
+        a = dict(base, **kw)
+        return L.seven_league_cdc_simulate_batched(
+            a["model"], a["net"], a["mnet"], a["theta"], a["p"], a["Y0"], a["off"], a["n_sets"], a["total"],
+            a["T"], a["n_steps"], a["m"], a["seed"], a["yt"], a["grid"], a["mean"], a["var"], a["ws"],
+            a["ws_bytes"], a["stream"])
+    need = sl.cdc_workspace_size(10, 1, 2)
+    assert need >= 256 + 2 * 192 * 4
+    assert call() == sl.SL_ERR_WORKSPACE                        # 256 bytes hold no tables
+    assert call(m=9) == sl.SL_ERR_UNSUPPORTED
+    assert call(n_steps=0) == sl.SL_ERR_UNSUPPORTED
+    assert call(T=0.0) == sl.SL_ERR_ARG
+    assert call(net=None) == sl.SL_ERR_ARG
+    assert call(p=2) == sl.SL_ERR_ARG
+    bad = sl.sl_net(0x1000, 3, 7, sl.ACT_RELU, sl.PREC_FP32)   # marginal network of another m
+    assert call(mnet=ctypes.byref(bad)) == sl.SL_ERR_ARG
+    bad_act = sl.sl_net(0x1000, 3, 5, 5, sl.PREC_FP32)
+    assert call(mnet=ctypes.byref(bad_act)) == sl.SL_ERR_ARG
+    assert call(Y0=None) == sl.SL_ERR_ARG
+    assert call(off=None) == sl.SL_ERR_ARG
+    assert call(n_sets=0) == sl.SL_ERR_ARG
+    assert call(yt=None) == sl.SL_ERR_ARG
+    assert call(ws=None) == sl.SL_ERR_WORKSPACE
+    assert call(model=sl.MODEL_GBM_EXACT, net=None, p=3) == sl.SL_ERR_ARG
+    # with out_YT given the call needs the status word and the tables: 256 + align256(2 * 768)
+    assert call(model=sl.MODEL_OU_EXACT, net=None, p=3, ws_bytes=1791) == sl.SL_ERR_WORKSPACE
+    assert sl.cdc_workspace_size(10 ** 6, 16, 16) >= 256 + 16 * 16 * 768 + 4 * 10 ** 6
+
+
 def test_workspace_sizes(lib):
     assert sl.simulate_workspace_size(0, 1) >= 256
     assert sl.simulate_workspace_size(10 ** 6, 16) >= 256 + 4 * 10 ** 6
