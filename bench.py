@@ -34,6 +34,10 @@ METRIC = "path-steps/s (7L online, BF16-TC vs FP32) at <=2e-3 rel err; EM label 
 UNIT = "path-steps/s"
 WORKLOAD = "GBM 7L online: 16 theta x 1e6 paths x 16 coarse steps, m=7, MLP 4->50x4->7 ReLU"
 ALG_FLOPS_PER_PATH_STEP = 2 * (4 * 50 + 3 * 50 * 50 + 50 * 7)   # 16,100 (biases excluded)
+# 7L-CDC, m = 7, per path-step inside the marginal hull: two products-except-one of m differences
+# (m subtractions + 3m - 2 multiplications each), the m x m contraction and the final dot
+# (FMA = 2 flops); the normal draw is not counted
+CDC_FLOPS_PER_PATH_STEP = 2 * (7 + 3 * 7 - 2) + 2 * 7 * 7 + 2 * 7     # 164
 
 # DRAM traffic of the sampler kernel on the default workload, from the committed ncu summary;
 # used only while the kernel's sources are those the counters were taken on.
@@ -397,6 +401,42 @@ def main():
             torch.cuda.synchronize()
             secondary["softplus_bf16_path_steps_per_s"] = path_steps / (e0.elapsed_time(e1) / 3 * 1e-3)
             del yt_sp
+        # the 7L-CDC variant on the same paths (Table 6.1's second scheme): the network only at the
+        # marginal collocation points of each (set, step), an interpolation in Y per path.  With a
+        # network: workloads.near_affine_params (outputs shaped like collocation points; an
+        # untrained Xavier network's marginal points are unordered); with the exact GBM map.
+        P_cdc = torch.as_tensor(W.near_affine_params(4, 7, seed=0), device=dev)
+        net_cdc = sl.make_net(P_cdc, 4, 7)
+        ws_cdc = torch.empty(sl.cdc_workspace_size(total, 16, n_steps), dtype=torch.uint8, device=dev)
+        yt_c = torch.empty_like(yt)
+        mean_c = torch.empty_like(mean)
+        for model_c, key in ((sl.MODEL_MLP, "cdc"), (sl.MODEL_GBM_EXACT, "cdc_gbm_exact")):
+            net_c = net_cdc if model_c == sl.MODEL_MLP else None
+            run_c = lambda: sl.seven_league_cdc_simulate_batched(model_c, net_c, theta, Y0, off, T, n_steps, m, seed,
+                                                                 out_YT=yt_c, out_mean=mean_c, ws=ws_cdc,
+                                                                 total_paths=total)
+            run_c()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(5):
+                run_c()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if sl.workspace_status(ws_cdc) != 0:
+                secondary[key + "_error"] = "device status %d" % sl.workspace_status(ws_cdc)
+                continue
+            c_rate = path_steps / (e0.elapsed_time(e1) / 5 * 1e-3)
+            secondary[key + "_path_steps_per_s"] = c_rate
+            if model_c == sl.MODEL_MLP:
+                sms = torch.cuda.get_device_properties(dev).multi_processor_count
+                fp32_peak = sms * 128 * 2 * peaks["sm_max_mhz"] * 1e6
+                secondary["cdc_fp32_roofline_frac"] = CDC_FLOPS_PER_PATH_STEP * c_rate / fp32_peak
+                secondary["cdc_over_7l_bf16"] = c_rate / value
+        secondary["cdc_workload"] = ("7L-CDC on the GBM workload above (16 sets x %d paths x %d steps, m=7); tables "
+                                     "of (m+1) network evaluations per (set, step), then 2 paths per thread"
+                                     % (args.paths, n_steps))
+        del yt_c, ws_cdc
         # offline stage: EM label samples/s on the CIR labels workload
         th, yi, dtr = W.cir_label_rows(1024)
         thd, yid, dtd = (torch.as_tensor(a, device=dev) for a in (th, yi, dtr))
@@ -507,20 +547,29 @@ def main():
                                           % (v_c.item(), d0_c.item(), [round(x, 5) for x in dth_c[0].tolist()]))
         secondary["cir_adjoint_workload"] = ("CIR network (BF16 tcgen05), kappa=1 ybar=0.1 gamma=0.3 Y0=0.1, "
                                              "1e6 paths x 64 steps of dt=0.25, checkpoint every 8")
-        # the paper's own experiment (Table 6.1's path counts): OU, m = 5, trained network;
-        # time per 7L run of 16 steps (T = 2) in both forms, and the pathwise error at 2e5 paths
-        # against Eq. (6.6) on the same normals (exact-collocation OU model)
-        P_ou, _, _ = pipeline.train_ou_network(n_rows=1 << 14, n_steps=20000, device=dev)
+        # the paper's own experiment (Table 6.1's path counts): OU, m = 5, trained network (over the
+        # horizons 0.125 .. 2, so that it also gives the 7L-CDC scheme its marginal points); time per
+        # run of 16 steps (T = 2) for the 7L scheme in both forms and for the 7L-CDC scheme, and the
+        # pathwise error at 2e5 paths against Eq. (6.6) on the same normals (exact OU model)
+        P_ou, _, _ = pipeline.train_ou_network(n_rows=1 << 14, n_steps=20000, dts=tuple(0.125 * np.arange(1, 17)),
+                                               device=dev)
         th_ou, y0_ou = torch.tensor([[0.5, 0.3, 1.0]], device=dev), torch.tensor([1.5], device=dev)
         ou_ms = {}
-        for pr, key in ((sl.PREC_BF16, "bf16"), (sl.PREC_FP32, "fp32")):
+        for pr, key in ((sl.PREC_BF16, "bf16"), (sl.PREC_FP32, "fp32"), (sl.PREC_FP32, "cdc")):
             net_ou = sl.make_net(P_ou, 5, 5, prec=pr)
             for n_ou in (1000, 50000, 100000, 200000):
                 off_ou = torch.as_tensor(W.offsets_from_counts([n_ou]), device=dev)
                 yt_ou = torch.empty(n_ou, dtype=f32, device=dev)
-                ws_ou = torch.empty(sl.simulate_workspace_size(n_ou, 1), dtype=torch.uint8, device=dev)
-                run_ou = lambda: sl.seven_league_simulate_batched(sl.MODEL_MLP, net_ou, th_ou, y0_ou, off_ou, 2.0, 16,
-                                                                  5, 3, out_YT=yt_ou, ws=ws_ou, total_paths=n_ou)
+                if key == "cdc":
+                    ws_ou = torch.empty(sl.cdc_workspace_size(n_ou, 1, 16), dtype=torch.uint8, device=dev)
+                    run_ou = lambda: sl.seven_league_cdc_simulate_batched(sl.MODEL_MLP, net_ou, th_ou, y0_ou, off_ou,
+                                                                          2.0, 16, 5, 3, out_YT=yt_ou, ws=ws_ou,
+                                                                          total_paths=n_ou)
+                else:
+                    ws_ou = torch.empty(sl.simulate_workspace_size(n_ou, 1), dtype=torch.uint8, device=dev)
+                    run_ou = lambda: sl.seven_league_simulate_batched(sl.MODEL_MLP, net_ou, th_ou, y0_ou, off_ou, 2.0,
+                                                                      16, 5, 3, out_YT=yt_ou, ws=ws_ou,
+                                                                      total_paths=n_ou)
                 run_ou()
                 torch.cuda.synchronize()
                 e0.record(stream)
@@ -535,7 +584,8 @@ def main():
             secondary["ou_pathwise_err_" + key] = float((yt_ou - yt_ex).abs().mean().item())
         secondary["ou_table61_ms_per_run"] = ou_ms
         secondary["ou_table61_workload"] = ("OU (Ybar 0.5, sigma 0.3, lambda 1, Y0 1.5), m=5, trained 5->50x4->5 ReLU "
-                                            "network, T=2 in 16 steps; paths 1e3/5e4/1e5/2e5 as in Table 6.1")
+                                            "network (horizons 0.125..2), T=2 in 16 steps; paths 1e3/5e4/1e5/2e5 as "
+                                            "in Table 6.1; keys bf16/fp32 = 7L scheme, cdc = 7L-CDC scheme")
 
     # --- end to end through the C ABI with host buffers (pinned), copies timed.  Every step copies
     # its inputs host -> device, runs the sampler and copies Y_T and the set moments back; the steps

@@ -12,8 +12,8 @@
 // coincide) every path sits at z_0 and yhat = C[0].
 //
 // Two phases.  (1) Tables: for every (set, step) the m + 1 network evaluations,
-// in FP32 on CUDA cores (weights staged in shared memory, one evaluation per
-// thread), plus the barycentric weights of the z_k in FP64; 768 bytes per
+// in FP32 on CUDA cores (weights staged in shared memory, 8 lanes per
+// evaluation), plus the barycentric weights of the z_k in FP64; 768 bytes per
 // (set, step), with the continuation lines beyond the hull.  (2) Paths: one thread per path for the whole time loop, the
 // state and the normals in registers; the table of the path's (set, step) is
 // read through the L1 cache (the lanes of a warp share a set, so a load is one
@@ -41,7 +41,6 @@ using namespace simt;
 // P_k(Y) = prod_{l!=k} (Y - z_l), Q_j(X) = prod_{l!=j} (X - x_l).
 constexpr int kTabFloats = 192;
 constexpr int kSlo = 80, kShi = 88, kClo = 96, kChi = 104, kZlo = 112, kRow0 = 120, kCw = 128;
-constexpr int kTabThreads = 128;
 constexpr int kPathThreads = 256;
 
 struct CdcArgs {
@@ -79,144 +78,185 @@ __device__ __forceinline__ void exact_map(const float* th, float Y, float h, con
     }
 }
 
-template <int MODEL, int ACT>
-__device__ __forceinline__ void eval_map(const SmemNet& net, float* act, const float* th, int p, float Y,
-                                         float h, const GHConst& gh, int m, float (&y)[SL_MAX_M]) {
-    if (MODEL == SL_MODEL_MLP) {
-        float f[DS];
+// ---------------------------------------------------------------------------
+// Phase 1: the tables.  One kernel; a CTA takes kBatch (set, step) entries at a
+// time in three rounds: (A) the marginal nodes of each entry, (B) the m conditional
+// rows of each entry, (C) weights, continuation lines and the folded copy.  A
+// network evaluation is shared by the 8 lanes of a group: lane `sub` computes the
+// layer outputs sub, sub + 8, ... (the group's lanes read consecutive weight rows,
+// 52 floats apart: conflict-free; the four groups of a warp read the same rows:
+// broadcast), so that a small table (one set, a few steps) costs a few microseconds.
+// ---------------------------------------------------------------------------
+constexpr int kGroup = 8;                         // lanes per network evaluation
+constexpr int kTabThreads = 256;
+constexpr int kGroups = kTabThreads / kGroup;     // 32
+constexpr int kBatch = 8;                         // entries per round
+constexpr int kBufStride = 72;                    // floats per activation buffer (banks 8 apart)
+
+__device__ __forceinline__ float dot50_smem(const float* __restrict__ row, const float* __restrict__ in, float acc) {
 #pragma unroll
-        for (int k = 0; k < DS; ++k) f[k] = 0.0f;
-        f[0] = Y;
-        f[1] = h;
-        for (int k = 0; k < p && k < DS - 2; ++k) f[2 + k] = __ldg(th + k);
-        mlp_forward<ACT>(net, act, blockDim.x, f, y);
+    for (int k = 0; k < 48; k += 4) {
+        const float4 w4 = *reinterpret_cast<const float4*>(row + k);
+        const float4 x4 = *reinterpret_cast<const float4*>(in + k);
+        acc = fmaf(w4.x, x4.x, acc);
+        acc = fmaf(w4.y, x4.y, acc);
+        acc = fmaf(w4.z, x4.z, acc);
+        acc = fmaf(w4.w, x4.w, acc);
+    }
+    acc = fmaf(row[48], in[48], acc);
+    return fmaf(row[49], in[49], acc);
+}
+
+// One network evaluation by the 8 lanes of the group (mask gm): features in in[0, DS),
+// result y_j (j < m) in out[j]; `in` and `tmp` are the group's two buffers.
+template <int ACT>
+__device__ __forceinline__ void group_mlp(const SmemNet& s, float* in, float* tmp, int sub, unsigned gm, int m,
+                                          float* out) {
+    for (int o = sub; o < W; o += kGroup) {
+        float acc = s.b1[o];
+#pragma unroll
+        for (int k = 0; k < DS; ++k) acc = fmaf(s.W1[o * DS + k], in[k], acc);
+        tmp[o] = activation<ACT>(acc);
+    }
+    __syncwarp(gm);
+    float* src = tmp;
+    float* dst = in;
+    for (int l = 0; l < 3; ++l) {
+        for (int o = sub; o < W; o += kGroup) dst[o] = activation<ACT>(dot50_smem(s.Wh[l] + o * WS, src, s.bh[l][o]));
+        __syncwarp(gm);
+        float* t = src;
+        src = dst;
+        dst = t;
+    }
+    if (sub < m) out[sub] = dot50_smem(s.W5 + sub * WS, src, s.b5[sub]);
+    __syncwarp(gm);
+}
+
+// Collocation points at (Y, horizon h) for the group: the network (its features written
+// to `in` first) or the exact map; y_j for j < m in out[j], zero for m <= j < 8.
+template <int MODEL, int ACT>
+__device__ __forceinline__ void group_map(const SmemNet& net, float* in, float* tmp, int sub, unsigned gm,
+                                          const CdcArgs& a, int s, float Y, float h, float* out) {
+    const int m = a.m;
+    if (MODEL == SL_MODEL_MLP) {
+        const float* th = a.theta + static_cast<int64_t>(s) * a.p;
+        in[sub] = sub == 0 ? Y : sub == 1 ? h : (sub - 2 < a.p ? __ldg(th + sub - 2) : 0.0f);
+        __syncwarp(gm);
+        group_mlp<ACT>(net, in, tmp, sub, gm, m, out);
+        if (sub >= m) out[sub] = 0.0f;
+    } else {
+        float y[SL_MAX_M];
+        exact_map<MODEL>(a.theta + static_cast<int64_t>(s) * a.p, Y, h, a.gh, m, y);
+        float v = 0.0f;
 #pragma unroll
         for (int j = 0; j < SL_MAX_M; ++j)
-            if (j >= m) y[j] = 0.0f;
-    } else {
-        exact_map<MODEL>(th, Y, h, gh, m, y);
+            if (j == sub) v = y[j];
+        out[sub] = sub < m ? v : 0.0f;
     }
+    __syncwarp(gm);
 }
 
-// Phase 1a: marginal nodes z and their barycentric weights w (FP64 products of
-// the FP32 node differences, rounded once); w = 0 marks coinciding nodes.
-template <int MODEL, int ACT>
-__global__ void __launch_bounds__(kTabThreads) cdc_marginal_kernel(const CdcArgs a) {
+size_t table_smem_bytes(int model) {
+    return (model == SL_MODEL_MLP ? 2 * sizeof(SmemNet) : 0) +
+           (static_cast<size_t>(kGroups) * 2 * kBufStride + kBatch * 8 + kBatch * 64) * sizeof(float);
+}
+
+template <int MODEL, int ACT, int MACT>
+__global__ void __launch_bounds__(kTabThreads) cdc_table_kernel(const CdcArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SmemNet& net = *reinterpret_cast<SmemNet*>(smem_raw);
-    float* act = reinterpret_cast<float*>(smem_raw + sizeof(SmemNet)) + threadIdx.x;
+    SmemNet& cnet = *reinterpret_cast<SmemNet*>(smem_raw);
+    SmemNet& mnet = *reinterpret_cast<SmemNet*>(smem_raw + sizeof(SmemNet));
+    float* bufs = reinterpret_cast<float*>(smem_raw + (MODEL == SL_MODEL_MLP ? 2 * sizeof(SmemNet) : 0));
+    float* zs = bufs + kGroups * 2 * kBufStride;   // [kBatch][8] marginal nodes
+    float* Cs = zs + kBatch * 8;                   // [kBatch][8][8] conditional rows
     if (MODEL == SL_MODEL_MLP) {
-        stage_net(net, a.mparams, a.d_in, a.m);
+        stage_net(cnet, a.params, a.d_in, a.m);
+        stage_net(mnet, a.mparams, a.d_in, a.m);
         __syncthreads();
     }
+    const int grp = threadIdx.x / kGroup, sub = threadIdx.x % kGroup;
+    const unsigned gm = 0xFFu << (threadIdx.x & 24);
+    float* in = bufs + grp * 2 * kBufStride;
+    float* tmp = in + kBufStride;
     const int m = a.m;
     const int64_t n = static_cast<int64_t>(a.n_sets) * a.n_steps;
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    // no barrier inside the loop: mlp_forward touches only this thread's column of `act`
-    for (int64_t u = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; u < n; u += stride) {
-        const int s = static_cast<int>(u / a.n_steps), i = static_cast<int>(u % a.n_steps);
-        const float y0 = __ldg(a.Y0 + s);
-        float z[SL_MAX_M];
-        if (i == 0) {
-#pragma unroll
-            for (int k = 0; k < SL_MAX_M; ++k) z[k] = (k < m) ? y0 : 0.0f;
-        } else {
-            eval_map<MODEL, ACT>(net, act, a.theta + static_cast<int64_t>(s) * a.p, a.p, y0,
-                                 static_cast<float>(i) * a.dt, a.gh, m, z);
-        }
-        bool same = true;
-        for (int k = 1; k < m; ++k) same = same && (z[k] == z[0]);
-        float* t = a.tab + u * kTabFloats;
-#pragma unroll
-        for (int k = 0; k < SL_MAX_M; ++k) {
-            double prod = 1.0;
-            for (int l = 0; l < m; ++l)
-                if (l != k) prod *= static_cast<double>(z[k]) - static_cast<double>(z[l]);
-            t[k] = z[k];
-            t[8 + k] = (k < m && !same) ? static_cast<float>(1.0 / prod) : 0.0f;
-        }
-    }
-}
-
-// Phase 1b: conditional points C[k][j] = H_j(z_k, dt, theta) (rows k >= m zero).
-template <int MODEL, int ACT>
-__global__ void __launch_bounds__(kTabThreads) cdc_conditional_kernel(const CdcArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SmemNet& net = *reinterpret_cast<SmemNet*>(smem_raw);
-    float* act = reinterpret_cast<float*>(smem_raw + sizeof(SmemNet)) + threadIdx.x;
-    if (MODEL == SL_MODEL_MLP) {
-        stage_net(net, a.params, a.d_in, a.m);
-        __syncthreads();
-    }
-    const int m = a.m;
-    const int64_t n = static_cast<int64_t>(a.n_sets) * a.n_steps * SL_MAX_M;
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += stride) {
-        const int64_t u = v / SL_MAX_M;
-        const int k = static_cast<int>(v % SL_MAX_M);
-        const int s = static_cast<int>(u / a.n_steps);
-        float* t = a.tab + u * kTabFloats;
-        float y[SL_MAX_M];
-        if (k < m) {
-            eval_map<MODEL, ACT>(net, act, a.theta + static_cast<int64_t>(s) * a.p, a.p, t[k], a.dt, a.gh,
-                                 m, y);
-        } else {
-#pragma unroll
-            for (int j = 0; j < SL_MAX_M; ++j) y[j] = 0.0f;
-        }
-        float4* row = reinterpret_cast<float4*>(t + 16 + k * 8);
-        row[0] = make_float4(y[0], y[1], y[2], y[3]);
-        row[1] = make_float4(y[4], y[5], y[6], y[7]);
-    }
-}
-
-// Phase 1c: the continuation lines beyond the outermost nodes.  The two smallest
-// (largest) nodes, ties to the lower index; slopes (C[b][j] - C[a][j]) / (z_b - z_a)
-// in FP64 from the FP32 entries, rounded once (0 where the two nodes coincide: the
-// table is then degenerate, w = 0, or already non-finite through w).
-__global__ void __launch_bounds__(kTabThreads) cdc_edge_kernel(float* __restrict__ tab, int64_t n, int m,
-                                                                const GHConst gh) {
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t u = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; u < n; u += stride) {
-        float* t = tab + u * kTabFloats;
-        int lo = 0, hi = 0;
-        for (int k = 1; k < m; ++k) {
-            if (t[k] < t[lo]) lo = k;
-            if (t[k] > t[hi]) hi = k;
-        }
-        int lo2 = -1, hi2 = -1;
-        for (int k = 0; k < m; ++k) {
-            if (k != lo && (lo2 < 0 || t[k] < t[lo2])) lo2 = k;
-            if (k != hi && (hi2 < 0 || t[k] > t[hi2])) hi2 = k;
-        }
-        const double dlo = static_cast<double>(t[lo2]) - t[lo], dhi = static_cast<double>(t[hi2]) - t[hi];
-        for (int j = 0; j < SL_MAX_M; ++j) {
-            const float clo = t[16 + lo * 8 + j], chi = t[16 + hi * 8 + j];
-            t[kClo + j] = clo;
-            t[kChi + j] = chi;
-            t[kSlo + j] = (j < m && dlo != 0.0)
-                              ? static_cast<float>((static_cast<double>(t[16 + lo2 * 8 + j]) - clo) / dlo) : 0.0f;
-            t[kShi + j] = (j < m && dhi != 0.0)
-                              ? static_cast<float>((static_cast<double>(t[16 + hi2 * 8 + j]) - chi) / dhi) : 0.0f;
-        }
-        t[kZlo] = t[lo];
-        t[kZlo + 1] = t[hi];
-        for (int k = kZlo + 2; k < kRow0; ++k) t[k] = 0.0f;
-        for (int j = 0; j < SL_MAX_M; ++j) t[kRow0 + j] = t[16 + j];
-        // Cw[k][j] = w_k b_j C[k][j]: w_k again in FP64 from the FP32 nodes (0 when the
-        // nodes coincide, like the stored w)
-        const bool live = t[8] != 0.0f;
-        for (int k = 0; k < SL_MAX_M; ++k) {
-            double wk = 0.0;
-            if (live && k < m) {
-                double prod = 1.0;
-                for (int l = 0; l < m; ++l)
-                    if (l != k) prod *= static_cast<double>(t[k]) - static_cast<double>(t[l]);
-                wk = 1.0 / prod;
+    for (int64_t base = static_cast<int64_t>(blockIdx.x) * kBatch; base < n;
+         base += static_cast<int64_t>(gridDim.x) * kBatch) {
+        // (A) marginal nodes: group e < kBatch for entry base + e (whole warps 0 and 1)
+        if (grp < kBatch) {
+            const int64_t u = base + grp;
+            float* z = zs + grp * 8;
+            if (u < n) {
+                const int s = static_cast<int>(u / a.n_steps), i = static_cast<int>(u % a.n_steps);
+                const float y0 = __ldg(a.Y0 + s);
+                if (i == 0) z[sub] = sub < m ? y0 : 0.0f;
+                else group_map<MODEL, MACT>(mnet, in, tmp, sub, gm, a, s, y0, static_cast<float>(i) * a.dt, z);
+            } else {
+                z[sub] = 0.0f;
             }
-            for (int j = 0; j < SL_MAX_M; ++j)
-                t[kCw + 8 * k + j] = (j < m) ? static_cast<float>(wk * gh.bary[j] * t[16 + 8 * k + j]) : 0.0f;
         }
+        __syncthreads();
+        // (B) conditional rows: job grp + 32 r = entry e, row k
+#pragma unroll 1
+        for (int r = 0; r < kBatch * 8 / kGroups; ++r) {
+            const int job = grp + kGroups * r, e = job / 8, k = job % 8;
+            const int64_t u = base + e;
+            float* crow = Cs + e * 64 + k * 8;
+            if (u < n && k < m) {
+                const int s = static_cast<int>(u / a.n_steps);
+                group_map<MODEL, ACT>(cnet, in, tmp, sub, gm, a, s, zs[e * 8 + k], a.dt, crow);
+            } else {
+                crow[sub] = 0.0f;
+            }
+        }
+        __syncthreads();
+        // (C) thread (e, k): node k of entry e -- its weight, row k of C and Cw, and
+        // column k of the continuation lines
+        if (threadIdx.x < kBatch * 8) {
+            const int e = threadIdx.x / 8, k = threadIdx.x % 8;
+            const int64_t u = base + e;
+            if (u < n) {
+                const float* z = zs + e * 8;
+                const float* C = Cs + e * 64;
+                float* t = a.tab + u * kTabFloats;
+                bool same = true;
+                int lo = 0, hi = 0;
+                for (int l = 1; l < m; ++l) {
+                    same = same && z[l] == z[0];
+                    if (z[l] < z[lo]) lo = l;
+                    if (z[l] > z[hi]) hi = l;
+                }
+                int lo2 = -1, hi2 = -1;
+                for (int l = 0; l < m; ++l) {
+                    if (l != lo && (lo2 < 0 || z[l] < z[lo2])) lo2 = l;
+                    if (l != hi && (hi2 < 0 || z[l] > z[hi2])) hi2 = l;
+                }
+                double wk = 0.0;
+                if (!same && k < m) {
+                    double prod = 1.0;
+                    for (int l = 0; l < m; ++l)
+                        if (l != k) prod *= static_cast<double>(z[k]) - static_cast<double>(z[l]);
+                    wk = 1.0 / prod;
+                }
+                t[k] = z[k];
+                t[8 + k] = static_cast<float>(wk);
+                for (int j = 0; j < SL_MAX_M; ++j) {
+                    const float c = C[k * 8 + j];
+                    t[16 + 8 * k + j] = c;
+                    t[kCw + 8 * k + j] = (j < m) ? static_cast<float>(wk * a.gh.bary[j] * c) : 0.0f;
+                }
+                // column k of the lines through the two outermost nodes on each side
+                const double dlo = static_cast<double>(z[lo2]) - z[lo], dhi = static_cast<double>(z[hi2]) - z[hi];
+                const float clo = C[lo * 8 + k], chi = C[hi * 8 + k];
+                t[kClo + k] = clo;
+                t[kChi + k] = chi;
+                t[kSlo + k] = (k < m && dlo != 0.0) ? static_cast<float>((static_cast<double>(C[lo2 * 8 + k]) - clo) / dlo) : 0.0f;
+                t[kShi + k] = (k < m && dhi != 0.0) ? static_cast<float>((static_cast<double>(C[hi2 * 8 + k]) - chi) / dhi) : 0.0f;
+                t[kRow0 + k] = C[k];
+                t[kZlo + k] = k == 0 ? z[lo] : k == 1 ? z[hi] : 0.0f;   // z_lo, z_hi, then zero padding
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -394,35 +434,29 @@ __global__ void __launch_bounds__(kPathThreads) cdc_path_kernel(const SimArgs a,
     }
 }
 
+template <int MODEL, int ACT, int MACT>
+int launch_table_kernel(const CdcArgs& c, cudaStream_t st) {
+    auto k = cdc_table_kernel<MODEL, ACT, MACT>;
+    const size_t smem = table_smem_bytes(MODEL);
+    int rc = cuda_error(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
+                        "cdc_table attribute");
+    if (rc) return rc;
+    int per_sm = 0;
+    rc = cuda_error(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTabThreads, smem), "cdc_table occupancy");
+    if (rc) return rc;
+    const int64_t need = (static_cast<int64_t>(c.n_sets) * c.n_steps + kBatch - 1) / kBatch;
+    int64_t blocks = static_cast<int64_t>(sm_count()) * (per_sm > 0 ? per_sm : 1);
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    k<<<static_cast<unsigned>(blocks), kTabThreads, smem, st>>>(c);
+    return cuda_error(cudaGetLastError(), "cdc_table launch");
+}
+
 template <int MODEL, int ACT>
 int launch_tables(const CdcArgs& c, int mact, cudaStream_t st) {
-    const size_t smem = (MODEL == SL_MODEL_MLP)
-                            ? sizeof(SmemNet) + static_cast<size_t>(W) * kTabThreads * sizeof(float)
-                            : 0;
-    const int64_t n1 = static_cast<int64_t>(c.n_sets) * c.n_steps;
-    const int64_t cap = static_cast<int64_t>(sm_count()) * 8;
-    auto blocks = [&](int64_t n) {
-        int64_t b = (n + kTabThreads - 1) / kTabThreads;
-        return static_cast<unsigned>(b < 1 ? 1 : (b > cap ? cap : b));
-    };
     // the marginal network may use another activation than the conditional one
-    auto km = (mact == SL_ACT_SOFTPLUS) ? cdc_marginal_kernel<MODEL, SL_ACT_SOFTPLUS>
-                                        : cdc_marginal_kernel<MODEL, SL_ACT_RELU>;
-    auto kc = cdc_conditional_kernel<MODEL, ACT>;
-    int rc = cuda_error(cudaFuncSetAttribute(km, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
-                        "cdc_marginal attribute");
-    if (rc) return rc;
-    rc = cuda_error(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
-                    "cdc_conditional attribute");
-    if (rc) return rc;
-    km<<<blocks(n1), kTabThreads, smem, st>>>(c);
-    rc = cuda_error(cudaGetLastError(), "cdc_marginal launch");
-    if (rc) return rc;
-    kc<<<blocks(n1 * SL_MAX_M), kTabThreads, smem, st>>>(c);
-    rc = cuda_error(cudaGetLastError(), "cdc_conditional launch");
-    if (rc) return rc;
-    cdc_edge_kernel<<<blocks(n1), kTabThreads, 0, st>>>(c.tab, n1, c.m, c.gh);
-    return cuda_error(cudaGetLastError(), "cdc_edge launch");
+    if (mact == SL_ACT_SOFTPLUS) return launch_table_kernel<MODEL, ACT, SL_ACT_SOFTPLUS>(c, st);
+    return launch_table_kernel<MODEL, ACT, SL_ACT_RELU>(c, st);
 }
 
 template <int M>

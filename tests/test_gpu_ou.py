@@ -96,7 +96,7 @@ def test_pathwise_error_does_not_grow_with_step(sl, orc, ou_net):
 @pytest.fixture(scope="module")
 def ou_net_horizons(sl):
     from paper_2302_05170_b300 import pipeline
-    P, losses, _ = pipeline.train_ou_network(n_rows=1 << 14, n_steps=20000, dts=tuple(0.125 * np.arange(1, 17)))
+    P, losses, _ = pipeline.train_ou_network(n_rows=1 << 14, n_steps=40000, dts=tuple(0.125 * np.arange(1, 17)))
     assert losses[-500:].mean() < 0.02 * losses[:20].mean()
     return P
 
