@@ -10,8 +10,9 @@ collocation points and a trained network) against the exact solution Eq. (6.6).
   is sigma^2 dt instead of sigma^2 (1 - e^{-2 lambda T}) / (2 lambda)); the 7L scheme's does not.
 * Both network forms (FP32 CUDA cores, BF16 tensor cores) meet the same bounds.
 * The 7L-CDC variant (the other column of Table 6.1), with one network trained over the
-  horizons 0.125 .. 2 serving as the marginal and the conditional map: the same pathwise and
-  variance bounds against the exact solution on the same normals.
+  horizons 0.125 .. 2 serving as the marginal and the conditional map: small pathwise error
+  against the exact solution on the same normals, within 1.25x (+1e-3) of the 7L scheme's with
+  the same network at every step size, and the same variance to 2% of the exact variance.
 """
 import math
 
@@ -96,28 +97,32 @@ def test_pathwise_error_does_not_grow_with_step(sl, orc, ou_net):
 @pytest.fixture(scope="module")
 def ou_net_horizons(sl):
     from paper_2302_05170_b300 import pipeline
-    P, losses, _ = pipeline.train_ou_network(n_rows=1 << 14, n_steps=40000, dts=tuple(0.125 * np.arange(1, 17)))
+    P, losses, _ = pipeline.train_ou_network(n_rows=1 << 14, n_steps=20000, dts=tuple(0.125 * np.arange(1, 17)))
     assert losses[-500:].mean() < 0.02 * losses[:20].mean()
     return P
 
 
 def test_cdc_pathwise_error(sl, orc, ou_net_horizons):
+    """The 7L-CDC scheme keeps the accuracy of the 7L scheme with the same network: the network's
+    error dominates, the global interpolation in Y adds little (the exact OU map is affine in Y)."""
     n, seed = 20000, 13
     exact_var = SG * SG * (1 - math.exp(-2 * LAM * T)) / (2 * LAM)
-    net = sl.make_net(ou_net_horizons, 5, M)
     off = _dev(W.offsets_from_counts([n]), torch.int64)
-    errs, var7 = {}, {}
+    th, y0 = _dev([[YB, SG, LAM]]), _dev([Y0])
+    net = sl.make_net(ou_net_horizons, 5, M)
+    err, err7, dvar = {}, {}, {}
     for n_steps in (16, 4, 2):
         ref = _run(sl, sl.MODEL_OU_EXACT, None, n, n_steps, seed)
+        y7 = _run(sl, sl.MODEL_MLP, net, n, n_steps, seed)
         yt = torch.empty(n, device="cuda")
-        ws = sl.seven_league_cdc_simulate_batched(sl.MODEL_MLP, net, _dev([[YB, SG, LAM]]), _dev([Y0]), off, T,
-                                                  n_steps, M, seed, out_YT=yt)
+        ws = sl.seven_league_cdc_simulate_batched(sl.MODEL_MLP, net, th, y0, off, T, n_steps, M, seed, out_YT=yt)
         assert sl.workspace_status(ws) == 0
         y = yt.cpu().numpy().astype(np.float64)
-        errs[n_steps] = np.abs(y - ref).mean()
-        var7[n_steps] = abs(y.var() - ref.var()) / exact_var
-    print("7L-CDC pathwise mean |Y - exact|:", errs, "relative variance error:", var7)
+        err[n_steps], err7[n_steps] = np.abs(y - ref).mean(), np.abs(y7 - ref).mean()
+        dvar[n_steps] = abs(y.var() - y7.var()) / exact_var
+    print("pathwise mean |Y - exact|, 7L-CDC:", err, "7L:", err7, "|Var CDC - Var 7L| / exact:", dvar)
     for k in (16, 4, 2):
-        assert errs[k] < 0.02 * Y0, k
-        assert var7[k] < 0.05, k
-    assert errs[2] <= 1.5 * errs[16]
+        assert err[k] < 0.02 * Y0, k
+        assert err[k] <= 1.25 * err7[k] + 1e-3, k
+        assert dvar[k] < 0.02, k
+    assert err[2] <= 1.5 * err[16]
