@@ -64,12 +64,12 @@ template <int MODEL>
 __device__ __forceinline__ void exact_map(const float* th, float Y, float h, const GHConst& gh, int m,
                                           float (&y)[SL_MAX_M]) {
     if (MODEL == SL_MODEL_GBM_EXACT) {
-        const float mu = __ldg(th), sg = __ldg(th + 1);
+        const float mu = th[0], sg = th[1];
         const float am = (mu - 0.5f * sg * sg) * h, bm = sg * sqrtf(h);
 #pragma unroll
         for (int j = 0; j < SL_MAX_M; ++j) y[j] = (j < m) ? Y * expf(fmaf(bm, gh.x[j], am)) : 0.0f;
     } else {
-        const float yb = __ldg(th), sg = __ldg(th + 1), lam = __ldg(th + 2);
+        const float yb = th[0], sg = th[1], lam = th[2];
         const float c1 = expf(-lam * h);
         const float sd = sg * sqrtf(-expm1f(-2.0f * lam * h) / (2.0f * lam));
         const float c0 = yb * (-expm1f(-lam * h));
@@ -90,7 +90,7 @@ __device__ __forceinline__ void exact_map(const float* th, float Y, float h, con
 constexpr int kGroup = 8;                         // lanes per network evaluation
 constexpr int kTabThreads = 256;
 constexpr int kGroups = kTabThreads / kGroup;     // 32
-constexpr int kBatch = 8;                         // entries per round
+constexpr int kBatch = 4;                         // entries per round (one pass of round B)
 constexpr int kBufStride = 72;                    // floats per activation buffer (banks 8 apart)
 
 __device__ __forceinline__ float dot50_smem(const float* __restrict__ row, const float* __restrict__ in, float acc) {
@@ -107,6 +107,41 @@ __device__ __forceinline__ float dot50_smem(const float* __restrict__ row, const
     return fmaf(row[49], in[49], acc);
 }
 
+// One layer of 50 outputs for the 8 lanes of a group: lane `sub` computes outputs
+// sub + 8 r, r < 7 (the last only for sub < 2), as seven interleaved dot products over
+// the 50 inputs in src, so that the group's latency is one dot product, not seven.
+template <int ACT>
+__device__ __forceinline__ void group_layer50(const float* __restrict__ Wl, const float* __restrict__ bl,
+                                              const float* __restrict__ src, float* __restrict__ dst, int sub) {
+    constexpr int R = (W + kGroup - 1) / kGroup;   // 7
+    float acc[R];
+    // row r starts at Wl + (sub + 8 r) WS; rows past 49 recompute row 49 (not stored)
+    const float* row0 = Wl + sub * WS;
+    const int last = (W - 1 - sub) * WS;
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = bl[min(sub + kGroup * r, W - 1)];
+#pragma unroll 4
+    for (int k = 0; k < 48; k += 4) {
+        const float4 x4 = *reinterpret_cast<const float4*>(src + k);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float4 w4 = *reinterpret_cast<const float4*>(row0 + min(kGroup * WS * r, last) + k);
+            acc[r] = fmaf(w4.x, x4.x, acc[r]);
+            acc[r] = fmaf(w4.y, x4.y, acc[r]);
+            acc[r] = fmaf(w4.z, x4.z, acc[r]);
+            acc[r] = fmaf(w4.w, x4.w, acc[r]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const float* rr = row0 + min(kGroup * WS * r, last);
+        acc[r] = fmaf(rr[48], src[48], acc[r]);
+        acc[r] = fmaf(rr[49], src[49], acc[r]);
+        const int o = sub + kGroup * r;
+        if (o < W) dst[o] = activation<ACT>(acc[r]);
+    }
+}
+
 // One network evaluation by the 8 lanes of the group (mask gm): features in in[0, DS),
 // result y_j (j < m) in out[j]; `in` and `tmp` are the group's two buffers.
 template <int ACT>
@@ -119,16 +154,13 @@ __device__ __forceinline__ void group_mlp(const SmemNet& s, float* in, float* tm
         tmp[o] = activation<ACT>(acc);
     }
     __syncwarp(gm);
-    float* src = tmp;
-    float* dst = in;
-    for (int l = 0; l < 3; ++l) {
-        for (int o = sub; o < W; o += kGroup) dst[o] = activation<ACT>(dot50_smem(s.Wh[l] + o * WS, src, s.bh[l][o]));
-        __syncwarp(gm);
-        float* t = src;
-        src = dst;
-        dst = t;
-    }
-    if (sub < m) out[sub] = dot50_smem(s.W5 + sub * WS, src, s.b5[sub]);
+    group_layer50<ACT>(s.Wh[0], s.bh[0], tmp, in, sub);
+    __syncwarp(gm);
+    group_layer50<ACT>(s.Wh[1], s.bh[1], in, tmp, sub);
+    __syncwarp(gm);
+    group_layer50<ACT>(s.Wh[2], s.bh[2], tmp, in, sub);
+    __syncwarp(gm);
+    if (sub < m) out[sub] = dot50_smem(s.W5 + sub * WS, in, s.b5[sub]);
     __syncwarp(gm);
 }
 
@@ -136,17 +168,16 @@ __device__ __forceinline__ void group_mlp(const SmemNet& s, float* in, float* tm
 // to `in` first) or the exact map; y_j for j < m in out[j], zero for m <= j < 8.
 template <int MODEL, int ACT>
 __device__ __forceinline__ void group_map(const SmemNet& net, float* in, float* tmp, int sub, unsigned gm,
-                                          const CdcArgs& a, int s, float Y, float h, float* out) {
+                                          const CdcArgs& a, const float* th, float Y, float h, float* out) {
     const int m = a.m;
     if (MODEL == SL_MODEL_MLP) {
-        const float* th = a.theta + static_cast<int64_t>(s) * a.p;
-        in[sub] = sub == 0 ? Y : sub == 1 ? h : (sub - 2 < a.p ? __ldg(th + sub - 2) : 0.0f);
+        in[sub] = sub == 0 ? Y : sub == 1 ? h : (sub - 2 < a.p ? th[sub - 2] : 0.0f);
         __syncwarp(gm);
         group_mlp<ACT>(net, in, tmp, sub, gm, m, out);
         if (sub >= m) out[sub] = 0.0f;
     } else {
         float y[SL_MAX_M];
-        exact_map<MODEL>(a.theta + static_cast<int64_t>(s) * a.p, Y, h, a.gh, m, y);
+        exact_map<MODEL>(th, Y, h, a.gh, m, y);
         float v = 0.0f;
 #pragma unroll
         for (int j = 0; j < SL_MAX_M; ++j)
@@ -158,22 +189,25 @@ __device__ __forceinline__ void group_map(const SmemNet& net, float* in, float* 
 
 size_t table_smem_bytes(int model) {
     return (model == SL_MODEL_MLP ? 2 * sizeof(SmemNet) : 0) +
-           (static_cast<size_t>(kGroups) * 2 * kBufStride + kBatch * 8 + kBatch * 64) * sizeof(float);
+           (static_cast<size_t>(kGroups) * 2 * kBufStride + kBatch * 8 + kBatch * 64 + kBatch * 8) * sizeof(float);
 }
 
 template <int MODEL, int ACT, int MACT>
-__global__ void __launch_bounds__(kTabThreads) cdc_table_kernel(const CdcArgs a) {
+__global__ void __launch_bounds__(kTabThreads, 2) cdc_table_kernel(const CdcArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmemNet& cnet = *reinterpret_cast<SmemNet*>(smem_raw);
     SmemNet& mnet = *reinterpret_cast<SmemNet*>(smem_raw + sizeof(SmemNet));
     float* bufs = reinterpret_cast<float*>(smem_raw + (MODEL == SL_MODEL_MLP ? 2 * sizeof(SmemNet) : 0));
     float* zs = bufs + kGroups * 2 * kBufStride;   // [kBatch][8] marginal nodes
     float* Cs = zs + kBatch * 8;                   // [kBatch][8][8] conditional rows
+    float* ths = Cs + kBatch * 64;                 // [kBatch][8]: Y0 of the entry's set, then theta
+    const bool one_net = a.mparams == a.params;     // the conditional network gives the marginals too
     if (MODEL == SL_MODEL_MLP) {
         stage_net(cnet, a.params, a.d_in, a.m);
-        stage_net(mnet, a.mparams, a.d_in, a.m);
+        if (!one_net) stage_net(mnet, a.mparams, a.d_in, a.m);
         __syncthreads();
     }
+    const SmemNet& gnet = one_net ? cnet : mnet;
     const int grp = threadIdx.x / kGroup, sub = threadIdx.x % kGroup;
     const unsigned gm = 0xFFu << (threadIdx.x & 24);
     float* in = bufs + grp * 2 * kBufStride;
@@ -182,15 +216,27 @@ __global__ void __launch_bounds__(kTabThreads) cdc_table_kernel(const CdcArgs a)
     const int64_t n = static_cast<int64_t>(a.n_sets) * a.n_steps;
     for (int64_t base = static_cast<int64_t>(blockIdx.x) * kBatch; base < n;
          base += static_cast<int64_t>(gridDim.x) * kBatch) {
-        // (A) marginal nodes: group e < kBatch for entry base + e (whole warps 0 and 1)
+        // the batch's Y0 and theta, one global round trip for all groups
+        if (threadIdx.x < kBatch * 8) {
+            const int e = threadIdx.x / 8, c = threadIdx.x % 8;
+            const int64_t u = base + e;
+            float v = 0.0f;
+            if (u < n) {
+                const int s = static_cast<int>(u / a.n_steps);
+                v = c == 0 ? __ldg(a.Y0 + s) : (c - 1 < a.p ? __ldg(a.theta + static_cast<int64_t>(s) * a.p + c - 1) : 0.0f);
+            }
+            ths[threadIdx.x] = v;
+        }
+        __syncthreads();
+        // (A) marginal nodes: group e < kBatch for entry base + e (warp 0)
         if (grp < kBatch) {
             const int64_t u = base + grp;
             float* z = zs + grp * 8;
             if (u < n) {
-                const int s = static_cast<int>(u / a.n_steps), i = static_cast<int>(u % a.n_steps);
-                const float y0 = __ldg(a.Y0 + s);
+                const int i = static_cast<int>(u % a.n_steps);
+                const float y0 = ths[grp * 8];
                 if (i == 0) z[sub] = sub < m ? y0 : 0.0f;
-                else group_map<MODEL, MACT>(mnet, in, tmp, sub, gm, a, s, y0, static_cast<float>(i) * a.dt, z);
+                else group_map<MODEL, MACT>(gnet, in, tmp, sub, gm, a, ths + grp * 8 + 1, y0, static_cast<float>(i) * a.dt, z);
             } else {
                 z[sub] = 0.0f;
             }
@@ -203,8 +249,7 @@ __global__ void __launch_bounds__(kTabThreads) cdc_table_kernel(const CdcArgs a)
             const int64_t u = base + e;
             float* crow = Cs + e * 64 + k * 8;
             if (u < n && k < m) {
-                const int s = static_cast<int>(u / a.n_steps);
-                group_map<MODEL, ACT>(cnet, in, tmp, sub, gm, a, s, zs[e * 8 + k], a.dt, crow);
+                group_map<MODEL, ACT>(cnet, in, tmp, sub, gm, a, ths + e * 8 + 1, zs[e * 8 + k], a.dt, crow);
             } else {
                 crow[sub] = 0.0f;
             }
@@ -434,18 +479,42 @@ __global__ void __launch_bounds__(kPathThreads) cdc_path_kernel(const SimArgs a,
     }
 }
 
-template <int MODEL, int ACT, int MACT>
-int launch_table_kernel(const CdcArgs& c, cudaStream_t st) {
-    auto k = cdc_table_kernel<MODEL, ACT, MACT>;
-    const size_t smem = table_smem_bytes(MODEL);
-    int rc = cuda_error(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
-                        "cdc_table attribute");
+// Blocks per SM of kernel k launched with `threads` threads and `smem` dynamic bytes,
+// after raising its dynamic shared-memory limit: asked of the runtime once per device
+// (a query per call costs microseconds of host time, as much as a small launch's work).
+constexpr int kMaxDevices = 64;
+
+template <class K>
+int blocks_per_sm(K k, int threads, size_t smem, int (&cache)[kMaxDevices], int* out) {
+    int dev = 0;
+    int rc = cuda_error(cudaGetDevice(&dev), "cudaGetDevice");
+    if (rc) return rc;
+    if (dev >= 0 && dev < kMaxDevices && cache[dev] > 0) {
+        *out = cache[dev];
+        return SL_OK;
+    }
+    rc = cuda_error(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
+                    "kernel attribute");
     if (rc) return rc;
     int per_sm = 0;
-    rc = cuda_error(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTabThreads, smem), "cdc_table occupancy");
+    rc = cuda_error(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem), "occupancy");
+    if (rc) return rc;
+    if (per_sm < 1) per_sm = 1;
+    if (dev >= 0 && dev < kMaxDevices) cache[dev] = per_sm;
+    *out = per_sm;
+    return SL_OK;
+}
+
+template <int MODEL, int ACT, int MACT>
+int launch_table_kernel(const CdcArgs& c, cudaStream_t st) {
+    static int cache[kMaxDevices] = {};
+    auto k = cdc_table_kernel<MODEL, ACT, MACT>;
+    const size_t smem = table_smem_bytes(MODEL);
+    int per_sm = 1;
+    int rc = blocks_per_sm(k, kTabThreads, smem, cache, &per_sm);
     if (rc) return rc;
     const int64_t need = (static_cast<int64_t>(c.n_sets) * c.n_steps + kBatch - 1) / kBatch;
-    int64_t blocks = static_cast<int64_t>(sm_count()) * (per_sm > 0 ? per_sm : 1);
+    int64_t blocks = static_cast<int64_t>(sm_count()) * per_sm;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
     k<<<static_cast<unsigned>(blocks), kTabThreads, smem, st>>>(c);
@@ -461,13 +530,14 @@ int launch_tables(const CdcArgs& c, int mact, cudaStream_t st) {
 
 template <int M>
 int launch_paths_m(const SimArgs& a, const float* tab, cudaStream_t st) {
+    static int cache[kMaxDevices] = {};
     auto kern = cdc_path_kernel<M>;
-    int per_sm = 0;
-    int rc = cuda_error(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPathThreads, 0),
-                        "cdc_path occupancy");
+    int per_sm = 1;
+    int rc = blocks_per_sm(kern, kPathThreads, 0, cache, &per_sm);
     if (rc) return rc;
-    const int64_t need = (a.total + static_cast<int64_t>(kPathThreads) * kPair - 1) / (static_cast<int64_t>(kPathThreads) * kPair);
-    int64_t blocks = static_cast<int64_t>(sm_count()) * (per_sm > 0 ? per_sm : 1);
+    const int64_t per_block = static_cast<int64_t>(kPathThreads) * kPair;
+    const int64_t need = (a.total + per_block - 1) / per_block;
+    int64_t blocks = static_cast<int64_t>(sm_count()) * per_sm;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
     kern<<<static_cast<unsigned>(blocks), kPathThreads, 0, st>>>(a, tab);

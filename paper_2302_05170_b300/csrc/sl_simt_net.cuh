@@ -22,31 +22,45 @@ struct SmemNet {
     float b5[SL_MAX_M];
 };
 
-__device__ inline void stage_net(SmemNet& s, const float* __restrict__ P, int d_in, int m) {
+// dst[i] = src_of(i) for i < n by the whole block, eight independent loads in flight
+// per thread (the weights are cold in a small launch: a load at a time would leave the
+// staging latency-bound).
+template <class F>
+__device__ __forceinline__ void stage_loop(float* dst, int n, F src_of) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    const float* p = P;
-    for (int i = tid; i < W * DS; i += nt) {
-        const int o = i / DS, k = i % DS;
-        s.W1[i] = (k < d_in) ? p[o * d_in + k] : 0.0f;
+    for (int base = 0; base < n; base += 8 * nt) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = base + u * nt + tid;
+            v[u] = i < n ? src_of(i) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = base + u * nt + tid;
+            if (i < n) dst[i] = v[u];
+        }
     }
+}
+
+__device__ inline void stage_net(SmemNet& s, const float* __restrict__ P, int d_in, int m) {
+    const float* p = P;
+    stage_loop(s.W1, W * DS, [&](int i) { const int o = i / DS, k = i % DS; return k < d_in ? __ldg(p + o * d_in + k) : 0.0f; });
     p += W * d_in;
-    for (int i = tid; i < WS; i += nt) s.b1[i] = (i < W) ? p[i] : 0.0f;
+    stage_loop(s.b1, WS, [&](int i) { return i < W ? __ldg(p + i) : 0.0f; });
     p += W;
     for (int l = 0; l < 3; ++l) {
-        for (int i = tid; i < W * WS; i += nt) {
-            const int o = i / WS, k = i % WS;
-            s.Wh[l][i] = (k < W) ? p[o * W + k] : 0.0f;
-        }
+        stage_loop(s.Wh[l], W * WS, [&](int i) { const int o = i / WS, k = i % WS; return k < W ? __ldg(p + o * W + k) : 0.0f; });
         p += W * W;
-        for (int i = tid; i < WS; i += nt) s.bh[l][i] = (i < W) ? p[i] : 0.0f;
+        stage_loop(s.bh[l], WS, [&](int i) { return i < W ? __ldg(p + i) : 0.0f; });
         p += W;
     }
-    for (int i = tid; i < SL_MAX_M * WS; i += nt) {
+    stage_loop(s.W5, SL_MAX_M * WS, [&](int i) {
         const int o = i / WS, k = i % WS;
-        s.W5[i] = (o < m && k < W) ? p[o * W + k] : 0.0f;
-    }
+        return (o < m && k < W) ? __ldg(p + o * W + k) : 0.0f;
+    });
     p += m * W;
-    for (int i = tid; i < SL_MAX_M; i += nt) s.b5[i] = (i < m) ? p[i] : 0.0f;
+    stage_loop(s.b5, SL_MAX_M, [&](int i) { return i < m ? __ldg(p + i) : 0.0f; });
 }
 
 template <int ACT>
