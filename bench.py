@@ -511,8 +511,9 @@ def main():
         th_a = torch.tensor([[0.1, 0.3]], device=dev)
         y0_a = torch.ones(1, device=dev)
         ws_a = torch.empty(sl.adjoint_workspace_size(n_a, 1, 64, 8, 2), dtype=torch.uint8, device=dev)
-        for pr, key in ((sl.PREC_FP32, "adjoint_fp32"), (sl.PREC_BF16, "adjoint_bf16")):
-            net_a = sl.make_net(P, 4, 7, prec=pr)
+        for pr, act_a, key in ((sl.PREC_FP32, sl.ACT_RELU, "adjoint_fp32"), (sl.PREC_BF16, sl.ACT_RELU, "adjoint_bf16"),
+                               (sl.PREC_BF16, sl.ACT_SOFTPLUS, "adjoint_bf16_softplus")):
+            net_a = sl.make_net(P, 4, 7, act=act_a, prec=pr)
             run_a = lambda: sl.seven_league_adjoint(sl.MODEL_MLP, net_a, th_a, y0_a, off_a, 1.0, 64, 7, 1, 1.0,
                                                     ckpt_k=8, ws=ws_a, total_paths=n_a)
             run_a()
@@ -525,7 +526,8 @@ def main():
             secondary[key + "_path_steps_per_s"] = n_a * 64 / (e0.elapsed_time(e1) * 1e-3)
             secondary[key + "_result"] = ("value %.5f dY0 %.5f dtheta %s"
                                           % (v_a.item(), d0_a.item(), [round(x, 5) for x in dth_a[0].tolist()]))
-        secondary["adjoint_workload"] = "GBM network, 1e6 paths x 64 steps, checkpoint every 8, call K=1"
+        secondary["adjoint_workload"] = ("GBM network, 1e6 paths x 64 steps, checkpoint every 8, call K=1 "
+                                         "(adjoint_bf16_softplus: the same weights read as a Softplus network)")
         # CIR adjoint on the trained CIR network (BF16 tcgen05 form): kappa=1, ybar=0.1, gamma=0.3,
         # Y0=0.1, 1e6 paths x 64 steps of dt=0.25 (inside the label rows' dt range), checkpoint every 8;
         # call K=1 lies far above the CIR range (every sensitivity is 0), K=ybar is the meaningful case

@@ -78,7 +78,7 @@ enum { SL_ACT_RELU = 0, SL_ACT_SOFTPLUS = 1 };
 enum { SL_PREC_FP32 = 0,        /* FP32 CUDA-core form */
        SL_PREC_BF16 = 1 };      /* tcgen05 BF16 tensor cores, FP32 accumulate, BF16 weights,
                                    activations split hi+lo in BF16; d_in <= SL_MAX_DIN_TC;
-                                   ReLU or Softplus in the sampler, ReLU in the adjoint */
+                                   ReLU or Softplus (sampler and adjoint) */
 enum { SL_PAYOFF_CALL = 0 };    /* f(Y_T) = max(Y_T - K, 0) */
 
 /*
@@ -333,12 +333,14 @@ size_t sl_adjoint_workspace_size(int64_t total_paths, int n_sets, int n_steps, i
  * backward of an autograd function.  out_paths: device FP32 [(2+p)][total]
  * per-path (f, df/dY0, df/dtheta_0..) or NULL (kept in the workspace).
  * Network forms: net->prec = SL_PREC_FP32 runs the FP32 CUDA-core form (one
- * launch). SL_PREC_BF16 (ReLU, d_in <= SL_MAX_DIN_TC) runs the tcgen05 form in
- * three launches on `stream`: the BF16 sampler (the same paths as
- * seven_league_simulate_batched) keeping the checkpoint rows, a compaction of
- * the in-the-money paths, and a reverse sweep over those paths only that
+ * launch). SL_PREC_BF16 (ReLU or Softplus, d_in <= SL_MAX_DIN_TC) runs the
+ * tcgen05 form in three launches on `stream`: the BF16 sampler (the same paths
+ * as seven_league_simulate_batched) keeping the checkpoint rows, a compaction
+ * of the in-the-money paths, and a reverse sweep over those paths only that
  * back-propagates through the same BF16 weights (hi + lo BF16 cotangents, FP32
- * accumulation). total_paths < 2^32 for the BF16 form.
+ * accumulation; ReLU patterns recorded as bits, Softplus derivatives taken from
+ * the pre-activations recomputed layer by layer). total_paths < 2^32 for the
+ * BF16 form.
  */
 int seven_league_adjoint(int model, const sl_net* net, const float* theta, int p, const float* Y0,
                          const int64_t* path_offsets, int n_sets, int64_t total_paths, float T,

@@ -388,8 +388,6 @@ int seven_league_adjoint(int model, const sl_net* net, const float* theta, int p
         if (net->act != SL_ACT_RELU && net->act != SL_ACT_SOFTPLUS) return set_error(SL_ERR_ARG, "act");
         if (net->prec != SL_PREC_FP32 && net->prec != SL_PREC_BF16) return set_error(SL_ERR_ARG, "prec");
         if (net->prec == SL_PREC_BF16) {
-            if (net->act != SL_ACT_RELU)
-                return set_error(SL_ERR_UNSUPPORTED, "the BF16 tensor-core form supports ReLU only");
             if (net->d_in > SL_MAX_DIN_TC)
                 return set_error(SL_ERR_UNSUPPORTED, "BF16 form: d_in=%d > %d", net->d_in, SL_MAX_DIN_TC);
         }

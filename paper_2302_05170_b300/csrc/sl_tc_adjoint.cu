@@ -24,8 +24,16 @@
 //     c. lambda <- d/dY_i, g_theta += d/dtheta.
 //  Per-set FP64 means come from the shared deterministic reduction.
 //
+// Softplus networks have no bit pattern to record: dz_l = dh_l * sigma(z_l) needs the
+// pre-activation itself.  Per step (last first) and per layer l = 4..1 of the backward
+// chain, each thread keeps dh_l of its row in registers while the tile recomputes the
+// step's forward up to z_l in the accumulator; sigma(z_l) = 1 / (1 + e^{-z_l}) is then
+// taken in FP32 from the accumulator, so nothing is stored and nothing is rounded beyond
+// the ReLU form.  Cost per step: 10 forward and 5 backward layer groups (ReLU: 4 + 5), plus
+// the segment's states recomputed from its checkpoint.
+//
 // Tensor memory per tile: 128 columns -- accumulator 0..63, A operand 64..119.
-// Shared memory per tile: the block's ReLU patterns, 8 steps x 4 layers x 2 words
+// Shared memory per tile (ReLU): the block's ReLU patterns, 8 steps x 4 layers x 2 words
 // per path (32 KB).
 #include "sl_tc_common.cuh"
 
@@ -197,6 +205,61 @@ __device__ __forceinline__ void tile_backward_bits(const Tile& T, uint32_t m0, u
     tc_fence_before();
 }
 
+// The accumulator row's columns 0..49 as FP32 values (the cotangent dh of a layer).
+__device__ __forceinline__ void tile_acc50(const Tile& T, float (&d)[SL_WIDTH]) {
+    tc_fence_after();
+    uint32_t v[32], v2[16], u[8];
+    tmem_ld32(T.taddr, v);
+    tmem_ld16(T.taddr + 32, v2);
+    tmem_ld8(T.taddr + 48, u);
+    tmem_wait_ld();
+#pragma unroll
+    for (int j = 0; j < 32; ++j) d[j] = __uint_as_float(v[j]);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) d[32 + j] = __uint_as_float(v2[j]);
+    d[48] = __uint_as_float(u[0]);
+    d[49] = __uint_as_float(u[1]);
+    tc_fence_before();
+}
+
+// Backward epilogue of a Softplus layer: the accumulator holds the layer's pre-activation
+// z (just recomputed); dz = dh * sigma(z), sigma(z) = 1 / (1 + e^{-z}) (0 when e^{-z}
+// overflows), split into BF16 hi + lo and written as the next A row (layout of
+// tile_backward_bits).
+__device__ __forceinline__ void tile_backward_sp(const Tile& T, const float (&dh)[SL_WIDTH]) {
+    tc_fence_after();
+    uint32_t v[32], v2[16], u[8];
+    tmem_ld32(T.taddr, v);
+    tmem_ld16(T.taddr + 32, v2);
+    tmem_ld8(T.taddr + 48, u);
+    tmem_wait_ld();
+    auto dz = [&](int j, uint32_t zb) {
+        return __float_as_uint(dh[j] * __frcp_rn(1.0f + __expf(-__uint_as_float(zb))));
+    };
+    const uint32_t at = T.taddr + 64;
+    uint32_t hw[16], lw[16];
+#pragma unroll
+    for (int i2 = 0; i2 < 16; ++i2) split_rn(dz(2 * i2, v[2 * i2]), dz(2 * i2 + 1, v[2 * i2 + 1]), hw[i2], lw[i2]);
+    tmem_st16(at, hw);
+    uint32_t h9[9], l9[9];
+#pragma unroll
+    for (int i2 = 0; i2 < 9; ++i2) {
+        const uint32_t ra = (i2 < 8) ? v2[2 * i2] : u[0];
+        const uint32_t rb = (i2 < 8) ? v2[2 * i2 + 1] : u[1];
+        split_rn(dz(32 + 2 * i2, ra), dz(33 + 2 * i2, rb), h9[i2], l9[i2]);
+    }
+    const uint32_t gb[16] = {h9[0], h9[1], h9[2], h9[3], h9[4], h9[5], h9[6], h9[7],
+                             h9[8], 0u, 0u, 0u, lw[0], lw[1], lw[2], lw[3]};
+    const uint32_t gc[16] = {lw[4], lw[5], lw[6], lw[7], lw[8], lw[9], lw[10], lw[11],
+                             lw[12], lw[13], lw[14], lw[15], l9[0], l9[1], l9[2], l9[3]};
+    const uint32_t gd[8] = {l9[4], l9[5], l9[6], l9[7], l9[8], 0u, 0u, 0u};
+    tmem_st16(at + 16, gb);
+    tmem_st16(at + 32, gc);
+    tmem_st8(at + 48, gd);
+    tmem_wait_st();
+    tc_fence_before();
+}
+
 // Cotangent of the collocation points, c_j = lambda * ell_j(X), as the A row
 // of W5^T: words 0..3 = hi pairs (c_0, c_1) .. (c_6, c_7), words 4..7 = lo pairs.
 __device__ __forceinline__ void tile_cotangent(const Tile& T, float lam) {
@@ -260,7 +323,10 @@ __device__ __forceinline__ void tile_begin_listed(Tile& T, const SimArgs& a, int
     T.z4 = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-template <int WG>
+template <int ACT>
+constexpr int mask_words_per_tile() { return ACT == SL_ACT_RELU ? kMaskWordsPerTile : 0; }
+
+template <int WG, int ACT>
 __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const AdjTC A) {
     constexpr int S = WG;
     constexpr uint32_t kCols = (S * 128 <= 128) ? 128 : (S * 128 <= 256) ? 256 : 512;
@@ -272,7 +338,7 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
     unsigned char* sB = smem;
     unsigned char* sBT = smem + kBBytes;
     uint32_t* masks = reinterpret_cast<uint32_t*>(sBT + kBTBytes);     // [S][kMaskSteps][4][2][128]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(masks + S * kMaskWordsPerTile);   // d_ready[S], drain
+    uint64_t* bars = reinterpret_cast<uint64_t*>(masks + S * mask_words_per_tile<ACT>());   // d_ready[S], drain
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + S + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -323,7 +389,7 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
     T.d_bar = smem_u32(&bars[wg]);
     T.bar_id = 1 + wg;
     T.dph = 0;
-    uint32_t* tmask = masks + wg * kMaskWordsPerTile + r;   // word (step, layer l, half h) at ((step*4 + l-1)*2 + h)*128
+    uint32_t* tmask = masks + wg * mask_words_per_tile<ACT>() + r;   // word (step, layer l, half h) at ((step*4 + l-1)*2 + h)*128
 
     const int64_t n_list = static_cast<int64_t>(*A.count);
     const int64_t n_tiles = (n_list + kTile - 1) / kTile;
@@ -345,7 +411,9 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
             const int i1 = min(i0 + A.k, a.n_steps);
             float Ys[kMaxCkptK];
             Ys[0] = A.ckpt[static_cast<int64_t>(c) * a.total + g];
-            if (i1 - i0 > kMaskSteps) {
+            // ReLU: blocks of kMaskSteps steps recorded at once; Softplus: one step at a time
+            constexpr int kBlk = (ACT == SL_ACT_RELU) ? kMaskSteps : 1;
+            if (i1 - i0 > kBlk) {
                 // a long segment: recompute its states first (Y_{i0+1} .. Y_{i1-1})
                 for (int i = i0; i < i1 - 1; ++i) {
                     T.Y = Ys[i - i0];
@@ -356,7 +424,7 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
 #pragma unroll
                     for (int l = 1; l <= 4; ++l) {
                         const bool w = tile_wait(T, abort_flag, a.status);
-                        if (w) tile_hidden(T);
+                        if (w) tile_hidden_act<ACT>(T);
                         ok = tile_sync_issue(T, C, l, w, issuer);
                         if (!ok) break;
                     }
@@ -368,6 +436,49 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
                     Ys[i - i0 + 1] = T.Y;
                 }
             }
+            if constexpr (ACT == SL_ACT_SOFTPLUS) {
+                for (int i = i1 - 1; ok && i >= i0; --i) {
+                    // backward chain with c_j = lambda * ell_j(X_i); dh4 = W5^T c
+                    tile_rng_any(T, a, i, blk);
+                    tile_cotangent(T, lam);
+                    ok = tile_sync_issue_T(T, CT, 0, ok, issuer);
+                    if (!ok) break;
+                    for (int lt = 1; lt <= 4; ++lt) {
+                        const int l = 5 - lt;               // dh_l is in the accumulator
+                        bool w = tile_wait(T, abort_flag, a.status);
+                        float dh[SL_WIDTH];
+                        if (w) tile_acc50(T, dh);
+                        // the step's forward again, up to z_l (issues 0 .. l-1)
+                        T.Y = Ys[i - i0];
+                        tile_features(T, a);
+                        ok = tile_sync_issue(T, C, 0, w, issuer);
+                        for (int ll = 1; ok && ll < l; ++ll) {
+                            const bool w2 = tile_wait(T, abort_flag, a.status);
+                            if (w2) tile_hidden_act<ACT>(T);
+                            ok = tile_sync_issue(T, C, ll, w2, issuer);
+                        }
+                        if (!ok) break;
+                        w = tile_wait(T, abort_flag, a.status);
+                        if (w) tile_backward_sp(T, dh);
+                        ok = tile_sync_issue_T(T, CT, lt, w, issuer);   // dh_{l-1} = W_l^T dz_l
+                        if (!ok) break;
+                    }
+                    if (!ok) break;
+                    const bool w = tile_wait(T, abort_flag, a.status);
+                    if (w) {
+                        tc_fence_after();
+                        uint32_t gf[8];
+                        tmem_ld8(T.taddr, gf);
+                        tmem_wait_ld();
+                        tc_fence_before();
+                        lam = __uint_as_float(gf[0]);
+#pragma unroll
+                        for (int q = 0; q < SL_MAX_DIN_TC - 2; ++q)
+                            if (q < p) gth[q] += __uint_as_float(gf[2 + q]);
+                    }
+                    ok = bar_and(T.bar_id, w);
+                }
+            } else {
             // blocks of at most kMaskSteps steps, last first: a forward pass over the block that
             // records every hidden layer's ReLU pattern, then the reverse steps of the block
             for (int j1 = i1; ok && j1 > i0;) {
@@ -423,6 +534,7 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
                 }
                 j1 = j0;
             }
+            }
         }
         if (!ok) break;
         if (valid) {
@@ -451,10 +563,11 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
     }
 }
 
-template <int WG>
+template <int WG, int ACT>
 int launch_reverse(const AdjTC& A, cudaStream_t st) {
-    auto kern = tc_adjoint_reverse_kernel<WG>;
-    const size_t smem = 1024 + kBBytes + kBTBytes + static_cast<size_t>(WG) * kMaskWordsPerTile * 4 + (WG + 1) * 8 + 16;
+    auto kern = tc_adjoint_reverse_kernel<WG, ACT>;
+    const size_t smem = 1024 + kBBytes + kBTBytes + static_cast<size_t>(WG) * mask_words_per_tile<ACT>() * 4 +
+                        (WG + 1) * 8 + 16;
     int rc = cuda_error(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(smem)),
                         "tc_adjoint attribute");
@@ -472,7 +585,7 @@ int launch_reverse(const AdjTC& A, cudaStream_t st) {
 
 }  // namespace
 
-// Tensor-core adjoint: requires an MLP model with ReLU, d_in <= 7, m <= 8.
+// Tensor-core adjoint: requires an MLP model (ReLU or Softplus), d_in <= 7, m <= 8.
 // ckpt: [n_ckpt + 1][total] (the sampler writes rows 0 .. n_steps / k); yt:
 // [total]; list: [total]; count: one word.
 int launch_tc_adjoint(const SimArgs& s, float K, int k, int n_ckpt, float* ckpt, float* pv, float* yt,
@@ -506,7 +619,10 @@ int launch_tc_adjoint(const SimArgs& s, float K, int k, int n_ckpt, float* ckpt,
     A.pv = pv;
     A.list = list;
     A.count = count;
-    return launch_reverse<3>(A, st);
+    // Softplus keeps a layer's cotangent (50 floats per thread) live across the forward
+    // recompute: two warpgroups per CTA leave 255 registers per thread
+    if (s.act == SL_ACT_SOFTPLUS) return launch_reverse<2, SL_ACT_SOFTPLUS>(A, st);
+    return launch_reverse<3, SL_ACT_RELU>(A, st);
 }
 
 }  // namespace sl

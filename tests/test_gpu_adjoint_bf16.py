@@ -1,5 +1,5 @@
-"""GPU parity of the BF16 tensor-core adjoint (network model, ReLU) against the
-FP64 oracle run on the same BF16-valued weights and biases.
+"""GPU parity of the BF16 tensor-core adjoint (network model, ReLU or Softplus)
+against the FP64 oracle run on the same BF16-valued weights and biases.
 
 The tensor-core form samples the same paths as the BF16 sampler and
 back-propagates through the same BF16 weights with BF16 hi + lo cotangents and
@@ -15,6 +15,8 @@ FP32 accumulation.  Its per-path values are checked like the sampler's:
   linear pieces and the same 2e-3 gate applies.  Paths with a smaller margin
   may follow a different piece; over all paths (far from the payoff kink) the
   sensitivities must still agree within the gate for at least 97% of paths;
+* Softplus networks are smooth: every path away from the payoff kink is held to the
+  2e-3 gate (no margin selection);
 * per-set means: the kernel's FP64 set means equal the means of its own per-path values
   (rel 1e-12); against the oracle, the means over a set's paths with margin >= MARGIN (away
   from the kink) agree within 2e-3 of (mean |per-path value| + 0.1).  Over all paths the means
@@ -44,8 +46,8 @@ def _thetas(n_sets, p, seed):
     return np.random.default_rng(seed).uniform(0.05, 0.4, (n_sets, p)).astype(np.float32)
 
 
-def _adj(sl, P, d_in, m, th, y0, off, T, n_steps, seed, K, k, prec):
-    net = sl.make_net(_dev(P), d_in, m, prec=prec)
+def _adj(sl, P, d_in, m, th, y0, off, T, n_steps, seed, K, k, prec, act=0):
+    net = sl.make_net(_dev(P), d_in, m, act=act, prec=prec)
     p = d_in - 2
     total = int(off[-1])
     paths = torch.empty((2 + p, total), dtype=torch.float32, device="cuda")
@@ -58,26 +60,29 @@ def _adj(sl, P, d_in, m, th, y0, off, T, n_steps, seed, K, k, prec):
     return v.cpu().numpy(), d0.cpu().numpy(), dth.cpu().numpy(), paths.cpu().numpy()
 
 
-def _strike(orc, P, d_in, m, th, y0, off, T, n_steps, seed, idx=None):
+def _strike(orc, P, d_in, m, th, y0, off, T, n_steps, seed, idx=None, act=0):
     """A strike near the median of the oracle's Y_T (so about half the paths are in the money)."""
     Pb = W.bf16_round(P).astype(np.float64)
-    yt = orc.seven_league_paths(0, Pb, th, y0, off, T, n_steps, m, seed, d_in=d_in, idx=idx)
+    yt = orc.seven_league_paths(0, Pb, th, y0, off, T, n_steps, m, seed, d_in=d_in, idx=idx, act=act)
     return float(np.median(yt))
 
 
-def _check(orc, P, d_in, m, th, y0, off, T, n_steps, seed, K, got):
+def _check(orc, P, d_in, m, th, y0, off, T, n_steps, seed, K, got, act=0):
     v, d0, dth, paths = got
     Pb = W.bf16_round(P).astype(np.float64)
-    yt, val, g = orc.seven_league_payoff_grad(0, Pb, th, y0, off, T, n_steps, m, seed, K, d_in=d_in)
+    yt, val, g = orc.seven_league_payoff_grad(0, Pb, th, y0, off, T, n_steps, m, seed, K, d_in=d_in, act=act)
     assert 0.2 < np.mean(val > 0) < 0.8          # a non-trivial mix of in- and out-of-the-money paths
     idx = np.arange(len(yt))
     s, q = flat_sets(off, idx)
     mx = max_abs_normals(orc, seed, 0, s, q, n_steps)
     ok, *info = gate(rel_err(paths[0], val, 1.0), mx, TOL)
     assert ok, ("payoff", info)
-    mg = orc.seven_league_relu_margin(Pb, th, y0, off, T, n_steps, m, seed, d_in=d_in)
     far = np.abs(yt - K) > 5 * TOL * (np.abs(yt) + 1.0)
-    sure = far & (mg >= MARGIN)
+    if act == 0:
+        mg = orc.seven_league_relu_margin(Pb, th, y0, off, T, n_steps, m, seed, d_in=d_in)
+        sure = far & (mg >= MARGIN)
+    else:                                       # smooth network: no linear pieces to switch
+        sure = far
     for c in range(g.shape[1]):
         err = rel_err(paths[1 + c], g[:, c], 1.0)
         if sure.any():
@@ -120,6 +125,39 @@ def test_paths_vs_oracle(sl, orc, d_in, m, counts, n_steps, k):
     K = _strike(orc, P, d_in, m, th, y0, off, 2.0, n_steps, 5)
     got = _adj(sl, P, d_in, m, th, y0, off, 2.0, n_steps, 5, K, k, sl.PREC_BF16)
     _check(orc, P, d_in, m, th, y0, off, 2.0, n_steps, 5, K, got)
+
+
+@pytest.mark.parametrize("d_in,m,counts,n_steps,k", [
+    (4, 7, [3000, 129, 5000], 16, 4),
+    (5, 5, [0, 1, 4000, 383], 10, 3),
+    (3, 2, [1500], 6, 32),
+    (4, 7, [37], 1, 1),
+    (6, 8, [2500], 9, 9),
+])
+def test_softplus_paths_vs_oracle(sl, orc, d_in, m, counts, n_steps, k):
+    """Softplus network (the paper's activation): the reverse sweep recomputes each layer's
+    pre-activation; per-path sensitivities on every path away from the payoff kink."""
+    P = W.xavier_params(d_in, m, seed=20 + d_in + m)
+    th = _thetas(len(counts), d_in - 2, m)
+    off = W.offsets_from_counts(counts)
+    y0 = np.linspace(0.9, 1.1, len(counts)).astype(np.float32)
+    K = _strike(orc, P, d_in, m, th, y0, off, 2.0, n_steps, 5, act=1)
+    got = _adj(sl, P, d_in, m, th, y0, off, 2.0, n_steps, 5, K, k, sl.PREC_BF16, act=1)
+    assert _check(orc, P, d_in, m, th, y0, off, 2.0, n_steps, 5, K, got, act=1) > 0.9
+
+
+def test_softplus_bf16_vs_fp32_forms(sl, orc):
+    """Both forms of a Softplus network on the same paths: the set sensitivities agree to the
+    BF16 weight quantisation (each form against the oracle on its own weights above)."""
+    P = W.xavier_params(4, 7, seed=31)
+    th = _thetas(2, 2, 7)
+    off = W.offsets_from_counts([20000, 15000])
+    y0 = np.array([1.0, 0.95], np.float32)
+    K = _strike(orc, P, 4, 7, th, y0, off, 2.0, 16, 6, idx=np.arange(0, 35000, 7), act=1)
+    a = _adj(sl, P, 4, 7, th, y0, off, 2.0, 16, 6, K, 8, sl.PREC_BF16, act=1)
+    b = _adj(sl, P, 4, 7, th, y0, off, 2.0, 16, 6, K, 8, sl.PREC_FP32, act=1)
+    for x, y in zip(a[:3], b[:3]):
+        assert np.allclose(x, y, rtol=0.05, atol=0.02 * np.abs(y).max() + 1e-6), (x, y)
 
 
 def _ou_network(yb, sg, lam, dt, m, shift=2.0, noise=0.0, seed=0):
