@@ -221,7 +221,7 @@ size_t sl_cdc_workspace_size(int64_t total_paths, int n_sets, int n_steps);
  * Batched 7L-CDC sampler.  Arguments, outputs and errors as
  * seven_league_simulate_batched, plus marg_net (SL_MODEL_MLP only; NULL = use
  * net; same d_in and m as net, its own activation).  The workspace holds, at
- * byte offset 256, the tables of the call: FP32 [n_sets][n_steps][192] with,
+ * byte offset 256, the tables of the call: FP32 [n_sets][n_steps][224] with,
  * per (set, step): [0,8) z (the marginal nodes, zero beyond m); [8,16) w
  * (their barycentric weights 1/prod_{l!=k}(z_k - z_l), computed in FP64 from
  * the FP32 nodes; all zero when the nodes coincide); [16,80) C[8][8] (row k =
@@ -230,9 +230,12 @@ size_t sl_cdc_workspace_size(int64_t total_paths, int n_sets, int n_steps);
  * two smallest and the two largest nodes (ties to the lower index; FP64,
  * rounded once; 0 if the two nodes coincide); [96,104) C_lo and [104,112)
  * C_hi, the rows of the smallest and the largest node; [112] z_lo, [113]
- * z_hi; [114,120) zero; [120,128) a copy of C[0]; [128,192) Cw[8][8] =
- * w_k b_j C[k][j] (b_j the barycentric weights of the Gauss-Hermite points,
- * FP64 product rounded once; zero when the nodes coincide).  Nodes that
+ * z_hi; [114,120) zero; then monomial coefficients (a = 0..m-1, FP64 sums
+ * rounded once) of g_m through a row y, sum_j y_j b_j prod_{l!=j}(X - x_l)
+ * (b_j the Gauss-Hermite points' barycentric weights): [120,128) D of row
+ * C[0]; [128,192) A[k][a] of w_k times row k of C (zero when the nodes
+ * coincide); [192,200) of C_lo, [200,208) of S_lo, [208,216) of C_hi,
+ * [216,224) of S_hi.  Nodes that
  * coincide only in part give non-finite paths (SL_DEV_NONFINITE).
  */
 int seven_league_cdc_simulate_batched(int model, const sl_net* net, const sl_net* marg_net,

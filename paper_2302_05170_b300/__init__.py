@@ -277,7 +277,7 @@ def seven_league_simulate(model, theta, Y0, T, n_steps, m, weights, n_paths, see
     return out
 
 
-CDC_TABLE_FLOATS = 192  # per (set, step): z | w | C | S_lo | S_hi | C_lo | C_hi | z_lo, z_hi | C[0] | Cw
+CDC_TABLE_FLOATS = 224  # per (set, step): z | w | C | S_lo | S_hi | C_lo | C_hi | z_lo, z_hi | D | A | B_lo | Sm_lo | B_hi | Sm_hi
 
 
 def cdc_workspace_size(total_paths, n_sets, n_steps):
@@ -309,7 +309,7 @@ def seven_league_cdc_simulate_batched(model, net, theta, Y0, path_offsets, T, n_
 
 
 def cdc_tables(ws, n_sets, n_steps):
-    """View of the tables a 7L-CDC call left in its workspace: FP32 [n_sets, n_steps, 192]."""
+    """View of the tables a 7L-CDC call left in its workspace: FP32 [n_sets, n_steps, 224]."""
     n = n_sets * n_steps * CDC_TABLE_FLOATS
     return ws[256:256 + 4 * n].view(_torch().float32).view(n_sets, n_steps, CDC_TABLE_FLOATS)
 

@@ -32,15 +32,22 @@ namespace {
 using namespace simt;
 
 // Table of one (set, step), floats: z[8] | w[8] | C[8][8] | S_lo[8] | S_hi[8] |
-// C_lo[8] | C_hi[8] | z_lo, z_hi, pad | C[0] | Cw[8][8].  Below the smallest node z_lo
-// the points are C_lo + (Y - z_lo) S_lo (the line through the two smallest nodes),
-// above z_hi likewise with the two largest.  Cw[k][j] = w_k b_j C[k][j] (b_j the
-// barycentric weights of the Gauss-Hermite points) folds both interpolations'
-// weights into the table: inside the hull
-//   Y_{i+1} = sum_k P_k(Y) sum_j Cw[k][j] Q_j(X),
-// P_k(Y) = prod_{l!=k} (Y - z_l), Q_j(X) = prod_{l!=j} (X - x_l).
-constexpr int kTabFloats = 192;
-constexpr int kSlo = 80, kShi = 88, kClo = 96, kChi = 104, kZlo = 112, kRow0 = 120, kCw = 128;
+// C_lo[8] | C_hi[8] | z_lo, z_hi, pad | D[8] | A[8][8] | B_lo[8] | Sm_lo[8] | B_hi[8] |
+// Sm_hi[8].  Below the smallest node z_lo the points are C_lo + (Y - z_lo) S_lo (the
+// line through the two smallest nodes), above z_hi likewise with the two largest.
+// g_m through points y is the polynomial sum_j y_j b_j Q_j(X), Q_j(X) = prod_{l!=j}
+// (X - x_l), b_j the barycentric weights of the Gauss-Hermite points; its monomial
+// coefficients sum_j y_j (b_j q_j[a]) are formed once per (set, step) in FP64 (q_j[a]
+// the coefficients of Q_j, from the host):
+//   A[k][a]: w_k times those of row k of C, so that inside the hull
+//            Y_{i+1} = sum_k P_k(Y) sum_a A[k][a] X^a,  P_k(Y) = prod_{l!=k} (Y - z_l);
+//   D: those of row 0 (coinciding nodes); B_lo, Sm_lo (B_hi, Sm_hi): those of C_lo and
+//      S_lo (C_hi, S_hi), so that beyond the hull Y_{i+1} = B(X) + (Y - z_edge) Sm(X).
+// The path kernel evaluates them by Horner's rule in X (X ~ N(0, 1): the coefficients
+// of a collocation row decay, and Horner is as accurate as the barycentric form there).
+constexpr int kTabFloats = 224;
+constexpr int kSlo = 80, kShi = 88, kClo = 96, kChi = 104, kZlo = 112, kD = 120, kA = 128, kBlo = 192,
+              kSmlo = 200, kBhi = 208, kSmhi = 216;
 constexpr int kPathThreads = 256;
 
 struct CdcArgs {
@@ -56,6 +63,7 @@ struct CdcArgs {
     int m;
     float* tab;                // [n_sets][n_steps][kTabFloats]
     GHConst gh;
+    double bq[SL_MAX_M][SL_MAX_M];   // b_j q_j[a]: monomial coefficients of b_j Q_j (FP64, zero past m)
 };
 
 // Collocation points of the exact models over the horizon h from Y:
@@ -255,8 +263,8 @@ __global__ void __launch_bounds__(kTabThreads, 2) cdc_table_kernel(const CdcArgs
             }
         }
         __syncthreads();
-        // (C) thread (e, k): node k of entry e -- its weight, row k of C and Cw, and
-        // column k of the continuation lines
+        // (C) thread (e, k): node k of entry e -- its weight, row k of C and of A, column k
+        // of the continuation lines, and coefficient a = k of the monomial rows D, B, Sm
         if (threadIdx.x < kBatch * 8) {
             const int e = threadIdx.x / 8, k = threadIdx.x % 8;
             const int64_t u = base + e;
@@ -285,10 +293,11 @@ __global__ void __launch_bounds__(kTabThreads, 2) cdc_table_kernel(const CdcArgs
                 }
                 t[k] = z[k];
                 t[8 + k] = static_cast<float>(wk);
-                for (int j = 0; j < SL_MAX_M; ++j) {
-                    const float c = C[k * 8 + j];
-                    t[16 + 8 * k + j] = c;
-                    t[kCw + 8 * k + j] = (j < m) ? static_cast<float>(wk * a.gh.bary[j] * c) : 0.0f;
+                for (int j = 0; j < SL_MAX_M; ++j) t[16 + 8 * k + j] = C[k * 8 + j];
+                for (int ai = 0; ai < SL_MAX_M; ++ai) {   // row k of A
+                    double acc = 0.0;
+                    for (int j = 0; j < m; ++j) acc += static_cast<double>(C[k * 8 + j]) * a.bq[j][ai];
+                    t[kA + 8 * k + ai] = static_cast<float>(wk * acc);
                 }
                 // column k of the lines through the two outermost nodes on each side
                 const double dlo = static_cast<double>(z[lo2]) - z[lo], dhi = static_cast<double>(z[hi2]) - z[hi];
@@ -297,8 +306,23 @@ __global__ void __launch_bounds__(kTabThreads, 2) cdc_table_kernel(const CdcArgs
                 t[kChi + k] = chi;
                 t[kSlo + k] = (k < m && dlo != 0.0) ? static_cast<float>((static_cast<double>(C[lo2 * 8 + k]) - clo) / dlo) : 0.0f;
                 t[kShi + k] = (k < m && dhi != 0.0) ? static_cast<float>((static_cast<double>(C[hi2 * 8 + k]) - chi) / dhi) : 0.0f;
-                t[kRow0 + k] = C[k];
                 t[kZlo + k] = k == 0 ? z[lo] : k == 1 ? z[hi] : 0.0f;   // z_lo, z_hi, then zero padding
+                // coefficient k of the monomial rows (the lines' slopes are linear in the rows:
+                // sum_j S_j bq[j][k] = (sum_j C[b][j] bq[j][k] - sum_j C[a][j] bq[j][k]) / (z_b - z_a))
+                double d0 = 0.0, blo = 0.0, blo2 = 0.0, bhi = 0.0, bhi2 = 0.0;
+                for (int j = 0; j < m; ++j) {
+                    const double f = a.bq[j][k];
+                    d0 += static_cast<double>(C[j]) * f;
+                    blo += static_cast<double>(C[lo * 8 + j]) * f;
+                    blo2 += static_cast<double>(C[lo2 * 8 + j]) * f;
+                    bhi += static_cast<double>(C[hi * 8 + j]) * f;
+                    bhi2 += static_cast<double>(C[hi2 * 8 + j]) * f;
+                }
+                t[kD + k] = static_cast<float>(d0);
+                t[kBlo + k] = static_cast<float>(blo);
+                t[kSmlo + k] = dlo != 0.0 ? static_cast<float>((blo2 - blo) / dlo) : 0.0f;
+                t[kBhi + k] = static_cast<float>(bhi);
+                t[kSmhi + k] = dhi != 0.0 ? static_cast<float>((bhi2 - bhi) / dhi) : 0.0f;
             }
         }
         __syncthreads();
@@ -329,26 +353,26 @@ __device__ __forceinline__ void load8(const float* p, float (&v)[8]) {
     v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
 }
 
+// sum_a c[a] X^a for a < M (Horner).
+template <int M>
+__device__ __forceinline__ float horner(const float (&c)[8], float X) {
+    float h = c[M - 1];
+#pragma unroll
+    for (int a = M - 2; a >= 0; --a) h = fmaf(h, X, c[a]);
+    return h;
+}
+
 // One step of NP paths of the same (set, step) table t: Y[p] <- g_m(X[p]) through the
 // conditional points at Y[p].  The table is loaded once for all NP paths.
 template <int M, int NP>
-__device__ __forceinline__ void cdc_step(const float* __restrict__ t, float (&Y)[NP], const float (&X)[NP],
-                                         const float (&gx)[8], const float (&gb)[8]) {
-    float Q[NP][M];
-#pragma unroll
-    for (int p = 0; p < NP; ++p) prod_except<M>(X[p], gx, Q[p]);
+__device__ __forceinline__ void cdc_step(const float* __restrict__ t, float (&Y)[NP], const float (&X)[NP]) {
     const float4 w4 = __ldg(reinterpret_cast<const float4*>(t + 8));
     const float2 edge = __ldg(reinterpret_cast<const float2*>(t + kZlo));
     float row[8];
     if (w4.x == 0.0f) {                      // coinciding nodes: every path at z_0
-        load8(t + kRow0, row);
+        load8(t + kD, row);
 #pragma unroll
-        for (int p = 0; p < NP; ++p) {
-            float y = 0.0f;
-#pragma unroll
-            for (int j = 0; j < M; ++j) y = fmaf(row[j] * gb[j], Q[p][j], y);
-            Y[p] = y;
-        }
+        for (int p = 0; p < NP; ++p) Y[p] = horner<M>(row, X[p]);
         return;
     }
     bool out[NP];
@@ -368,14 +392,9 @@ __device__ __forceinline__ void cdc_step(const float* __restrict__ t, float (&Y)
     }
 #pragma unroll
     for (int k = 0; k < M; ++k) {
-        load8(t + kCw + 8 * k, row);
+        load8(t + kA + 8 * k, row);
 #pragma unroll
-        for (int p = 0; p < NP; ++p) {
-            float v = 0.0f;
-#pragma unroll
-            for (int j = 0; j < M; ++j) v = fmaf(row[j], Q[p][j], v);
-            acc[p] = fmaf(P[p][k], v, acc[p]);
-        }
+        for (int p = 0; p < NP; ++p) acc[p] = fmaf(P[p][k], horner<M>(row, X[p]), acc[p]);
     }
     float ynew[NP];
 #pragma unroll
@@ -385,14 +404,11 @@ __device__ __forceinline__ void cdc_step(const float* __restrict__ t, float (&Y)
         for (int p = 0; p < NP; ++p) {
             if (!out[p]) continue;
             const bool below = Y[p] < edge.x;
-            float sl[8];
-            load8(t + (below ? kClo : kChi), row);
-            load8(t + (below ? kSlo : kShi), sl);
+            float sm[8];
+            load8(t + (below ? kBlo : kBhi), row);
+            load8(t + (below ? kSmlo : kSmhi), sm);
             const float dY = Y[p] - (below ? edge.x : edge.y);
-            float y = 0.0f;
-#pragma unroll
-            for (int j = 0; j < M; ++j) y = fmaf(fmaf(dY, sl[j], row[j]) * gb[j], Q[p][j], y);
-            ynew[p] = y;
+            ynew[p] = fmaf(dY, horner<M>(sm, X[p]), horner<M>(row, X[p]));
         }
     }
 #pragma unroll
@@ -403,8 +419,7 @@ __device__ __forceinline__ void cdc_step(const float* __restrict__ t, float (&Y)
 // indices g[p]; write[p] false for a padding lane).
 template <int M, int NP>
 __device__ __forceinline__ void cdc_paths(const SimArgs& a, const float* __restrict__ ts, int s,
-                                          const int64_t (&q)[NP], const int64_t (&g)[NP], const bool (&write)[NP],
-                                          const float (&gx)[8], const float (&gb)[8]) {
+                                          const int64_t (&q)[NP], const int64_t (&g)[NP], const bool (&write)[NP]) {
     float Y[NP], X[NP];
     float4 z4[NP];
     const float y0 = __ldg(a.Y0 + s);
@@ -421,7 +436,7 @@ __device__ __forceinline__ void cdc_paths(const SimArgs& a, const float* __restr
                                 static_cast<uint32_t>(i >> 2));
             X[p] = pick4(z4[p], i & 3);
         }
-        cdc_step<M, NP>(ts + static_cast<int64_t>(i) * kTabFloats, Y, X, gx, gb);
+        cdc_step<M, NP>(ts + static_cast<int64_t>(i) * kTabFloats, Y, X);
         if (a.out_grid) {
 #pragma unroll
             for (int p = 0; p < NP; ++p)
@@ -442,13 +457,7 @@ __device__ __forceinline__ void cdc_paths(const SimArgs& a, const float* __restr
 constexpr int kPair = 2;
 
 template <int M>
-__global__ void __launch_bounds__(kPathThreads) cdc_path_kernel(const SimArgs a, const float* __restrict__ tab) {
-    float gx[8], gb[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        gx[j] = j < M ? a.gh.x[j] : 0.0f;
-        gb[j] = j < M ? a.gh.bary[j] : 0.0f;
-    }
+__global__ void __launch_bounds__(kPathThreads, 4) cdc_path_kernel(const SimArgs a, const float* __restrict__ tab) {
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x * kPair;
     for (int64_t g0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) * kPair; g0 < a.total;
          g0 += stride) {
@@ -465,15 +474,13 @@ __global__ void __launch_bounds__(kPathThreads) cdc_path_kernel(const SimArgs a,
             same = same && s[p] == s[0];
         }
         if (same) {
-            cdc_paths<M, kPair>(a, tab + static_cast<int64_t>(s[0]) * a.n_steps * kTabFloats, s[0], q, g, write,
-                                gx, gb);
+            cdc_paths<M, kPair>(a, tab + static_cast<int64_t>(s[0]) * a.n_steps * kTabFloats, s[0], q, g, write);
         } else {
 #pragma unroll
             for (int p = 0; p < kPair; ++p) {
                 const int64_t q1[1] = {q[p]}, g1[1] = {g[p]};
                 const bool w1[1] = {write[p]};
-                cdc_paths<M, 1>(a, tab + static_cast<int64_t>(s[p]) * a.n_steps * kTabFloats, s[p], q1, g1, w1,
-                                gx, gb);
+                cdc_paths<M, 1>(a, tab + static_cast<int64_t>(s[p]) * a.n_steps * kTabFloats, s[p], q1, g1, w1);
             }
         }
     }
@@ -556,6 +563,28 @@ int launch_paths(const SimArgs& a, const float* tab, cudaStream_t st) {
     }
 }
 
+// bq[j][a]: the monomial coefficients of b_j Q_j(X) = b_j prod_{l!=j} (X - x_l) (FP64,
+// from the FP64 Gauss-Hermite points; zero for j or a >= m).
+int gh_monomials(int m, double (&bq)[SL_MAX_M][SL_MAX_M]) {
+    double x[SL_MAX_M], w[SL_MAX_M], b[SL_MAX_M];
+    const int rc = gauss_hermite_fp64(m, x, w, b);
+    if (rc) return rc;
+    for (int j = 0; j < SL_MAX_M; ++j)
+        for (int ai = 0; ai < SL_MAX_M; ++ai) bq[j][ai] = 0.0;
+    for (int j = 0; j < m; ++j) {
+        double c[SL_MAX_M] = {1.0};          // coefficients, lowest degree first
+        int deg = 0;
+        for (int l = 0; l < m; ++l) {
+            if (l == j) continue;
+            for (int ai = deg + 1; ai >= 1; --ai) c[ai] = c[ai - 1] - x[l] * c[ai];   // times (X - x_l)
+            c[0] = -x[l] * c[0];
+            ++deg;
+        }
+        for (int ai = 0; ai < m; ++ai) bq[j][ai] = b[j] * c[ai];
+    }
+    return SL_OK;
+}
+
 size_t table_bytes(int n_sets, int n_steps) {
     return align256(static_cast<size_t>(n_sets) * static_cast<size_t>(n_steps) * kTabFloats * sizeof(float));
 }
@@ -630,6 +659,8 @@ int seven_league_cdc_simulate_batched(int model, const sl_net* net, const sl_net
     c.m = m;
     c.tab = tab;
     rc = make_gh_const(m, &c.gh);
+    if (rc) return rc;
+    rc = gh_monomials(m, c.bq);
     if (rc) return rc;
 
     SimArgs a{};

@@ -168,7 +168,7 @@ def test_cdc_argument_checks(lib):
             a["T"], a["n_steps"], a["m"], a["seed"], a["yt"], a["grid"], a["mean"], a["var"], a["ws"],
             a["ws_bytes"], a["stream"])
     need = sl.cdc_workspace_size(10, 1, 2)
-    assert need >= 256 + 2 * 192 * 4
+    assert need >= 256 + 2 * 224 * 4
     assert call() == sl.SL_ERR_WORKSPACE                        # 256 bytes hold no tables
     assert call(m=9) == sl.SL_ERR_UNSUPPORTED
     assert call(n_steps=0) == sl.SL_ERR_UNSUPPORTED
@@ -185,9 +185,9 @@ def test_cdc_argument_checks(lib):
     assert call(yt=None) == sl.SL_ERR_ARG
     assert call(ws=None) == sl.SL_ERR_WORKSPACE
     assert call(model=sl.MODEL_GBM_EXACT, net=None, p=3) == sl.SL_ERR_ARG
-    # with out_YT given the call needs the status word and the tables: 256 + align256(2 * 768)
-    assert call(model=sl.MODEL_OU_EXACT, net=None, p=3, ws_bytes=1791) == sl.SL_ERR_WORKSPACE
-    assert sl.cdc_workspace_size(10 ** 6, 16, 16) >= 256 + 16 * 16 * 768 + 4 * 10 ** 6
+    # with out_YT given the call needs the status word and the tables: 256 + align256(2 * 896)
+    assert call(model=sl.MODEL_OU_EXACT, net=None, p=3, ws_bytes=2047) == sl.SL_ERR_WORKSPACE
+    assert sl.cdc_workspace_size(10 ** 6, 16, 16) >= 256 + 16 * 16 * 896 + 4 * 10 ** 6
 
 
 def test_workspace_sizes(lib):

@@ -140,11 +140,18 @@ def test_every_m(sl, orc, m):
     _check(orc, r["yt"], _oracle(orc, 1, None, th, y0, off, 1.0, 6, m, 5, 1.0), off, 5, 6, 1.0)
 
 
-def _gauss_hermite_fp32(m):
-    """The library's Gauss-Hermite points and barycentric weights as the kernels see them (FP32)."""
-    import paper_2302_05170_b300 as sl
-    x, w, b = sl.gauss_hermite(m)
-    return (np.asarray(x, np.float32).astype(np.float64), w, np.asarray(b, np.float32).astype(np.float64))
+def _gh_monomials(m):
+    """[j][a]: monomial coefficients of b_j prod_{l!=j} (X - x_l) from numpy's Gauss-Hermite points."""
+    from numpy.polynomial import hermite_e, polynomial as Pn
+    x = hermite_e.hermegauss(m)[0]
+    out = np.zeros((m, m))
+    for j in range(m):
+        c = np.array([1.0])
+        for l in range(m):
+            if l != j:
+                c = Pn.polymul(c, [-x[l], 1.0])
+        out[j] = c / np.prod([x[j] - x[l] for l in range(m) if l != j])
+    return out
 
 
 def _tables_vs_oracle(tab, z, C, m, tol):
@@ -176,14 +183,28 @@ def _tables_vs_oracle(tab, z, C, m, tol):
         slope = (take(Cc, ib) - take(Cc, ia)) / (zb - za)[..., None]
         assert np.allclose(t[..., scol:scol + m], slope, rtol=2 ** -23, atol=0)
     assert np.all(tab[:, :, 114:120] == 0)
-    assert np.array_equal(tab[:, :, 120:128], tab[:, :, 16:24])          # copy of C[0]
-    # Cw[k][j] = w_k b_j C[k][j] (w_k in FP64 from the FP32 nodes, b_j of the FP32 Gauss-Hermite
-    # points, one rounding)
-    _, _, b = _gauss_hermite_fp32(m)
-    Cw = tab[:, 1:, 128:].reshape(n_sets, n_steps - 1, 8, 8)[..., :m, :m].astype(np.float64)
-    want = want_w[..., :, None] * b[None, None, None, :] * Cc
-    assert np.allclose(Cw, want, rtol=2 ** -22, atol=0)
-    assert np.all(tab[:, 0, 128:] == 0)
+    # monomial rows of g_m: coefficient a of sum_j y_j b_j Q_j(X), Q_j = prod_{l!=j} (X - x_l), for
+    # y = row k of C times w_k (A), row 0 (D), the outer rows and slopes (B, Sm); FP64 from the
+    # kernel's own FP32 entries, one rounding (the tolerance scales with the summands' size)
+    bq = _gh_monomials(m)                                              # [j][a]
+    t0 = tab.astype(np.float64)
+    Call = t0[..., 16:80].reshape(n_sets, n_steps, 8, 8)[..., :m, :m]
+    wall = t0[..., 8:8 + m]
+    def near(got, rows, scale_rows):
+        want = rows @ bq
+        size = np.abs(scale_rows) @ np.abs(bq)
+        assert np.all(np.abs(got - want) <= 2 ** -21 * size + 1e-30), np.abs(got - want).max()
+    A = t0[..., 128:192].reshape(n_sets, n_steps, 8, 8)[..., :m, :m]
+    near(A, wall[..., :, None] * Call, wall[..., :, None] * Call)
+    near(t0[..., 120:120 + m], Call[..., 0, :], Call[..., 0, :])
+    for zcol, ccol, scol, bcol, smcol in ((112, 96, 80, 192, 200), (113, 104, 88, 208, 216)):
+        near(t0[..., bcol:bcol + m], t0[..., ccol:ccol + m], t0[..., ccol:ccol + m])
+        live = wall[..., 0] != 0
+        sm = t0[..., smcol:smcol + m]
+        want = t0[..., scol:scol + m] @ bq
+        size = (np.abs(t0[..., scol:scol + m]) @ np.abs(bq))
+        assert np.all(np.abs(sm - want)[live] <= (2 ** -20 * size + 1e-30)[live])
+    assert np.all(tab[:, :, 120 + m:128] == 0) and np.all(tab[:, 0, 128:192] == 0)
 
 
 @pytest.mark.parametrize("act", [0, 1])
