@@ -197,7 +197,8 @@ __device__ __forceinline__ void group_map(const SmemNet& net, float* in, float* 
 
 size_t table_smem_bytes(int model) {
     return (model == SL_MODEL_MLP ? 2 * sizeof(SmemNet) : 0) +
-           (static_cast<size_t>(kGroups) * 2 * kBufStride + kBatch * 8 + kBatch * 64 + kBatch * 8) * sizeof(float);
+           (static_cast<size_t>(kGroups) * 2 * kBufStride + kBatch * 8 + kBatch * 64 + kBatch * 8) * sizeof(float) +
+           static_cast<size_t>(kBatch) * (8 + 2) * sizeof(double) + static_cast<size_t>(kBatch) * 4 * sizeof(int);
 }
 
 template <int MODEL, int ACT, int MACT>
@@ -209,6 +210,9 @@ __global__ void __launch_bounds__(kTabThreads, 2) cdc_table_kernel(const CdcArgs
     float* zs = bufs + kGroups * 2 * kBufStride;   // [kBatch][8] marginal nodes
     float* Cs = zs + kBatch * 8;                   // [kBatch][8][8] conditional rows
     float* ths = Cs + kBatch * 64;                 // [kBatch][8]: Y0 of the entry's set, then theta
+    double* wsh = reinterpret_cast<double*>(ths + kBatch * 8);   // [kBatch][8] node weights (FP64)
+    double* dsh = wsh + kBatch * 8;                // [kBatch][2] z_lo2 - z_lo, z_hi2 - z_hi
+    int* ish = reinterpret_cast<int*>(dsh + kBatch * 2);         // [kBatch][4] lo, lo2, hi, hi2
     const bool one_net = a.mparams == a.params;     // the conditional network gives the marginals too
     if (MODEL == SL_MODEL_MLP) {
         stage_net(cnet, a.params, a.d_in, a.m);
@@ -263,8 +267,8 @@ __global__ void __launch_bounds__(kTabThreads, 2) cdc_table_kernel(const CdcArgs
             }
         }
         __syncthreads();
-        // (C) thread (e, k): node k of entry e -- its weight, row k of C and of A, column k
-        // of the continuation lines, and coefficient a = k of the monomial rows D, B, Sm
+        // (C1) thread (e, k): node k of entry e -- its weight, row k of C, column k of the
+        // continuation lines
         if (threadIdx.x < kBatch * 8) {
             const int e = threadIdx.x / 8, k = threadIdx.x % 8;
             const int64_t u = base + e;
@@ -293,12 +297,8 @@ __global__ void __launch_bounds__(kTabThreads, 2) cdc_table_kernel(const CdcArgs
                 }
                 t[k] = z[k];
                 t[8 + k] = static_cast<float>(wk);
+                wsh[e * 8 + k] = wk;
                 for (int j = 0; j < SL_MAX_M; ++j) t[16 + 8 * k + j] = C[k * 8 + j];
-                for (int ai = 0; ai < SL_MAX_M; ++ai) {   // row k of A
-                    double acc = 0.0;
-                    for (int j = 0; j < m; ++j) acc += static_cast<double>(C[k * 8 + j]) * a.bq[j][ai];
-                    t[kA + 8 * k + ai] = static_cast<float>(wk * acc);
-                }
                 // column k of the lines through the two outermost nodes on each side
                 const double dlo = static_cast<double>(z[lo2]) - z[lo], dhi = static_cast<double>(z[hi2]) - z[hi];
                 const float clo = C[lo * 8 + k], chi = C[hi * 8 + k];
@@ -307,22 +307,43 @@ __global__ void __launch_bounds__(kTabThreads, 2) cdc_table_kernel(const CdcArgs
                 t[kSlo + k] = (k < m && dlo != 0.0) ? static_cast<float>((static_cast<double>(C[lo2 * 8 + k]) - clo) / dlo) : 0.0f;
                 t[kShi + k] = (k < m && dhi != 0.0) ? static_cast<float>((static_cast<double>(C[hi2 * 8 + k]) - chi) / dhi) : 0.0f;
                 t[kZlo + k] = k == 0 ? z[lo] : k == 1 ? z[hi] : 0.0f;   // z_lo, z_hi, then zero padding
-                // coefficient k of the monomial rows (the lines' slopes are linear in the rows:
-                // sum_j S_j bq[j][k] = (sum_j C[b][j] bq[j][k] - sum_j C[a][j] bq[j][k]) / (z_b - z_a))
-                double d0 = 0.0, blo = 0.0, blo2 = 0.0, bhi = 0.0, bhi2 = 0.0;
-                for (int j = 0; j < m; ++j) {
-                    const double f = a.bq[j][k];
-                    d0 += static_cast<double>(C[j]) * f;
-                    blo += static_cast<double>(C[lo * 8 + j]) * f;
-                    blo2 += static_cast<double>(C[lo2 * 8 + j]) * f;
-                    bhi += static_cast<double>(C[hi * 8 + j]) * f;
-                    bhi2 += static_cast<double>(C[hi2 * 8 + j]) * f;
+                if (k == 0) {
+                    ish[e * 4 + 0] = lo;
+                    ish[e * 4 + 1] = lo2;
+                    ish[e * 4 + 2] = hi;
+                    ish[e * 4 + 3] = hi2;
+                    dsh[e * 2 + 0] = dlo;
+                    dsh[e * 2 + 1] = dhi;
                 }
-                t[kD + k] = static_cast<float>(d0);
-                t[kBlo + k] = static_cast<float>(blo);
-                t[kSmlo + k] = dlo != 0.0 ? static_cast<float>((blo2 - blo) / dlo) : 0.0f;
-                t[kBhi + k] = static_cast<float>(bhi);
-                t[kSmhi + k] = dhi != 0.0 ? static_cast<float>((bhi2 - bhi) / dhi) : 0.0f;
+            }
+        }
+        __syncthreads();
+        // (C2) thread (e, k, a), all 256: coefficient a of row k of A, and for k < 5 coefficient
+        // a of the monomial row D (k = 0), B_lo, Sm_lo, B_hi, Sm_hi (k = 1..4); the lines'
+        // slopes are linear in the rows: sum_j S_j bq[j][a] = (sum_j (C[b][j] - C[a][j]) bq[j][a]) / (z_b - z_a)
+        {
+            const int e = threadIdx.x / 64, k = (threadIdx.x / 8) % 8, ai = threadIdx.x % 8;
+            const int64_t u = base + e;
+            if (e < kBatch && u < n) {
+                const float* C = Cs + e * 64;
+                float* t = a.tab + u * kTabFloats;
+                double acc = 0.0;
+                for (int j = 0; j < m; ++j) acc += static_cast<double>(C[k * 8 + j]) * a.bq[j][ai];
+                t[kA + 8 * k + ai] = static_cast<float>(wsh[e * 8 + k] * acc);
+                if (k < 5) {
+                    const int r0 = k == 0 ? 0 : ish[e * 4 + (k <= 2 ? 0 : 2)];   // D: row 0; B/Sm: lo or hi
+                    const int r1 = ish[e * 4 + (k <= 2 ? 1 : 3)];                 // lo2 or hi2
+                    const double d = dsh[e * 2 + (k <= 2 ? 0 : 1)];
+                    double b0 = 0.0, b1 = 0.0;
+                    for (int j = 0; j < m; ++j) {
+                        b0 += static_cast<double>(C[r0 * 8 + j]) * a.bq[j][ai];
+                        b1 += static_cast<double>(C[r1 * 8 + j]) * a.bq[j][ai];
+                    }
+                    const bool slope = (k == 2 || k == 4);
+                    const float v = slope ? (d != 0.0 ? static_cast<float>((b1 - b0) / d) : 0.0f) : static_cast<float>(b0);
+                    const int col = k == 0 ? kD : k == 1 ? kBlo : k == 2 ? kSmlo : k == 3 ? kBhi : kSmhi;
+                    t[col + ai] = v;
+                }
             }
         }
         __syncthreads();
