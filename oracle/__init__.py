@@ -99,7 +99,7 @@ def _declare(L):
     L.orc_em_labels.restype = _c_int
     L.orc_cdc_conditional_points.argtypes = [_c_int, _d, _d, _c_dbl, _d]
     L.orc_cdc_tables.argtypes = [_c_int, _d, _d, _c_int, _c_int, _c_int, _c_int, _d, _c_int, _d, _c_int,
-                                 _c_dbl, _c_int, _c_int, _d, _d]
+                                 _c_dbl, _c_int, _c_int, _i64, _c_i64, _d, _d]
     L.orc_cdc_tables.restype = _c_int
     L.orc_cdc_paths.argtypes = [_c_int, _d, _d, _c_int, _c_int, _c_int, _c_int, _d, _c_int, _d, _i64,
                                 _c_int, _c_dbl, _c_int, _c_int, _c_u64, _i64, _c_i64, _d, _d, _c_int]
@@ -320,18 +320,21 @@ def cdc_conditional_points(z, C, Y):
 
 
 def cdc_tables(model, P, theta, Y0, T, n_steps, m, Pm=None, d_in=3, act=ACT_RELU, width=WIDTH,
-               n_hidden=N_HIDDEN):
-    """Marginal nodes z [n_sets, n_steps, m] and conditional points at them
-    C [n_sets, n_steps, m (node k), m (point j)]."""
+               n_hidden=N_HIDDEN, sets=None):
+    """Marginal nodes z [n, n_steps, m] and conditional points at them C [n, n_steps, m (node k),
+    m (point j)] for the sets `sets` (row r = set sets[r]; None: every set, n = n_sets)."""
     y0 = _f64(Y0).reshape(-1)
     n_sets = y0.shape[0]
     th = _f64(theta).reshape(n_sets, -1)
     Pp = _f64(P) if P is not None else np.zeros(1)
     Pmp = _f64(Pm) if Pm is not None else None
-    z = np.zeros((n_sets, n_steps, m))
-    C = np.zeros((n_sets, n_steps, m, m))
+    sel = None if sets is None else _i64a(sets)
+    n = n_sets if sel is None else sel.shape[0]
+    z = np.zeros((n, n_steps, m))
+    C = np.zeros((n, n_steps, m, m))
     rc = lib().orc_cdc_tables(model, _p(Pp, _d), _p(Pmp, _d), d_in, width, n_hidden, act, _p(th, _d),
-                              th.shape[1], _p(y0, _d), n_sets, float(T), n_steps, m, _p(z, _d), _p(C, _d))
+                              th.shape[1], _p(y0, _d), n_sets, float(T), n_steps, m, _p(sel, _i64),
+                              0 if sel is None else n, _p(z, _d), _p(C, _d))
     if rc:
         raise ValueError("orc_cdc_tables failed")
     return z, C

@@ -794,22 +794,25 @@ void orc_cdc_conditional_points(int m, const double* z, const double* C, double 
     }
 }
 
-/* Tables of every (set s, step i): z[(s*n_steps + i)*m + k] and
- * C[((s*n_steps + i)*m + k)*m + j].  Pm: the marginal network's parameters
- * (the same shape as P; NULL: P itself). */
+/* Tables of the sets sets[r] (r < n_sel; sets == NULL: every set, r = s), every step i:
+ * z[(r*n_steps + i)*m + k] and C[((r*n_steps + i)*m + k)*m + j].  Pm: the marginal
+ * network's parameters (the same shape as P; NULL: P itself). */
 int orc_cdc_tables(int model, const double* P, const double* Pm, int d_in, int width, int n_hidden,
                    int act, const double* theta, int p, const double* Y0, int n_sets, double T,
-                   int n_steps, int m, double* z, double* C) {
+                   int n_steps, int m, const int64_t* sets, int64_t n_sel, double* z, double* C) {
     double xn[64], wn[64];
     if (orc_gauss_hermite(m, xn, wn) != 0) return 1;
     orc_net N = {model, d_in, width, n_hidden, act, m, p, P, xn};
     orc_net NM = {model, d_in, width, n_hidden, act, m, p, Pm ? Pm : P, xn};
     double dt = T / (double)n_steps;
-    for (int s = 0; s < n_sets; ++s) {
-        const double* th = theta + (int64_t)s * p;
+    int64_t n_rows = sets ? n_sel : n_sets;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t r = 0; r < n_rows; ++r) {
+        int64_t s = sets ? sets[r] : r;
+        const double* th = theta + s * p;
         for (int i = 0; i < n_steps; ++i) {
-            double* zi = z + ((int64_t)s * n_steps + i) * m;
-            double* Ci = C + ((int64_t)s * n_steps + i) * m * m;
+            double* zi = z + (r * n_steps + i) * m;
+            double* Ci = C + (r * n_steps + i) * m * m;
             if (i == 0) {
                 for (int k = 0; k < m; ++k) zi[k] = Y0[s];
             } else {
@@ -821,6 +824,11 @@ int orc_cdc_tables(int model, const double* P, const double* Pm, int d_in, int w
     return 0;
 }
 
+static int cmp_i64(const void* a, const void* b) {
+    int64_t x = *(const int64_t*)a, y = *(const int64_t*)b;
+    return (x > y) - (x < y);
+}
+
 /* Y_T (and optionally the grid) of selected flat paths of a batched 7L-CDC
  * call; arguments as orc_7l_paths plus the marginal network Pm. */
 int orc_cdc_paths(int model, const double* P, const double* Pm, int d_in, int width, int n_hidden,
@@ -829,25 +837,36 @@ int orc_cdc_paths(int model, const double* P, const double* Pm, int d_in, int wi
                   int64_t n_idx, double* out_YT, double* out_grid, int n_threads) {
     double xn[64], wn[64];
     if (orc_gauss_hermite(m, xn, wn) != 0) return 1;
-    size_t nt = (size_t)n_sets * n_steps;
-    double* z = (double*)malloc(sizeof(double) * nt * m + 1);
-    double* C = (double*)malloc(sizeof(double) * nt * m * m + 1);
-    if (!z || !C) { free(z); free(C); return 1; }
+    /* the tables of the sets the selected paths belong to (sorted, distinct) */
+    int64_t* sets = (int64_t*)malloc(sizeof(int64_t) * (n_idx > 0 ? n_idx : 1));
+    if (!sets) return 1;
+    for (int64_t k = 0; k < n_idx; ++k) sets[k] = owning_set(offsets, n_sets, idx ? idx[k] : k);
+    qsort(sets, (size_t)n_idx, sizeof(int64_t), cmp_i64);
+    int64_t n_sel = 0;
+    for (int64_t k = 0; k < n_idx; ++k)
+        if (n_sel == 0 || sets[k] != sets[n_sel - 1]) sets[n_sel++] = sets[k];
+    size_t nt = (size_t)(n_sel > 0 ? n_sel : 1) * n_steps;
+    double* z = (double*)malloc(sizeof(double) * nt * m);
+    double* C = (double*)malloc(sizeof(double) * nt * m * m);
+    if (!z || !C) { free(sets); free(z); free(C); return 1; }
+    set_threads(n_threads);
     int rc = orc_cdc_tables(model, P, Pm, d_in, width, n_hidden, act, theta, p, Y0, n_sets, T,
-                            n_steps, m, z, C);
-    if (rc) { free(z); free(C); return rc; }
+                            n_steps, m, sets, n_sel, z, C);
+    if (rc) { free(sets); free(z); free(C); return rc; }
     set_threads(n_threads);
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t k = 0; k < n_idx; ++k) {
         int64_t g = idx ? idx[k] : k;
         int s = owning_set(offsets, n_sets, g);
         uint32_t q = (uint32_t)(g - offsets[s]);
+        int64_t key = s, *hit = (int64_t*)bsearch(&key, sets, (size_t)n_sel, sizeof(int64_t), cmp_i64);
+        int64_t row = hit - sets;
         double* grid = out_grid ? out_grid + k * (int64_t)(n_steps + 1) : NULL;
         double Y = Y0[s];
         if (grid) grid[0] = Y;
         for (int i = 0; i < n_steps; ++i) {
             double yhat[ORC_MAX_W];
-            size_t r = (size_t)s * n_steps + i;
+            size_t r = (size_t)row * n_steps + i;
             orc_cdc_conditional_points(m, z + r * m, C + r * m * m, Y, yhat);
             double X = orc_normal(seed, ORC_TAG_7L, (uint32_t)s, q, (uint32_t)i);
             Y = orc_lagrange(m, xn, yhat, X);
@@ -855,6 +874,7 @@ int orc_cdc_paths(int model, const double* P, const double* Pm, int d_in, int wi
         }
         out_YT[k] = Y;
     }
+    free(sets);
     free(z);
     free(C);
     return 0;

@@ -24,7 +24,7 @@ oracle's own FP64 path and tables (1 for a well-conditioned path).
   through them diverges (the status word then reports non-finite paths).
 * Degenerate laws (sigma = 0: every marginal collapses to a point), ragged and empty sets,
   one step, batch independence (bit-exact), CUDA graph replay, FP64 set moments, the full
-  16 x 1e6 x 16 workload on sampled paths.
+  16 x 1e6 x 16 workload on sampled paths, 2^31 + 129 paths in one set, 2^20 sets.
 """
 import numpy as np
 import pytest
@@ -100,10 +100,11 @@ def _oracle(orc, model, P, theta, Y0, offsets, T, n_steps, m, seed, scale, Pm=No
     """The oracle's Y_T of the selected paths and their kappa."""
     yt, grid = orc.cdc_paths(model, P, theta, Y0, offsets, T, n_steps, m, seed, Pm=Pm, idx=idx, d_in=d_in,
                              act=act, grid=True)
-    z, C = orc.cdc_tables(model, P, theta, Y0, T, n_steps, m, Pm=Pm, d_in=d_in, act=act)
     idx = np.arange(len(yt)) if idx is None else idx
     sets, _ = flat_sets(offsets, idx)
-    return yt, _kappa(z, C, grid, sets, scale)
+    used = np.unique(sets)
+    z, C = orc.cdc_tables(model, P, theta, Y0, T, n_steps, m, Pm=Pm, d_in=d_in, act=act, sets=used)
+    return yt, _kappa(z, C, grid, np.searchsorted(used, sets), scale)
 
 
 def _check(orc, got, want, offsets, seed, n_steps, scale, idx=None, tol=TOL):
@@ -335,3 +336,40 @@ def test_full_size_sampled(sl, orc):
     for s in range(16):
         seg = r["yt"][off[s]:off[s + 1]].astype(np.float64)
         assert r["mean"][s] == pytest.approx(seg.mean(), rel=1e-12)
+
+
+def test_more_than_2_31_paths(sl, orc):
+    """One set of 2^31 + 129 paths (flat and in-set indices past int32), 2 steps, exact GBM map:
+    sampled paths including the last ones against the oracle; the set mean is finite."""
+    n = (1 << 31) + 129
+    off = W.offsets_from_counts([n])
+    th = [[0.1, 0.3]]
+    yt = torch.empty(n, dtype=torch.float32, device="cuda")
+    mean = torch.empty(1, dtype=torch.float64, device="cuda")
+    ws = sl.seven_league_cdc_simulate_batched(1, None, _dev(th), _dev([1.0]), _dev(off, torch.int64), 1.0, 2, 7, 2,
+                                              out_YT=yt, out_mean=mean)
+    assert sl.workspace_status(ws) == 0
+    idx = np.concatenate([np.arange(0, 64), np.arange((1 << 31) - 64, (1 << 31) + 64), np.arange(n - 64, n)])
+    got = yt[torch.as_tensor(idx, device="cuda")].cpu().numpy()
+    want = _oracle(orc, 1, None, th, [1.0], off, 1.0, 2, 7, 2, 1.0, idx=idx)
+    _check(orc, got, want, off, 2, 2, 1.0, idx=idx)
+    assert np.isfinite(mean.item())
+    del yt
+
+
+def test_many_sets(sl, orc):
+    """2^20 parameter sets with 0 or 1 path each, 3 steps, a network: 3 * 2^20 table entries."""
+    n_sets = 1 << 20
+    rng = np.random.default_rng(21)
+    counts = rng.integers(0, 2, n_sets)
+    off = W.offsets_from_counts(counts)
+    th = rng.uniform([0.0, 0.1], [0.2, 0.5], (n_sets, 2)).astype(np.float32)
+    y0 = rng.uniform(0.8, 1.2, n_sets).astype(np.float32)
+    P = W.near_affine_params(4, 7, seed=22)
+    net = sl.make_net(_dev(P), 4, 7)
+    r = _run(sl, 0, net, th, y0, off, 1.0, 3, 7, 4, moments=True)
+    sets = np.concatenate([np.nonzero(counts)[0][:40], np.nonzero(counts)[0][-40:]])
+    idx = off[sets]
+    want = _oracle(orc, 0, P, th, y0, off, 1.0, 3, 7, 4, 1.0, idx=idx, d_in=4)
+    _check(orc, r["yt"][idx], want, off, 4, 3, 1.0, idx=idx)
+    assert np.array_equal(r["mean"][sets], r["yt"][idx].astype(np.float64)) and np.all(r["mean"][counts == 0] == 0)
