@@ -62,8 +62,12 @@ typedef enum {
 
 /* Device status word bits (read with sl_workspace_status). */
 #define SL_DEV_NONFINITE 0x1u   /* a path produced a non-finite state */
-#define SL_DEV_OFFSETS 0x2u     /* path_offsets not non-decreasing or total mismatch */
+#define SL_DEV_OFFSETS 0x2u     /* path_offsets not non-decreasing or total mismatch (the
+                                   samplers check a path's set against path_offsets in
+                                   checked builds) */
 #define SL_DEV_TIMEOUT 0x4u     /* a bounded mbarrier wait expired */
+#define SL_DEV_INDEX 0x8u       /* an index derived on the device fell outside its array
+                                   (checked builds, libsevenleague_checked.so) */
 
 /* Collocation maps H (Eq. 6.3) */
 enum { SL_MODEL_MLP = 0,        /* the network; theta = its parameter inputs (p = d_in - 2) */

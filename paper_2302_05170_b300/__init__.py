@@ -19,6 +19,10 @@ from . import workloads  # noqa: F401  (seeded synthetic inputs)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsevenleague.so")
+# the same library built with -DSL_CHECKED: kernels verify device-derived indices (a path's
+# set against path_offsets, listed paths against the path count) and report SL_DEV_OFFSETS /
+# SL_DEV_INDEX instead of trusting them; load(LIB_CHECKED_PATH) in a process of its own
+LIB_CHECKED_PATH = os.path.join(_HERE, "libsevenleague_checked.so")
 
 # Codes of include/sevenleague.h
 SL_OK, SL_ERR_ARG, SL_ERR_UNSUPPORTED, SL_ERR_WORKSPACE, SL_ERR_CUDA, SL_ERR_DEVICE, SL_ERR_TIMEOUT = range(7)
@@ -28,7 +32,7 @@ ACT_RELU, ACT_SOFTPLUS = 0, 1
 PREC_FP32, PREC_BF16 = 0, 1
 PAYOFF_CALL = 0
 WIDTH, N_HIDDEN, MIN_M, MAX_M = 50, 4, 2, 8
-SL_DEV_NONFINITE, SL_DEV_OFFSETS, SL_DEV_TIMEOUT = 0x1, 0x2, 0x4   # device status bits
+SL_DEV_NONFINITE, SL_DEV_OFFSETS, SL_DEV_TIMEOUT, SL_DEV_INDEX = 0x1, 0x2, 0x4, 0x8   # device status bits
 _STATUS_NAMES = {1: "SL_ERR_ARG", 2: "SL_ERR_UNSUPPORTED", 3: "SL_ERR_WORKSPACE",
                  4: "SL_ERR_CUDA", 5: "SL_ERR_DEVICE", 6: "SL_ERR_TIMEOUT"}
 
@@ -62,10 +66,13 @@ _vp, _i, _i64, _u64, _f, _sz = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, c
                                  ctypes.c_float, ctypes.c_size_t)
 
 
-def build(verbose: bool = False) -> str:
-    """Compile the CUDA sources for sm_103a (nvcc) into the in-tree library."""
-    from .build import build as _b
-    return _b(verbose=verbose)
+from . import build as _build_module   # noqa: E402  (the submodule; `build` below is the function)
+
+
+def build(verbose: bool = False, checked: bool = False) -> str:
+    """Compile the CUDA sources for sm_103a (nvcc) into the in-tree library (checked=True:
+    the checked build, libsevenleague_checked.so)."""
+    return _build_module.build(verbose=verbose, checked=checked)
 
 
 def load(path: str = LIB_PATH):

@@ -226,6 +226,7 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_simt_kernel(const AdjArgs
         if (a.offsets) {
             s = owning_set(a.offsets, a.n_sets, g);
             q64 = g - __ldg(a.offsets + s);
+            if (!path_in_set(a.offsets, s, g, a.status)) continue;
         }
         const uint32_t q = static_cast<uint32_t>(q64);
         const float* th = a.theta + static_cast<int64_t>(s) * p;

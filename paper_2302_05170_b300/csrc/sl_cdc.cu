@@ -492,6 +492,7 @@ __global__ void __launch_bounds__(kPathThreads, 4) cdc_path_kernel(const SimArgs
             g[p] = write[p] ? g0 + p : g0;
             s[p] = a.offsets ? owning_set(a.offsets, a.n_sets, g[p]) : 0;
             q[p] = a.offsets ? g[p] - __ldg(a.offsets + s[p]) : g[p];
+            if (write[p]) write[p] = path_in_set(a.offsets, s[p], g[p], a.status);
             same = same && s[p] == s[0];
         }
         if (same) {

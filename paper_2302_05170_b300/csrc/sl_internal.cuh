@@ -125,6 +125,24 @@ __device__ __forceinline__ void raise_status(unsigned* status, unsigned bits) {
     if (status) atomicOr(status, bits);
 }
 
+// Checked builds (-DSL_CHECKED: libsevenleague_checked.so) verify the indices the kernels
+// derive from caller data -- a path's set s must satisfy offsets[s] <= g < offsets[s+1], a
+// listed path must lie below the path count -- and on a failure set a status bit and skip
+// the path's outputs instead of trusting the index.  The normal build compiles them away.
+#ifdef SL_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+
+// Flat path g lies in set s (checked builds; always true otherwise).
+__device__ __forceinline__ bool path_in_set(const int64_t* off, int s, int64_t g, unsigned* status) {
+    if (!kChecked || !off) return true;
+    const bool ok = __ldg(off + s) <= g && g < __ldg(off + s + 1);
+    if (!ok) raise_status(status, SL_DEV_OFFSETS);
+    return ok;
+}
+
 // Kernel-side description of a 7L sampling call (shared by all forms).
 struct SimArgs {
     const float* params;      // network parameters (FP32, flat)

@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(256) simt_7l_kernel(const SimArgs a) {
         if (a.offsets) {
             s = owning_set(a.offsets, a.n_sets, g);
             q = g - __ldg(a.offsets + s);
+            if (!path_in_set(a.offsets, s, g, a.status)) continue;
         }
         const float* th = a.theta + static_cast<int64_t>(s) * a.p;
         float Y = a.Y0 ? __ldg(a.Y0 + s) : a.y0_scalar;

@@ -391,16 +391,26 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
     T.dph = 0;
     uint32_t* tmask = masks + wg * mask_words_per_tile<ACT>() + r;   // word (step, layer l, half h) at ((step*4 + l-1)*2 + h)*128
 
-    const int64_t n_list = static_cast<int64_t>(*A.count);
+    int64_t n_list = static_cast<int64_t>(*A.count);
+    if (kChecked && n_list > a.total) {            // the list holds at most one entry per path
+        raise_status(a.status, SL_DEV_INDEX);
+        n_list = a.total;
+    }
     const int64_t n_tiles = (n_list + kTile - 1) / kTile;
     const int64_t tile_stride = static_cast<int64_t>(gridDim.x) * S;
     const int p = a.p;
     bool ok = true;
     for (int64_t tile = static_cast<int64_t>(blockIdx.x) * S + wg; tile < n_tiles; tile += tile_stride) {
         const int64_t li = tile * kTile + r;
-        const bool valid = li < n_list;
-        const int64_t g = A.list[valid ? li : n_list - 1];
+        bool valid = li < n_list;
+        int64_t g = A.list[valid ? li : n_list - 1];
+        if (kChecked && g >= a.total) {                // a listed path past the path count
+            raise_status(a.status, SL_DEV_INDEX);
+            g = 0;
+            valid = false;
+        }
         tile_begin_listed(T, a, g, valid);
+        if (T.valid) T.valid = path_in_set(a.offsets, T.s, g, a.status);
         int blk = -1;
         float lam = valid ? 1.0f : 0.0f;
         float gth[SL_MAX_DIN_TC - 2];

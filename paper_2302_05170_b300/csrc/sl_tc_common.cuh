@@ -354,6 +354,7 @@ __device__ __forceinline__ void tile_begin(Tile& T, const SimArgs& a, int64_t ti
     if (a.offsets) {
         T.s = owning_set(a.offsets, a.n_sets, T.valid ? T.g : a.total - 1);
         qq = T.g - __ldg(a.offsets + T.s);
+        if (T.valid) T.valid = path_in_set(a.offsets, T.s, T.g, a.status);
     }
     T.q = static_cast<uint32_t>(qq);
     const float* th = a.theta + static_cast<int64_t>(T.s) * a.p;
