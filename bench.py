@@ -403,9 +403,17 @@ def main():
             del yt_sp
         # the 7L-CDC variant on the same paths (Table 6.1's second scheme): the network only at the
         # marginal collocation points of each (set, step), an interpolation in Y per path.  With a
-        # network: workloads.near_affine_params (outputs shaped like collocation points; an
-        # untrained Xavier network's marginal points are unordered); with the exact GBM map.
-        P_cdc = torch.as_tensor(W.near_affine_params(4, 7, seed=0), device=dev)
+        # network (trained weights: the GBM network trained again over the horizons 0.125 .. 2, so
+        # that it gives the marginal points too; otherwise workloads.near_affine_params, outputs
+        # shaped like collocation points -- an untrained Xavier network's marginal points are
+        # unordered) and with the exact GBM map.
+        if args.weights == "trained":
+            P_cdc, _, _ = pipeline.train_gbm_online_network(n_rows=1 << 15, n_steps=args.train_steps,
+                                                            dts=tuple(0.125 * np.arange(1, 17)))
+            cdc_net_kind = "GBM network trained over the horizons 0.125..2 (%d Adam steps)" % args.train_steps
+        else:
+            P_cdc = torch.as_tensor(W.near_affine_params(4, 7, seed=0), device=dev)
+            cdc_net_kind = "workloads.near_affine_params (seed 0)"
         net_cdc = sl.make_net(P_cdc, 4, 7)
         ws_cdc = torch.empty(sl.cdc_workspace_size(total, 16, n_steps), dtype=torch.uint8, device=dev)
         yt_c = torch.empty_like(yt)
@@ -434,8 +442,23 @@ def main():
                 secondary["cdc_fp32_roofline_frac"] = CDC_FLOPS_PER_PATH_STEP * c_rate / fp32_peak
                 secondary["cdc_over_7l_bf16"] = c_rate / value
         secondary["cdc_workload"] = ("7L-CDC on the GBM workload above (16 sets x %d paths x %d steps, m=7); tables "
-                                     "of (m+1) network evaluations per (set, step), then 2 paths per thread"
-                                     % (args.paths, n_steps))
+                                     "of (m+1) network evaluations per (set, step), then 2 paths per thread; "
+                                     "network: %s" % (args.paths, n_steps, cdc_net_kind))
+        if args.weights == "trained" and "cdc_error" not in secondary:
+            # accuracy on every path against the exact-collocation GBM chain on the same normals:
+            # the 7L-CDC scheme and the 7L scheme (BF16 form) with the same network
+            yt_ex = torch.empty_like(yt)
+            sl.seven_league_simulate_batched(sl.MODEL_GBM_EXACT, None, theta, Y0, off, T, n_steps, m, seed,
+                                             out_YT=yt_ex, total_paths=total)
+            sl.seven_league_cdc_simulate_batched(sl.MODEL_MLP, net_cdc, theta, Y0, off, T, n_steps, m, seed,
+                                                 out_YT=yt_c, ws=ws_cdc, total_paths=total)
+            yt_7 = torch.empty_like(yt)
+            sl.seven_league_simulate_batched(sl.MODEL_MLP, sl.make_net(P_cdc, 4, 7, prec=sl.PREC_BF16), theta, Y0,
+                                             off, T, n_steps, m, seed, out_YT=yt_7, total_paths=total)
+            ex = yt_ex.double()
+            secondary["cdc_mean_abs_err_vs_exact_map"] = float((yt_c.double() - ex).abs().mean().item())
+            secondary["7l_same_network_mean_abs_err_vs_exact_map"] = float((yt_7.double() - ex).abs().mean().item())
+            del yt_ex, yt_7
         del yt_c, ws_cdc
         # offline stage: EM label samples/s on the CIR labels workload
         th, yi, dtr = W.cir_label_rows(1024)

@@ -104,6 +104,18 @@ def _declare(L):
     L.orc_cdc_paths.argtypes = [_c_int, _d, _d, _c_int, _c_int, _c_int, _c_int, _d, _c_int, _d, _i64,
                                 _c_int, _c_dbl, _c_int, _c_int, _c_u64, _i64, _c_i64, _d, _d, _c_int]
     L.orc_cdc_paths.restype = _c_int
+    L.orc_cdcq_G.argtypes = [_c_int, _d, _d, _c_dbl]
+    L.orc_cdcq_G.restype = _c_dbl
+    L.orc_cdcq_Ginv.argtypes = [_c_int, _d, _d, _c_dbl]
+    L.orc_cdcq_Ginv.restype = _c_dbl
+    L.orc_cdcq_F.argtypes = [_c_int, _d, _d, _c_dbl, _c_dbl]
+    L.orc_cdcq_F.restype = _c_dbl
+    L.orc_cdcq_tables.argtypes = [_c_int, _d, _d, _c_int, _c_int, _c_int, _c_int, _d, _c_int, _d, _c_int,
+                                  _c_dbl, _c_int, _c_int, _i64, _c_i64, _d, _d]
+    L.orc_cdcq_tables.restype = _c_int
+    L.orc_cdcq_paths.argtypes = [_c_int, _d, _d, _c_int, _c_int, _c_int, _c_int, _d, _c_int, _d, _i64,
+                                 _c_int, _c_dbl, _c_int, _c_int, _c_u64, _i64, _c_i64, _d, _d, _c_int]
+    L.orc_cdcq_paths.restype = _c_int
 
 
 def _p(a, ct):
@@ -357,4 +369,74 @@ def cdc_paths(model, P, theta, Y0, offsets, T, n_steps, m, seed, Pm=None, idx=No
                              _p(ix, _i64), n, _p(out, _d), _p(gr, _d), threads)
     if rc:
         raise ValueError("orc_cdc_paths failed")
+    return (out, gr) if grid else out
+
+
+# --- the 7L-CDC variant in the marginal's quantile coordinate -------------------------------
+def _gh_nodes(m):
+    xn, wn = np.zeros(64), np.zeros(64)
+    lib().orc_gauss_hermite(m, _p(xn, _d), _p(wn, _d))
+    return xn[:m].copy()
+
+
+def cdcq_G(z, xi):
+    """G(xi) through (x_k, z_k) at the Gauss-Hermite points, continued linearly."""
+    zz = _f64(z)
+    m = zz.shape[0]
+    xn = _gh_nodes(m)
+    return lib().orc_cdcq_G(m, _p(xn, _d), _p(zz, _d), float(xi))
+
+
+def cdcq_Ginv(z, y):
+    zz = _f64(z)
+    m = zz.shape[0]
+    xn = _gh_nodes(m)
+    return lib().orc_cdcq_Ginv(m, _p(xn, _d), _p(zz, _d), float(y))
+
+
+def cdcq_F(eta, xi, X):
+    """sum_k sum_j eta[k, j] L_k(xi) L_j(X) at the Gauss-Hermite points."""
+    e = _f64(eta)
+    m = e.shape[0]
+    xn = _gh_nodes(m)
+    return lib().orc_cdcq_F(m, _p(xn, _d), _p(e, _d), float(xi), float(X))
+
+
+def cdcq_tables(model, P, theta, Y0, T, n_steps, m, Pm=None, d_in=3, act=ACT_RELU, width=WIDTH,
+                n_hidden=N_HIDDEN, sets=None):
+    """Nodes of t_{i+1} zn [n, n_steps, m] and eta [n, n_steps, m (node k), m (point j)]."""
+    y0 = _f64(Y0).reshape(-1)
+    n_sets = y0.shape[0]
+    th = _f64(theta).reshape(n_sets, -1)
+    Pp = _f64(P) if P is not None else np.zeros(1)
+    Pmp = _f64(Pm) if Pm is not None else None
+    sel = None if sets is None else _i64a(sets)
+    n = n_sets if sel is None else sel.shape[0]
+    zn = np.zeros((n, n_steps, m))
+    eta = np.zeros((n, n_steps, m, m))
+    rc = lib().orc_cdcq_tables(model, _p(Pp, _d), _p(Pmp, _d), d_in, width, n_hidden, act, _p(th, _d),
+                               th.shape[1], _p(y0, _d), n_sets, float(T), n_steps, m, _p(sel, _i64),
+                               0 if sel is None else n, _p(zn, _d), _p(eta, _d))
+    if rc:
+        raise ValueError("orc_cdcq_tables failed")
+    return zn, eta
+
+
+def cdcq_paths(model, P, theta, Y0, offsets, T, n_steps, m, seed, Pm=None, idx=None, d_in=3,
+               act=ACT_RELU, grid=False, threads=0, width=WIDTH, n_hidden=N_HIDDEN):
+    """Y_T (and optionally the grid) of selected flat paths of the quantile-coordinate chain."""
+    o, n_sets = _offsets(offsets)
+    th = _f64(theta).reshape(n_sets, -1)
+    Pp = _f64(P) if P is not None else np.zeros(1)
+    Pmp = _f64(Pm) if Pm is not None else None
+    y0 = _f64(Y0).reshape(n_sets)
+    ix = None if idx is None else _i64a(idx)
+    n = int(o[-1]) if ix is None else ix.shape[0]
+    out = np.zeros(n)
+    gr = np.zeros((n, n_steps + 1)) if grid else None
+    rc = lib().orc_cdcq_paths(model, _p(Pp, _d), _p(Pmp, _d), d_in, width, n_hidden, act, _p(th, _d),
+                              th.shape[1], _p(y0, _d), _p(o, _i64), n_sets, float(T), n_steps, m, seed,
+                              _p(ix, _i64), n, _p(out, _d), _p(gr, _d), threads)
+    if rc:
+        raise ValueError("orc_cdcq_paths failed")
     return (out, gr) if grid else out

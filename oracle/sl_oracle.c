@@ -20,7 +20,9 @@
  * differences for every derivative, and closed-form Black-Scholes values;
  * the 7L-CDC variant against polynomial reproduction, scipy's exact marginal
  * and conditional quantiles, and the 7L chain wherever the conditional map is
- * affine in Y (tests/test_oracle_cdc.py).
+ * affine in Y (tests/test_oracle_cdc.py); its quantile-coordinate reading
+ * against the inverse-map identities, tensor-product polynomial reproduction
+ * and the exact OU chain (tests/test_oracle_cdcq.py).
  * No function in this file is "parity unpinned".
  */
 #include <math.h>
@@ -877,5 +879,154 @@ int orc_cdc_paths(int model, const double* P, const double* Pm, int d_in, int wi
     free(sets);
     free(z);
     free(C);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * The 7L-CDC variant in the marginal's quantile coordinate (a second reading of
+ * the same outline).  The marginal collocation points z^(i)_k of Y at t_i define
+ * the marginal collocation map G_i(xi) = sum_k z^(i)_k L_k(xi) through the
+ * Gauss-Hermite points x_k (the SCMC representation of Y_{t_i}: Y = G_i(xi) with
+ * xi standard normal), continued beyond [x_0, x_{m-1}] by the line through the two
+ * outermost nodes on that side.  A path carries xi_i instead of Y_i:
+ *  - eta[k][j] = G_{i+1}^{-1}(C[k][j]): the conditional points at the marginal
+ *    nodes of t_i, expressed in the quantile coordinate of t_{i+1};
+ *  - xi_{i+1} = sum_k sum_j eta[k][j] L_k(xi_i) L_j(X_{i+1}) (Lagrange in both
+ *    variables through the Gauss-Hermite points);
+ *  - Y_i = G_i(xi_i) wherever Y is output (the grid, Y_T = G_N(xi_N)).
+ * At i = 0 the marginal is the point Y0: every row of C is H(Y0, dt), so xi_1
+ * does not depend on xi_0 (taken as 0).  If the nodes at t_{i+1} all coincide,
+ * G_{i+1} is constant: eta = 0 and Y_{i+1} = z^(i+1)_0.  G must increase from
+ * its first to its last node (z_0 < z_{m-1}); the inverse inside the hull is
+ * the root of G(xi) = y found by 60 bisections of [x_0, x_{m-1}].
+ * With the exact OU map (G linear, C affine in z and x_j) the chain equals the
+ * 7L chain exactly.
+ * ---------------------------------------------------------------------- */
+
+/* G(xi) through (x_k, z_k), k < m, with the linear continuation. */
+double orc_cdcq_G(int m, const double* xn, const double* z, double xi) {
+    if (xi < xn[0]) return z[0] + (xi - xn[0]) * (z[1] - z[0]) / (xn[1] - xn[0]);
+    if (xi > xn[m - 1])
+        return z[m - 1] + (xi - xn[m - 1]) * (z[m - 1] - z[m - 2]) / (xn[m - 1] - xn[m - 2]);
+    return orc_lagrange(m, xn, z, xi);
+}
+
+/* G^{-1}(y): the continuation lines beyond [z_0, z_{m-1}], bisection inside;
+ * NaN if G does not increase from its first to its last node; 0 if all nodes
+ * coincide. */
+double orc_cdcq_Ginv(int m, const double* xn, const double* z, double y) {
+    int same = 1;
+    for (int k = 1; k < m; ++k)
+        if (z[k] != z[0]) same = 0;
+    if (same) return 0.0;
+    if (!(z[m - 1] > z[0])) return NAN;
+    if (y < z[0]) return xn[0] + (y - z[0]) * (xn[1] - xn[0]) / (z[1] - z[0]);
+    if (y > z[m - 1]) return xn[m - 1] + (y - z[m - 1]) * (xn[m - 1] - xn[m - 2]) / (z[m - 1] - z[m - 2]);
+    double lo = xn[0], hi = xn[m - 1];
+    for (int it = 0; it < 60; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (orc_lagrange(m, xn, z, mid) < y) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+/* sum_k sum_j eta[k*m + j] L_k(xi) L_j(X) (plain Lagrange definition). */
+double orc_cdcq_F(int m, const double* xn, const double* eta, double xi, double X) {
+    double v = 0.0;
+    for (int k = 0; k < m; ++k) {
+        double Lk = 1.0;
+        for (int l = 0; l < m; ++l)
+            if (l != k) Lk *= (xi - xn[l]) / (xn[k] - xn[l]);
+        double row = 0.0;
+        for (int j = 0; j < m; ++j) {
+            double Lj = 1.0;
+            for (int l = 0; l < m; ++l)
+                if (l != j) Lj *= (X - xn[l]) / (xn[j] - xn[l]);
+            row += eta[k * m + j] * Lj;
+        }
+        v += Lk * row;
+    }
+    return v;
+}
+
+/* Tables of the sets sets[r] (NULL: every set), every step i: the nodes of t_{i+1},
+ * zn[(r*n_steps + i)*m + k], and eta[((r*n_steps + i)*m + k)*m + j]. */
+int orc_cdcq_tables(int model, const double* P, const double* Pm, int d_in, int width, int n_hidden,
+                    int act, const double* theta, int p, const double* Y0, int n_sets, double T,
+                    int n_steps, int m, const int64_t* sets, int64_t n_sel, double* zn, double* eta) {
+    double xn[64], wn[64];
+    if (orc_gauss_hermite(m, xn, wn) != 0) return 1;
+    orc_net N = {model, d_in, width, n_hidden, act, m, p, P, xn};
+    orc_net NM = {model, d_in, width, n_hidden, act, m, p, Pm ? Pm : P, xn};
+    double dt = T / (double)n_steps;
+    int64_t n_rows = sets ? n_sel : n_sets;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t r = 0; r < n_rows; ++r) {
+        int64_t s = sets ? sets[r] : r;
+        const double* th = theta + s * p;
+        for (int i = 0; i < n_steps; ++i) {
+            double z[ORC_MAX_W], znext[ORC_MAX_W], C[ORC_MAX_W * 8];
+            if (i == 0) {
+                for (int k = 0; k < m; ++k) z[k] = Y0[s];
+            } else {
+                collocation(&NM, Y0[s], i * dt, th, z, NULL);
+            }
+            collocation(&NM, Y0[s], (i + 1) * dt, th, znext, NULL);
+            for (int k = 0; k < m; ++k) collocation(&N, z[k], dt, th, C + k * m, NULL);
+            double* zo = zn + (r * n_steps + i) * m;
+            double* eo = eta + (r * n_steps + i) * m * m;
+            for (int k = 0; k < m; ++k) zo[k] = znext[k];
+            for (int k = 0; k < m * m; ++k) eo[k] = orc_cdcq_Ginv(m, xn, znext, C[k]);
+        }
+    }
+    return 0;
+}
+
+/* Y_T (and optionally the grid Y_i = G_i(xi_i)) of selected flat paths of the
+ * quantile-coordinate 7L-CDC chain; arguments as orc_cdc_paths. */
+int orc_cdcq_paths(int model, const double* P, const double* Pm, int d_in, int width, int n_hidden,
+                   int act, const double* theta, int p, const double* Y0, const int64_t* offsets,
+                   int n_sets, double T, int n_steps, int m, uint64_t seed, const int64_t* idx,
+                   int64_t n_idx, double* out_YT, double* out_grid, int n_threads) {
+    double xn[64], wn[64];
+    if (orc_gauss_hermite(m, xn, wn) != 0) return 1;
+    int64_t* sets = (int64_t*)malloc(sizeof(int64_t) * (n_idx > 0 ? n_idx : 1));
+    if (!sets) return 1;
+    for (int64_t k = 0; k < n_idx; ++k) sets[k] = owning_set(offsets, n_sets, idx ? idx[k] : k);
+    qsort(sets, (size_t)n_idx, sizeof(int64_t), cmp_i64);
+    int64_t n_sel = 0;
+    for (int64_t k = 0; k < n_idx; ++k)
+        if (n_sel == 0 || sets[k] != sets[n_sel - 1]) sets[n_sel++] = sets[k];
+    size_t nt = (size_t)(n_sel > 0 ? n_sel : 1) * n_steps;
+    double* zn = (double*)malloc(sizeof(double) * nt * m);
+    double* eta = (double*)malloc(sizeof(double) * nt * m * m);
+    if (!zn || !eta) { free(sets); free(zn); free(eta); return 1; }
+    set_threads(n_threads);
+    int rc = orc_cdcq_tables(model, P, Pm, d_in, width, n_hidden, act, theta, p, Y0, n_sets, T,
+                             n_steps, m, sets, n_sel, zn, eta);
+    if (rc) { free(sets); free(zn); free(eta); return rc; }
+    set_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < n_idx; ++k) {
+        int64_t g = idx ? idx[k] : k;
+        int s = owning_set(offsets, n_sets, g);
+        uint32_t q = (uint32_t)(g - offsets[s]);
+        int64_t key = s, *hit = (int64_t*)bsearch(&key, sets, (size_t)n_sel, sizeof(int64_t), cmp_i64);
+        int64_t row = hit - sets;
+        double* grid = out_grid ? out_grid + k * (int64_t)(n_steps + 1) : NULL;
+        if (grid) grid[0] = Y0[s];
+        double xi = 0.0, Y = Y0[s];
+        for (int i = 0; i < n_steps; ++i) {
+            size_t r = (size_t)row * n_steps + i;
+            double X = orc_normal(seed, ORC_TAG_7L, (uint32_t)s, q, (uint32_t)i);
+            xi = orc_cdcq_F(m, xn, eta + r * m * m, xi, X);
+            Y = orc_cdcq_G(m, xn, zn + r * m, xi);
+            if (grid) grid[i + 1] = Y;
+        }
+        out_YT[k] = Y;
+    }
+    free(sets);
+    free(zn);
+    free(eta);
     return 0;
 }
