@@ -898,7 +898,9 @@ int orc_cdc_paths(int model, const double* P, const double* Pm, int d_in, int wi
  * does not depend on xi_0 (taken as 0).  If the nodes at t_{i+1} all coincide,
  * G_{i+1} is constant: eta = 0 and Y_{i+1} = z^(i+1)_0.  G must increase from
  * its first to its last node (z_0 < z_{m-1}); the inverse inside the hull is
- * the root of G(xi) = y found by 60 bisections of [x_0, x_{m-1}].
+ * the root of G(xi) = y in the first node interval [x_k, x_{k+1}] with
+ * z_k <= y <= z_{k+1} (one exists whenever z_0 <= y <= z_{m-1}), found by 60
+ * bisections of that interval (for a G that increases, the one root).
  * With the exact OU map (G linear, C affine in z and x_j) the chain equals the
  * 7L chain exactly.
  * ---------------------------------------------------------------------- */
@@ -922,7 +924,9 @@ double orc_cdcq_Ginv(int m, const double* xn, const double* z, double y) {
     if (!(z[m - 1] > z[0])) return NAN;
     if (y < z[0]) return xn[0] + (y - z[0]) * (xn[1] - xn[0]) / (z[1] - z[0]);
     if (y > z[m - 1]) return xn[m - 1] + (y - z[m - 1]) * (xn[m - 1] - xn[m - 2]) / (z[m - 1] - z[m - 2]);
-    double lo = xn[0], hi = xn[m - 1];
+    int k = 0;
+    while (k < m - 2 && !(z[k] <= y && y <= z[k + 1])) ++k;
+    double lo = xn[k], hi = xn[k + 1];
     for (int it = 0; it < 60; ++it) {
         double mid = 0.5 * (lo + hi);
         if (orc_lagrange(m, xn, z, mid) < y) lo = mid; else hi = mid;
