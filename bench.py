@@ -418,11 +418,13 @@ def main():
         ws_cdc = torch.empty(sl.cdc_workspace_size(total, 16, n_steps), dtype=torch.uint8, device=dev)
         yt_c = torch.empty_like(yt)
         mean_c = torch.empty_like(mean)
-        for model_c, key in ((sl.MODEL_MLP, "cdc"), (sl.MODEL_GBM_EXACT, "cdc_gbm_exact")):
+        for model_c, space_c, key in ((sl.MODEL_MLP, sl.CDC_QUANTILE, "cdc"), (sl.MODEL_GBM_EXACT, sl.CDC_QUANTILE,
+                                                                              "cdc_gbm_exact"),
+                                      (sl.MODEL_MLP, sl.CDC_Y, "cdc_y")):
             net_c = net_cdc if model_c == sl.MODEL_MLP else None
             run_c = lambda: sl.seven_league_cdc_simulate_batched(model_c, net_c, theta, Y0, off, T, n_steps, m, seed,
-                                                                 out_YT=yt_c, out_mean=mean_c, ws=ws_cdc,
-                                                                 total_paths=total)
+                                                                 space=space_c, out_YT=yt_c, out_mean=mean_c,
+                                                                 ws=ws_cdc, total_paths=total)
             run_c()
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -436,27 +438,29 @@ def main():
                 continue
             c_rate = path_steps / (e0.elapsed_time(e1) / 5 * 1e-3)
             secondary[key + "_path_steps_per_s"] = c_rate
-            if model_c == sl.MODEL_MLP:
+            if key == "cdc":
                 sms = torch.cuda.get_device_properties(dev).multi_processor_count
                 fp32_peak = sms * 128 * 2 * peaks["sm_max_mhz"] * 1e6
                 secondary["cdc_fp32_roofline_frac"] = CDC_FLOPS_PER_PATH_STEP * c_rate / fp32_peak
                 secondary["cdc_over_7l_bf16"] = c_rate / value
         secondary["cdc_workload"] = ("7L-CDC on the GBM workload above (16 sets x %d paths x %d steps, m=7); tables "
-                                     "of (m+1) network evaluations per (set, step), then 2 paths per thread; "
-                                     "network: %s" % (args.paths, n_steps, cdc_net_kind))
+                                     "of network evaluations per (set, step), then 2 paths per thread; cdc: in the "
+                                     "marginal's quantile coordinate, cdc_y: interpolation in Y; network: %s"
+                                     % (args.paths, n_steps, cdc_net_kind))
         if args.weights == "trained" and "cdc_error" not in secondary:
             # accuracy on every path against the exact-collocation GBM chain on the same normals:
             # the 7L-CDC scheme and the 7L scheme (BF16 form) with the same network
             yt_ex = torch.empty_like(yt)
             sl.seven_league_simulate_batched(sl.MODEL_GBM_EXACT, None, theta, Y0, off, T, n_steps, m, seed,
                                              out_YT=yt_ex, total_paths=total)
-            sl.seven_league_cdc_simulate_batched(sl.MODEL_MLP, net_cdc, theta, Y0, off, T, n_steps, m, seed,
-                                                 out_YT=yt_c, ws=ws_cdc, total_paths=total)
+            ex = yt_ex.double()
+            for space_c, key in ((sl.CDC_QUANTILE, "cdc"), (sl.CDC_Y, "cdc_y")):
+                sl.seven_league_cdc_simulate_batched(sl.MODEL_MLP, net_cdc, theta, Y0, off, T, n_steps, m, seed,
+                                                     space=space_c, out_YT=yt_c, ws=ws_cdc, total_paths=total)
+                secondary[key + "_mean_abs_err_vs_exact_map"] = float((yt_c.double() - ex).abs().mean().item())
             yt_7 = torch.empty_like(yt)
             sl.seven_league_simulate_batched(sl.MODEL_MLP, sl.make_net(P_cdc, 4, 7, prec=sl.PREC_BF16), theta, Y0,
                                              off, T, n_steps, m, seed, out_YT=yt_7, total_paths=total)
-            ex = yt_ex.double()
-            secondary["cdc_mean_abs_err_vs_exact_map"] = float((yt_c.double() - ex).abs().mean().item())
             secondary["7l_same_network_mean_abs_err_vs_exact_map"] = float((yt_7.double() - ex).abs().mean().item())
             del yt_ex, yt_7
         del yt_c, ws_cdc
@@ -580,16 +584,17 @@ def main():
                                                device=dev)
         th_ou, y0_ou = torch.tensor([[0.5, 0.3, 1.0]], device=dev), torch.tensor([1.5], device=dev)
         ou_ms = {}
-        for pr, key in ((sl.PREC_BF16, "bf16"), (sl.PREC_FP32, "fp32"), (sl.PREC_FP32, "cdc")):
+        for pr, key in ((sl.PREC_BF16, "bf16"), (sl.PREC_FP32, "fp32"), (sl.PREC_FP32, "cdc"), (sl.PREC_FP32, "cdc_y")):
             net_ou = sl.make_net(P_ou, 5, 5, prec=pr)
             for n_ou in (1000, 50000, 100000, 200000):
                 off_ou = torch.as_tensor(W.offsets_from_counts([n_ou]), device=dev)
                 yt_ou = torch.empty(n_ou, dtype=f32, device=dev)
-                if key == "cdc":
+                if key.startswith("cdc"):
                     ws_ou = torch.empty(sl.cdc_workspace_size(n_ou, 1, 16), dtype=torch.uint8, device=dev)
+                    sp_ou = sl.CDC_Y if key == "cdc_y" else sl.CDC_QUANTILE
                     run_ou = lambda: sl.seven_league_cdc_simulate_batched(sl.MODEL_MLP, net_ou, th_ou, y0_ou, off_ou,
-                                                                          2.0, 16, 5, 3, out_YT=yt_ou, ws=ws_ou,
-                                                                          total_paths=n_ou)
+                                                                          2.0, 16, 5, 3, space=sp_ou, out_YT=yt_ou,
+                                                                          ws=ws_ou, total_paths=n_ou)
                 else:
                     ws_ou = torch.empty(sl.simulate_workspace_size(n_ou, 1), dtype=torch.uint8, device=dev)
                     run_ou = lambda: sl.seven_league_simulate_batched(sl.MODEL_MLP, net_ou, th_ou, y0_ou, off_ou, 2.0,
@@ -610,7 +615,7 @@ def main():
         secondary["ou_table61_ms_per_run"] = ou_ms
         secondary["ou_table61_workload"] = ("OU (Ybar 0.5, sigma 0.3, lambda 1, Y0 1.5), m=5, trained 5->50x4->5 ReLU "
                                             "network (horizons 0.125..2), T=2 in 16 steps; paths 1e3/5e4/1e5/2e5 as "
-                                            "in Table 6.1; keys bf16/fp32 = 7L scheme, cdc = 7L-CDC scheme")
+                                            "in Table 6.1; keys bf16/fp32 = 7L scheme, cdc / cdc_y = 7L-CDC scheme (quantile coordinate / Y)")
 
     # --- end to end through the C ABI with host buffers (pinned), copies timed.  Every step copies
     # its inputs host -> device, runs the sampler and copies Y_T and the set moments back; the steps

@@ -206,17 +206,39 @@ int sl_tc_get_pipeline(void);
  *     (features [Y0, t_i, theta]); G = marg_net (NULL: net) for SL_MODEL_MLP,
  *     the exact map for the exact models.  At i = 0, z_k = Y0[s];
  *   - conditional points at the nodes C[k][j] = H_j(z_k, dt, theta_s);
+ * and then, by `space`:
+ * SL_CDC_SPACE_Y (interpolation in Y through the marginal nodes):
  *   - a path at Y_i takes yhat_j = sum_k C[k][j] L_k(Y_i), L_k the Lagrange
  *     basis in Y through the z_k, while min z <= Y_i <= max z; beyond the
  *     outermost node on a side, the line through the two outermost nodes on
  *     that side (degree m-1 extrapolation grows without bound); yhat = C[0]
  *     when all z_k coincide, as at i = 0.  Then Y_{i+1} = g_m(X) through
  *     (x_j, yhat_j), with the normals of the 7L sampler (tag 0).
- * With a conditional map that is affine in Y (the exact GBM and OU maps) the
- * chain equals the 7L chain.  The network evaluations ((m + 1) per set and
- * step) run in FP32 on CUDA cores whatever net->prec says; the paths run in
- * FP32.
+ *   With a conditional map that is affine in Y (the exact GBM and OU maps)
+ *   the chain equals the 7L chain.  Lagrange interpolation through the
+ *   quantiles of a wide marginal (a lognormal with sigma sqrt(t) ~ 0.7) is
+ *   ill-conditioned: a network's errors in C are magnified up to ~1e3-1e5.
+ * SL_CDC_SPACE_QUANTILE (interpolation in the marginal's quantile coordinate):
+ *   - G_i(xi) = sum_k z^(i)_k L_k(xi) through the Gauss-Hermite points x_k
+ *     (continued beyond them by the lines through the two outermost nodes)
+ *     is the marginal collocation map of t_i; a path carries xi_i (xi_0 = 0)
+ *     with Y_i = G_i(xi_i);
+ *   - eta[k][j] = G_{i+1}^{-1}(C[k][j]) (beyond [z_0, z_{m-1}] the lines;
+ *     inside, the first root in the first node interval [x_k, x_{k+1}] with
+ *     z_k <= y <= z_{k+1}: the first of 32 equal cells of that interval where
+ *     G reaches y, and the root in it); xi_{i+1} = sum_k sum_j eta[k][j]
+ *     L_k(xi_i) L_j(X) for xi_i in [x_0, x_{m-1}] (beyond, the line in xi
+ *     through the two outermost node rows sum_j eta[k][j] L_j(X)),
+ *     Gauss-Hermite points in both variables (as well conditioned as g_m);
+ *   - G_{i+1} must increase from its first to its last node (else the paths
+ *     are NaN: SL_DEV_NONFINITE); coinciding nodes give Y_{i+1} = z_0.
+ *   With the exact OU map the chain equals the 7L chain.
+ * The network evaluations ((m + 1) per set and step; m + 2 in the quantile
+ * coordinate) run in FP32 on CUDA cores whatever net->prec says; the paths
+ * run in FP32; the inverses and the interpolants' coefficients in FP64.
  * ---------------------------------------------------------------------- */
+#define SL_CDC_SPACE_Y 0
+#define SL_CDC_SPACE_QUANTILE 1
 
 /* Bytes of workspace seven_league_cdc_simulate_batched needs. */
 size_t sl_cdc_workspace_size(int64_t total_paths, int n_sets, int n_steps);
@@ -224,9 +246,18 @@ size_t sl_cdc_workspace_size(int64_t total_paths, int n_sets, int n_steps);
 /*
  * Batched 7L-CDC sampler.  Arguments, outputs and errors as
  * seven_league_simulate_batched, plus marg_net (SL_MODEL_MLP only; NULL = use
- * net; same d_in and m as net, its own activation).  The workspace holds, at
- * byte offset 256, the tables of the call: FP32 [n_sets][n_steps][224] with,
- * per (set, step): [0,8) z (the marginal nodes, zero beyond m); [8,16) w
+ * net; same d_in and m as net, its own activation) and space
+ * (SL_CDC_SPACE_Y or SL_CDC_SPACE_QUANTILE; SL_ERR_ARG otherwise).  The
+ * workspace holds, at byte offset 256, the tables of the call: FP32
+ * [n_sets][n_steps][224].  SL_CDC_SPACE_QUANTILE, per (set, step): [0,8) the
+ * marginal nodes of t_{i+1}; [8,16) the monomial coefficients of G_{i+1}
+ * (FP64, rounded once); [16] x_0, [17] x_{m-1}, [18] the slope of the line
+ * below x_0, [19] above x_{m-1}, [20] z_0, [21] z_{m-1}, [22] x_1, [23]
+ * x_{m-2}; [24,88) eta[8][8]; [88,152) B[a][b] with xi_{i+1} = sum_a xi_i^a
+ * sum_b B[a][b] X^b (FP64, rounded once); [152,184) the monomial rows in X of
+ * the node rows 0, 1, m-2, m-1 (for xi beyond the hull); zero elsewhere and
+ * beyond m.  SL_CDC_SPACE_Y, per (set,
+ * step): [0,8) z (the marginal nodes, zero beyond m); [8,16) w
  * (their barycentric weights 1/prod_{l!=k}(z_k - z_l), computed in FP64 from
  * the FP32 nodes; all zero when the nodes coincide); [16,80) C[8][8] (row k =
  * the conditional points at z_k, zero beyond m); [80,88) S_lo and [88,96)
@@ -242,7 +273,7 @@ size_t sl_cdc_workspace_size(int64_t total_paths, int n_sets, int n_steps);
  * [216,224) of S_hi.  Nodes that
  * coincide only in part give non-finite paths (SL_DEV_NONFINITE).
  */
-int seven_league_cdc_simulate_batched(int model, const sl_net* net, const sl_net* marg_net,
+int seven_league_cdc_simulate_batched(int model, const sl_net* net, const sl_net* marg_net, int space,
                                       const float* theta, int p, const float* Y0,
                                       const int64_t* path_offsets, int n_sets, int64_t total_paths,
                                       float T, int n_steps, int m, uint64_t seed, float* out_YT,

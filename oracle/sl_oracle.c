@@ -892,15 +892,19 @@ int orc_cdc_paths(int model, const double* P, const double* Pm, int d_in, int wi
  *  - eta[k][j] = G_{i+1}^{-1}(C[k][j]): the conditional points at the marginal
  *    nodes of t_i, expressed in the quantile coordinate of t_{i+1};
  *  - xi_{i+1} = sum_k sum_j eta[k][j] L_k(xi_i) L_j(X_{i+1}) (Lagrange in both
- *    variables through the Gauss-Hermite points);
+ *    variables through the Gauss-Hermite points) for xi_i in [x_0, x_{m-1}];
+ *    beyond, the line in xi through the two outermost node rows (degree m-1
+ *    extrapolation in xi grows without bound along a path, as in Y);
  *  - Y_i = G_i(xi_i) wherever Y is output (the grid, Y_T = G_N(xi_N)).
  * At i = 0 the marginal is the point Y0: every row of C is H(Y0, dt), so xi_1
  * does not depend on xi_0 (taken as 0).  If the nodes at t_{i+1} all coincide,
  * G_{i+1} is constant: eta = 0 and Y_{i+1} = z^(i+1)_0.  G must increase from
  * its first to its last node (z_0 < z_{m-1}); the inverse inside the hull is
- * the root of G(xi) = y in the first node interval [x_k, x_{k+1}] with
- * z_k <= y <= z_{k+1} (one exists whenever z_0 <= y <= z_{m-1}), found by 60
- * bisections of that interval (for a G that increases, the one root).
+ * the first root of G(xi) = y in the first node interval [x_k, x_{k+1}] with
+ * z_k <= y <= z_{k+1} (one exists whenever z_0 <= y <= z_{m-1}): the interval
+ * is scanned at 32 equal steps for the first point where G >= y, and the root
+ * in that cell is found by 60 bisections (for a G that increases, the one
+ * root; a G that wiggles inside a node interval can cross y more than once).
  * With the exact OU map (G linear, C affine in z and x_j) the chain equals the
  * 7L chain exactly.
  * ---------------------------------------------------------------------- */
@@ -926,7 +930,10 @@ double orc_cdcq_Ginv(int m, const double* xn, const double* z, double y) {
     if (y > z[m - 1]) return xn[m - 1] + (y - z[m - 1]) * (xn[m - 1] - xn[m - 2]) / (z[m - 1] - z[m - 2]);
     int k = 0;
     while (k < m - 2 && !(z[k] <= y && y <= z[k + 1])) ++k;
-    double lo = xn[k], hi = xn[k + 1];
+    double h = (xn[k + 1] - xn[k]) / 32.0;
+    int c = 1;
+    while (c < 32 && orc_lagrange(m, xn, z, xn[k] + c * h) < y) ++c;
+    double lo = xn[k] + (c - 1) * h, hi = c < 32 ? xn[k] + c * h : xn[k + 1];
     for (int it = 0; it < 60; ++it) {
         double mid = 0.5 * (lo + hi);
         if (orc_lagrange(m, xn, z, mid) < y) lo = mid; else hi = mid;
@@ -934,8 +941,26 @@ double orc_cdcq_Ginv(int m, const double* xn, const double* z, double y) {
     return 0.5 * (lo + hi);
 }
 
-/* sum_k sum_j eta[k*m + j] L_k(xi) L_j(X) (plain Lagrange definition). */
+/* sum_k sum_j eta[k*m + j] L_k(xi) L_j(X) (plain Lagrange definition) for xi in
+ * [x_0, x_{m-1}]; beyond, the line in xi through the two outermost node rows
+ * (R_k(X) = sum_j eta[k][j] L_j(X)), as the interpolation in Y is continued. */
+static double cdcq_row(int m, const double* xn, const double* eta, int k, double X) {
+    double r = 0.0;
+    for (int j = 0; j < m; ++j) {
+        double Lj = 1.0;
+        for (int l = 0; l < m; ++l)
+            if (l != j) Lj *= (X - xn[l]) / (xn[j] - xn[l]);
+        r += eta[k * m + j] * Lj;
+    }
+    return r;
+}
+
 double orc_cdcq_F(int m, const double* xn, const double* eta, double xi, double X) {
+    if (xi < xn[0] || xi > xn[m - 1]) {
+        int a = xi < xn[0] ? 0 : m - 1, b = xi < xn[0] ? 1 : m - 2;
+        double ra = cdcq_row(m, xn, eta, a, X), rb = cdcq_row(m, xn, eta, b, X);
+        return ra + (xi - xn[a]) * (rb - ra) / (xn[b] - xn[a]);
+    }
     double v = 0.0;
     for (int k = 0; k < m; ++k) {
         double Lk = 1.0;

@@ -31,6 +31,7 @@ SDE_GBM, SDE_OU, SDE_CIR = 0, 1, 2
 ACT_RELU, ACT_SOFTPLUS = 0, 1
 PREC_FP32, PREC_BF16 = 0, 1
 PAYOFF_CALL = 0
+CDC_Y, CDC_QUANTILE = 0, 1          # 7L-CDC interpolation space (SL_CDC_SPACE_*)
 WIDTH, N_HIDDEN, MIN_M, MAX_M = 50, 4, 2, 8
 SL_DEV_NONFINITE, SL_DEV_OFFSETS, SL_DEV_TIMEOUT, SL_DEV_INDEX = 0x1, 0x2, 0x4, 0x8   # device status bits
 _STATUS_NAMES = {1: "SL_ERR_ARG", 2: "SL_ERR_UNSUPPORTED", 3: "SL_ERR_WORKSPACE",
@@ -119,7 +120,7 @@ def load(path: str = LIB_PATH):
     L.sl_cdc_workspace_size.argtypes = [_i64, _i, _i]
     L.sl_cdc_workspace_size.restype = _sz
     L.seven_league_cdc_simulate_batched.argtypes = [
-        _i, ctypes.POINTER(sl_net), ctypes.POINTER(sl_net), _vp, _i, _vp, _vp, _i, _i64, _f, _i, _i, _u64,
+        _i, ctypes.POINTER(sl_net), ctypes.POINTER(sl_net), _i, _vp, _i, _vp, _vp, _i, _i64, _f, _i, _i, _u64,
         _vp, _vp, _vp, _vp, _vp, _sz, _vp]
     L.em_collocation_labels_noalloc.argtypes = [_i, _vp, _vp, _vp, _i, _i64, _i, _i, _u64, _vp, _vp]
     L.sl_em_labels_noalloc_max_samples.restype = _sz
@@ -292,9 +293,10 @@ def cdc_workspace_size(total_paths, n_sets, n_steps):
 
 
 def seven_league_cdc_simulate_batched(model, net, theta, Y0, path_offsets, T, n_steps, m, seed,
-                                      marg_net=None, out_YT=None, out_grid=None, out_mean=None,
-                                      out_var=None, ws=None, total_paths=None, stream=None):
-    """Batched 7L-CDC sampler (see include/sevenleague.h); marg_net None = net.
+                                      marg_net=None, space=CDC_QUANTILE, out_YT=None, out_grid=None,
+                                      out_mean=None, out_var=None, ws=None, total_paths=None, stream=None):
+    """Batched 7L-CDC sampler (see include/sevenleague.h); marg_net None = net; space CDC_QUANTILE
+    (the marginal's quantile coordinate) or CDC_Y (interpolation in Y).
     Returns the workspace used (status word first, then the tables)."""
     torch = _torch()
     L = load()
@@ -307,7 +309,7 @@ def seven_league_cdc_simulate_batched(model, net, theta, Y0, path_offsets, T, n_
     netp = ctypes.byref(net) if net is not None else None
     mnetp = ctypes.byref(marg_net) if marg_net is not None else None
     _check(L.seven_league_cdc_simulate_batched(
-        model, netp, mnetp, _ptr(theta, torch.float32, "theta"), p, _ptr(Y0, torch.float32, "Y0"),
+        model, netp, mnetp, int(space), _ptr(theta, torch.float32, "theta"), p, _ptr(Y0, torch.float32, "Y0"),
         _ptr(path_offsets, torch.int64, "path_offsets"), n_sets, int(total_paths), float(T),
         n_steps, m, seed, _ptr(out_YT, torch.float32, "out_YT"),
         _ptr(out_grid, torch.float32, "out_grid"), _ptr(out_mean, torch.float64, "out_mean"),

@@ -64,6 +64,7 @@ struct CdcArgs {
     float* tab;                // [n_sets][n_steps][kTabFloats]
     GHConst gh;
     double bq[SL_MAX_M][SL_MAX_M];   // b_j q_j[a]: monomial coefficients of b_j Q_j (FP64, zero past m)
+    double xg[SL_MAX_M];             // the Gauss-Hermite points in FP64
 };
 
 // Collocation points of the exact models over the horizon h from Y:
@@ -350,6 +351,219 @@ __global__ void __launch_bounds__(kTabThreads, 2) cdc_table_kernel(const CdcArgs
     }
 }
 
+// ---------------------------------------------------------------------------
+// The quantile-coordinate reading.  A path carries xi with Y = G_i(xi), G_i the
+// marginal collocation map through the Gauss-Hermite points (continued beyond
+// them by the lines through the two outermost nodes).  Per (set, step) the
+// table holds, in the same 224-float slot:
+//   [0,8) zn, the marginal nodes of t_{i+1}; [8,16) Gm, the monomial coefficients
+//   of G_{i+1} inside [x_0, x_{m-1}]; [16] x_0, [17] x_{m-1}, [18] the slope below
+//   x_0, [19] above x_{m-1}, [20] zn_0, [21] zn_{m-1}, [22] x_1, [23] x_{m-2};
+//   [24,88) eta[k][j] =
+//   G_{i+1}^{-1}(C[k][j]); [88,152) B[a][b], the monomial coefficients of the
+//   tensor-product interpolant: xi_{i+1} = sum_a xi_i^a sum_b B[a][b] X^b for xi_i in
+//   [x_0, x_{m-1}]; [152,184) the monomial rows in X of the node rows R_0, R_1,
+//   R_{m-2}, R_{m-1} (R_k(X) = sum_j eta[k][j] L_j(X)): beyond the hull xi_{i+1}
+//   follows the line in xi through the two outermost node rows.
+// ---------------------------------------------------------------------------
+constexpr int kQGm = 8, kQEdge = 16, kQEta = 24, kQB = 88, kQR = 152;
+
+size_t tableq_smem_bytes(int model) {
+    return (model == SL_MODEL_MLP ? 2 * sizeof(SmemNet) : 0) +
+           (static_cast<size_t>(kGroups) * 2 * kBufStride + kBatch * 8 + kBatch * 8 + kBatch * 64 + kBatch * 8) *
+               sizeof(float) +
+           static_cast<size_t>(kBatch) * (8 + 64) * sizeof(double) + static_cast<size_t>(kBatch) * sizeof(int);
+}
+
+// G_{i+1}^{-1}(y) (flag 1: the nodes coincide, 0; flag 2: G does not increase from its
+// first to its last node, NaN).  Beyond [zn_0, zn_{m-1}] the lines through the two
+// outermost nodes; inside, the first root in the first node interval [x_k, x_{k+1}] with
+// zn_k <= y <= zn_{k+1}: the interval is scanned at 32 equal steps for the first point
+// where G >= y (FP32), the root in that cell is refined by Newton in FP32 (bisecting
+// whenever a step leaves the cell that brackets it, 8 steps), then by two Newton steps in
+// FP64 on the FP64 coefficients, clamped to the cell (the root may be one of its ends).
+__device__ double quantile_inverse(const float* zn, const float* g32, const double* g64, const double* xg, int m,
+                                   int flag, double y) {
+    if (flag == 1) return 0.0;
+    if (flag == 2) return __longlong_as_double(0x7ff8000000000000LL);
+    const double z0 = zn[0], z1 = zn[1], zl = zn[m - 1], zl1 = zn[m - 2];
+    if (y < z0) return xg[0] + (y - z0) * (xg[1] - xg[0]) / (z1 - z0);
+    if (y > zl) return xg[m - 1] + (y - zl) * (xg[m - 1] - xg[m - 2]) / (zl - zl1);
+    int k = 0;
+    while (k < m - 2 && !(static_cast<double>(zn[k]) <= y && y <= static_cast<double>(zn[k + 1]))) ++k;
+    const float yf = static_cast<float>(y);
+    auto g32at = [&](float v) {
+        float gv = g32[m - 1];
+        for (int ai = m - 2; ai >= 0; --ai) gv = fmaf(gv, v, g32[ai]);
+        return gv;
+    };
+    const double h = (xg[k + 1] - xg[k]) / 32.0;
+    int c = 1;
+    while (c < 32 && g32at(static_cast<float>(xg[k] + c * h)) < yf) ++c;
+    const double dlo = xg[k] + (c - 1) * h, dhi = c < 32 ? xg[k] + c * h : xg[k + 1];
+    float lo = static_cast<float>(dlo), hi = static_cast<float>(dhi);
+    float xi = 0.5f * (lo + hi);
+    for (int it = 0; it < 8; ++it) {
+        float gv = g32[m - 1], gd = 0.0f;
+        for (int ai = m - 2; ai >= 0; --ai) {
+            gd = fmaf(gd, xi, gv);
+            gv = fmaf(gv, xi, g32[ai]);
+        }
+        const float f = gv - yf;
+        if (f < 0.0f) lo = xi; else hi = xi;
+        float nx = (gd != 0.0f) ? xi - f / gd : 0.5f * (lo + hi);
+        if (!(nx > lo && nx < hi)) nx = 0.5f * (lo + hi);
+        xi = nx;
+    }
+    double x = xi;
+    for (int it = 0; it < 2; ++it) {
+        double gv = g64[m - 1], gd = 0.0;
+        for (int ai = m - 2; ai >= 0; --ai) {
+            gd = fma(gd, x, gv);
+            gv = fma(gv, x, g64[ai]);
+        }
+        const double nx = (gd != 0.0) ? x - (gv - y) / gd : x;
+        x = fmin(fmax(nx, dlo), dhi);      // the root lies in the cell (it may be an end)
+    }
+    return x;
+}
+
+template <int MODEL, int ACT, int MACT>
+__global__ void __launch_bounds__(kTabThreads, 2) cdcq_table_kernel(const CdcArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemNet& cnet = *reinterpret_cast<SmemNet*>(smem_raw);
+    SmemNet& mnet = *reinterpret_cast<SmemNet*>(smem_raw + sizeof(SmemNet));
+    float* bufs = reinterpret_cast<float*>(smem_raw + (MODEL == SL_MODEL_MLP ? 2 * sizeof(SmemNet) : 0));
+    float* zs = bufs + kGroups * 2 * kBufStride;   // [kBatch][8] marginal nodes of t_i
+    float* zns = zs + kBatch * 8;                  // [kBatch][8] marginal nodes of t_{i+1}
+    float* Cs = zns + kBatch * 8;                  // [kBatch][8][8] conditional rows
+    float* ths = Cs + kBatch * 64;                 // [kBatch][8]: Y0 of the entry's set, then theta
+    double* g64 = reinterpret_cast<double*>(ths + kBatch * 8);   // [kBatch][8] coefficients of G_{i+1}
+    double* e64 = g64 + kBatch * 8;                // [kBatch][8][8] eta
+    int* flag = reinterpret_cast<int*>(e64 + kBatch * 64);       // [kBatch]
+    const bool one_net = a.mparams == a.params;
+    if (MODEL == SL_MODEL_MLP) {
+        stage_net(cnet, a.params, a.d_in, a.m);
+        if (!one_net) stage_net(mnet, a.mparams, a.d_in, a.m);
+        __syncthreads();
+    }
+    const SmemNet& gnet = one_net ? cnet : mnet;
+    const int grp = threadIdx.x / kGroup, sub = threadIdx.x % kGroup;
+    const unsigned gm = 0xFFu << (threadIdx.x & 24);
+    float* in = bufs + grp * 2 * kBufStride;
+    float* tmp = in + kBufStride;
+    const int m = a.m;
+    const int64_t n = static_cast<int64_t>(a.n_sets) * a.n_steps;
+    for (int64_t base = static_cast<int64_t>(blockIdx.x) * kBatch; base < n;
+         base += static_cast<int64_t>(gridDim.x) * kBatch) {
+        if (threadIdx.x < kBatch * 8) {
+            const int e = threadIdx.x / 8, c = threadIdx.x % 8;
+            const int64_t u = base + e;
+            float v = 0.0f;
+            if (u < n) {
+                const int s = static_cast<int>(u / a.n_steps);
+                v = c == 0 ? __ldg(a.Y0 + s) : (c - 1 < a.p ? __ldg(a.theta + static_cast<int64_t>(s) * a.p + c - 1) : 0.0f);
+            }
+            ths[threadIdx.x] = v;
+        }
+        __syncthreads();
+        // (A) groups e < kBatch: the nodes of t_i; groups kBatch + e: the nodes of t_{i+1}
+        if (grp < 2 * kBatch) {
+            const int e = grp % kBatch;
+            const bool next = grp >= kBatch;
+            const int64_t u = base + e;
+            float* z = (next ? zns : zs) + e * 8;
+            if (u < n) {
+                const int i = static_cast<int>(u % a.n_steps) + (next ? 1 : 0);
+                const float y0 = ths[e * 8];
+                if (i == 0) z[sub] = sub < m ? y0 : 0.0f;
+                else group_map<MODEL, MACT>(gnet, in, tmp, sub, gm, a, ths + e * 8 + 1, y0, static_cast<float>(i) * a.dt, z);
+            } else {
+                z[sub] = 0.0f;
+            }
+        }
+        __syncthreads();
+        // (B) conditional rows at the nodes of t_i
+#pragma unroll 1
+        for (int r = 0; r < kBatch * 8 / kGroups; ++r) {
+            const int job = grp + kGroups * r, e = job / 8, k = job % 8;
+            const int64_t u = base + e;
+            float* crow = Cs + e * 64 + k * 8;
+            if (u < n && k < m) group_map<MODEL, ACT>(cnet, in, tmp, sub, gm, a, ths + e * 8 + 1, zs[e * 8 + k], a.dt, crow);
+            else crow[sub] = 0.0f;
+        }
+        __syncthreads();
+        // (C1) thread (e, a): coefficient a of G_{i+1}, node a of t_{i+1}, the edges
+        if (threadIdx.x < kBatch * 8) {
+            const int e = threadIdx.x / 8, ai = threadIdx.x % 8;
+            const int64_t u = base + e;
+            if (u < n) {
+                const float* zn = zns + e * 8;
+                float* t = a.tab + u * kTabFloats;
+                double acc = 0.0;
+                for (int k = 0; k < m; ++k) acc += static_cast<double>(zn[k]) * a.bq[k][ai];
+                g64[e * 8 + ai] = acc;
+                t[kQGm + ai] = static_cast<float>(acc);
+                t[ai] = zn[ai];
+                if (ai == 0) {
+                    bool same = true;
+                    for (int k = 1; k < m; ++k) same = same && zn[k] == zn[0];
+                    flag[e] = same ? 1 : (zn[m - 1] > zn[0] ? 0 : 2);
+                    const double x0 = a.xg[0], x1 = a.xg[1], xl = a.xg[m - 1], xl1 = a.xg[m - 2];
+                    t[kQEdge + 0] = static_cast<float>(x0);
+                    t[kQEdge + 1] = static_cast<float>(xl);
+                    t[kQEdge + 2] = static_cast<float>((static_cast<double>(zn[1]) - zn[0]) / (x1 - x0));
+                    t[kQEdge + 3] = static_cast<float>((static_cast<double>(zn[m - 1]) - zn[m - 2]) / (xl - xl1));
+                    t[kQEdge + 4] = zn[0];
+                    t[kQEdge + 5] = zn[m - 1];
+                    t[kQEdge + 6] = static_cast<float>(x1);
+                    t[kQEdge + 7] = static_cast<float>(xl1);
+                }
+            }
+        }
+        __syncthreads();
+        // (C2) thread (e, k, j): eta[k][j] = G_{i+1}^{-1}(C[k][j])
+        {
+            const int e = threadIdx.x / 64, k = (threadIdx.x / 8) % 8, j = threadIdx.x % 8;
+            const int64_t u = base + e;
+            if (u < n) {
+                double v = 0.0;
+                if (k < m && j < m) {
+                    float* t = a.tab + u * kTabFloats;
+                    v = quantile_inverse(zns + e * 8, t + kQGm, g64 + e * 8, a.xg, m, flag[e], Cs[e * 64 + k * 8 + j]);
+                }
+                e64[e * 64 + k * 8 + j] = v;
+                a.tab[u * kTabFloats + kQEta + k * 8 + j] = static_cast<float>(v);
+            }
+        }
+        __syncthreads();
+        // (C3) thread (e, a, b): B[a][b] = sum_k bq[k][a] sum_j eta[k][j] bq[j][b]
+        {
+            const int e = threadIdx.x / 64, ai = (threadIdx.x / 8) % 8, b = threadIdx.x % 8;
+            const int64_t u = base + e;
+            if (u < n) {
+                double acc = 0.0;
+                for (int k = 0; k < m; ++k) {
+                    double row = 0.0;
+                    for (int j = 0; j < m; ++j) row += e64[e * 64 + k * 8 + j] * a.bq[j][b];
+                    acc += a.bq[k][ai] * row;
+                }
+                float* t = a.tab + u * kTabFloats;
+                t[kQB + ai * 8 + b] = static_cast<float>(acc);
+                if (ai < 4) {                          // node row r of R_0, R_1, R_{m-2}, R_{m-1}
+                    const int kr = ai < 2 ? ai : m - 4 + ai;
+                    double row = 0.0;
+                    for (int j = 0; j < m; ++j) row += e64[e * 64 + kr * 8 + j] * a.bq[j][b];
+                    t[kQR + ai * 8 + b] = static_cast<float>(row);
+                } else if (ai == 4 && b == 0) {
+                    for (int z = kQR + 32; z < kTabFloats; ++z) t[z] = 0.0f;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // P_k(X) = prod_{l != k} (X - n_l) for k < M (prefix and suffix products).
 template <int M>
 __device__ __forceinline__ void prod_except(float X, const float (&nd)[8], float (&P)[M]) {
@@ -436,9 +650,53 @@ __device__ __forceinline__ void cdc_step(const float* __restrict__ t, float (&Y)
     for (int p = 0; p < NP; ++p) Y[p] = ynew[p];
 }
 
-// The whole time loop of NP paths of one set s (path indices q[p] within the set, flat
-// indices g[p]; write[p] false for a padding lane).
+// Quantile coordinate: xi[p] <- sum_a xi^a sum_b B[a][b] X^b (Horner in X for every row,
+// then in xi), the table loaded once for all NP paths.
 template <int M, int NP>
+__device__ __forceinline__ void cdcq_step(const float* __restrict__ t, float (&xi)[NP], const float (&X)[NP]) {
+    float row[8], acc[NP];
+    load8(t + kQB + 8 * (M - 1), row);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) acc[p] = horner<M>(row, X[p]);
+#pragma unroll
+    for (int ai = M - 2; ai >= 0; --ai) {
+        load8(t + kQB + 8 * ai, row);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) acc[p] = fmaf(acc[p], xi[p], horner<M>(row, X[p]));
+    }
+    const float2 hull = __ldg(reinterpret_cast<const float2*>(t + kQEdge));   // x_0, x_{m-1}
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        if (xi[p] < hull.x || xi[p] > hull.y) {    // beyond the hull: the line through the outer rows
+            const bool below = xi[p] < hull.x;
+            float ra[8], rb[8];
+            load8(t + kQR + (below ? 0 : 24), ra);
+            load8(t + kQR + (below ? 8 : 16), rb);
+            const float va = horner<M>(ra, X[p]), vb = horner<M>(rb, X[p]);
+            const float xa = below ? hull.x : hull.y;
+            const float xb = below ? __ldg(t + kQEdge + 6) : __ldg(t + kQEdge + 7);   // x_1, x_{m-2}
+            acc[p] = fmaf(xi[p] - xa, (vb - va) / (xb - xa), va);
+        }
+        xi[p] = acc[p];
+    }
+}
+
+// Y = G_{i+1}(xi) from the table of step i: Horner inside [x_0, x_{m-1}], the lines beyond.
+template <int M>
+__device__ __forceinline__ float cdcq_value(const float* __restrict__ t, float xi) {
+    const float4 e = __ldg(reinterpret_cast<const float4*>(t + kQEdge));       // x_0, x_{m-1}, slopes
+    const float2 zz = __ldg(reinterpret_cast<const float2*>(t + kQEdge + 4));  // zn_0, zn_{m-1}
+    if (xi < e.x) return fmaf(xi - e.x, e.z, zz.x);
+    if (xi > e.y) return fmaf(xi - e.y, e.w, zz.y);
+    float gmr[8];
+    load8(t + kQGm, gmr);
+    return horner<M>(gmr, xi);
+}
+
+// The whole time loop of NP paths of one set s (path indices q[p] within the set, flat
+// indices g[p]; write[p] false for a padding lane).  SPACE: SL_CDC_SPACE_Y carries Y,
+// SL_CDC_SPACE_QUANTILE carries xi (Y = G_i(xi) where it is output).
+template <int M, int NP, int SPACE>
 __device__ __forceinline__ void cdc_paths(const SimArgs& a, const float* __restrict__ ts, int s,
                                           const int64_t (&q)[NP], const int64_t (&g)[NP], const bool (&write)[NP]) {
     float Y[NP], X[NP];
@@ -446,7 +704,7 @@ __device__ __forceinline__ void cdc_paths(const SimArgs& a, const float* __restr
     const float y0 = __ldg(a.Y0 + s);
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        Y[p] = y0;
+        Y[p] = SPACE == SL_CDC_SPACE_Y ? y0 : 0.0f;     // quantile coordinate: xi_0 = 0
         if (a.out_grid && write[p]) a.out_grid[g[p]] = y0;
     }
     for (int i = 0; i < a.n_steps; ++i) {
@@ -457,18 +715,24 @@ __device__ __forceinline__ void cdc_paths(const SimArgs& a, const float* __restr
                                 static_cast<uint32_t>(i >> 2));
             X[p] = pick4(z4[p], i & 3);
         }
-        cdc_step<M, NP>(ts + static_cast<int64_t>(i) * kTabFloats, Y, X);
+        const float* t = ts + static_cast<int64_t>(i) * kTabFloats;
+        if (SPACE == SL_CDC_SPACE_Y) cdc_step<M, NP>(t, Y, X);
+        else cdcq_step<M, NP>(t, Y, X);
         if (a.out_grid) {
 #pragma unroll
             for (int p = 0; p < NP; ++p)
-                if (write[p]) a.out_grid[static_cast<int64_t>(i + 1) * a.total + g[p]] = Y[p];
+                if (write[p])
+                    a.out_grid[static_cast<int64_t>(i + 1) * a.total + g[p]] =
+                        SPACE == SL_CDC_SPACE_Y ? Y[p] : cdcq_value<M>(t, Y[p]);
         }
     }
+    const float* tl = ts + static_cast<int64_t>(a.n_steps - 1) * kTabFloats;
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         if (!write[p]) continue;
-        if (a.out_YT) a.out_YT[g[p]] = Y[p];
-        if (!isfinite(Y[p])) raise_status(a.status, SL_DEV_NONFINITE);
+        const float yT = SPACE == SL_CDC_SPACE_Y ? Y[p] : cdcq_value<M>(tl, Y[p]);
+        if (a.out_YT) a.out_YT[g[p]] = yT;
+        if (!isfinite(yT)) raise_status(a.status, SL_DEV_NONFINITE);
     }
 }
 
@@ -477,7 +741,7 @@ __device__ __forceinline__ void cdc_paths(const SimArgs& a, const float* __restr
 // table loads of every step.
 constexpr int kPair = 2;
 
-template <int M>
+template <int M, int SPACE>
 __global__ void __launch_bounds__(kPathThreads, 4) cdc_path_kernel(const SimArgs a, const float* __restrict__ tab) {
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x * kPair;
     for (int64_t g0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) * kPair; g0 < a.total;
@@ -496,13 +760,13 @@ __global__ void __launch_bounds__(kPathThreads, 4) cdc_path_kernel(const SimArgs
             same = same && s[p] == s[0];
         }
         if (same) {
-            cdc_paths<M, kPair>(a, tab + static_cast<int64_t>(s[0]) * a.n_steps * kTabFloats, s[0], q, g, write);
+            cdc_paths<M, kPair, SPACE>(a, tab + static_cast<int64_t>(s[0]) * a.n_steps * kTabFloats, s[0], q, g, write);
         } else {
 #pragma unroll
             for (int p = 0; p < kPair; ++p) {
                 const int64_t q1[1] = {q[p]}, g1[1] = {g[p]};
                 const bool w1[1] = {write[p]};
-                cdc_paths<M, 1>(a, tab + static_cast<int64_t>(s[p]) * a.n_steps * kTabFloats, s[p], q1, g1, w1);
+                cdc_paths<M, 1, SPACE>(a, tab + static_cast<int64_t>(s[p]) * a.n_steps * kTabFloats, s[p], q1, g1, w1);
             }
         }
     }
@@ -534,11 +798,11 @@ int blocks_per_sm(K k, int threads, size_t smem, int (&cache)[kMaxDevices], int*
     return SL_OK;
 }
 
-template <int MODEL, int ACT, int MACT>
+template <int MODEL, int ACT, int MACT, int SPACE>
 int launch_table_kernel(const CdcArgs& c, cudaStream_t st) {
     static int cache[kMaxDevices] = {};
-    auto k = cdc_table_kernel<MODEL, ACT, MACT>;
-    const size_t smem = table_smem_bytes(MODEL);
+    auto k = SPACE == SL_CDC_SPACE_Y ? cdc_table_kernel<MODEL, ACT, MACT> : cdcq_table_kernel<MODEL, ACT, MACT>;
+    const size_t smem = SPACE == SL_CDC_SPACE_Y ? table_smem_bytes(MODEL) : tableq_smem_bytes(MODEL);
     int per_sm = 1;
     int rc = blocks_per_sm(k, kTabThreads, smem, cache, &per_sm);
     if (rc) return rc;
@@ -551,16 +815,20 @@ int launch_table_kernel(const CdcArgs& c, cudaStream_t st) {
 }
 
 template <int MODEL, int ACT>
-int launch_tables(const CdcArgs& c, int mact, cudaStream_t st) {
+int launch_tables(const CdcArgs& c, int mact, int space, cudaStream_t st) {
     // the marginal network may use another activation than the conditional one
-    if (mact == SL_ACT_SOFTPLUS) return launch_table_kernel<MODEL, ACT, SL_ACT_SOFTPLUS>(c, st);
-    return launch_table_kernel<MODEL, ACT, SL_ACT_RELU>(c, st);
+    if (space == SL_CDC_SPACE_Y) {
+        if (mact == SL_ACT_SOFTPLUS) return launch_table_kernel<MODEL, ACT, SL_ACT_SOFTPLUS, SL_CDC_SPACE_Y>(c, st);
+        return launch_table_kernel<MODEL, ACT, SL_ACT_RELU, SL_CDC_SPACE_Y>(c, st);
+    }
+    if (mact == SL_ACT_SOFTPLUS) return launch_table_kernel<MODEL, ACT, SL_ACT_SOFTPLUS, SL_CDC_SPACE_QUANTILE>(c, st);
+    return launch_table_kernel<MODEL, ACT, SL_ACT_RELU, SL_CDC_SPACE_QUANTILE>(c, st);
 }
 
-template <int M>
+template <int M, int SPACE>
 int launch_paths_m(const SimArgs& a, const float* tab, cudaStream_t st) {
     static int cache[kMaxDevices] = {};
-    auto kern = cdc_path_kernel<M>;
+    auto kern = cdc_path_kernel<M, SPACE>;
     int per_sm = 1;
     int rc = blocks_per_sm(kern, kPathThreads, 0, cache, &per_sm);
     if (rc) return rc;
@@ -573,24 +841,31 @@ int launch_paths_m(const SimArgs& a, const float* tab, cudaStream_t st) {
     return cuda_error(cudaGetLastError(), "cdc_path launch");
 }
 
-int launch_paths(const SimArgs& a, const float* tab, cudaStream_t st) {
+template <int SPACE>
+int launch_paths_s(const SimArgs& a, const float* tab, cudaStream_t st) {
     switch (a.m) {
-        case 2: return launch_paths_m<2>(a, tab, st);
-        case 3: return launch_paths_m<3>(a, tab, st);
-        case 4: return launch_paths_m<4>(a, tab, st);
-        case 5: return launch_paths_m<5>(a, tab, st);
-        case 6: return launch_paths_m<6>(a, tab, st);
-        case 7: return launch_paths_m<7>(a, tab, st);
-        default: return launch_paths_m<8>(a, tab, st);
+        case 2: return launch_paths_m<2, SPACE>(a, tab, st);
+        case 3: return launch_paths_m<3, SPACE>(a, tab, st);
+        case 4: return launch_paths_m<4, SPACE>(a, tab, st);
+        case 5: return launch_paths_m<5, SPACE>(a, tab, st);
+        case 6: return launch_paths_m<6, SPACE>(a, tab, st);
+        case 7: return launch_paths_m<7, SPACE>(a, tab, st);
+        default: return launch_paths_m<8, SPACE>(a, tab, st);
     }
 }
 
+int launch_paths(const SimArgs& a, const float* tab, int space, cudaStream_t st) {
+    return space == SL_CDC_SPACE_Y ? launch_paths_s<SL_CDC_SPACE_Y>(a, tab, st)
+                                   : launch_paths_s<SL_CDC_SPACE_QUANTILE>(a, tab, st);
+}
+
 // bq[j][a]: the monomial coefficients of b_j Q_j(X) = b_j prod_{l!=j} (X - x_l) (FP64,
-// from the FP64 Gauss-Hermite points; zero for j or a >= m).
-int gh_monomials(int m, double (&bq)[SL_MAX_M][SL_MAX_M]) {
+// from the FP64 Gauss-Hermite points; zero for j or a >= m); xg: those points.
+int gh_monomials(int m, double (&bq)[SL_MAX_M][SL_MAX_M], double (&xg)[SL_MAX_M]) {
     double x[SL_MAX_M], w[SL_MAX_M], b[SL_MAX_M];
     const int rc = gauss_hermite_fp64(m, x, w, b);
     if (rc) return rc;
+    for (int j = 0; j < SL_MAX_M; ++j) xg[j] = j < m ? x[j] : 0.0;
     for (int j = 0; j < SL_MAX_M; ++j)
         for (int ai = 0; ai < SL_MAX_M; ++ai) bq[j][ai] = 0.0;
     for (int j = 0; j < m; ++j) {
@@ -626,7 +901,7 @@ size_t sl_cdc_workspace_size(int64_t total_paths, int n_sets, int n_steps) {
            align256(static_cast<size_t>(total_paths) * sizeof(float)) + set_moments_scratch_bytes(n_sets);
 }
 
-int seven_league_cdc_simulate_batched(int model, const sl_net* net, const sl_net* marg_net,
+int seven_league_cdc_simulate_batched(int model, const sl_net* net, const sl_net* marg_net, int space,
                                       const float* theta, int p, const float* Y0,
                                       const int64_t* path_offsets, int n_sets, int64_t total_paths,
                                       float T, int n_steps, int m, uint64_t seed, float* out_YT,
@@ -634,6 +909,7 @@ int seven_league_cdc_simulate_batched(int model, const sl_net* net, const sl_net
                                       size_t ws_bytes, void* stream) {
     int rc = check_common(model, net, theta, p, T, n_steps, m);
     if (rc) return rc;
+    if (space != SL_CDC_SPACE_Y && space != SL_CDC_SPACE_QUANTILE) return set_error(SL_ERR_ARG, "space=%d", space);
     if (model == SL_MODEL_MLP && marg_net) {
         rc = check_net(marg_net, m, p);
         if (rc) return rc;
@@ -682,7 +958,7 @@ int seven_league_cdc_simulate_batched(int model, const sl_net* net, const sl_net
     c.tab = tab;
     rc = make_gh_const(m, &c.gh);
     if (rc) return rc;
-    rc = gh_monomials(m, c.bq);
+    rc = gh_monomials(m, c.bq, c.xg);
     if (rc) return rc;
 
     SimArgs a{};
@@ -703,13 +979,13 @@ int seven_league_cdc_simulate_batched(int model, const sl_net* net, const sl_net
 
     rc = cuda_error(cudaMemsetAsync(status, 0, kStatusBytes, st), "status clear");
     if (rc) return rc;
-    if (model == SL_MODEL_GBM_EXACT) rc = launch_tables<SL_MODEL_GBM_EXACT, 0>(c, 0, st);
-    else if (model == SL_MODEL_OU_EXACT) rc = launch_tables<SL_MODEL_OU_EXACT, 0>(c, 0, st);
-    else if (c.act == SL_ACT_SOFTPLUS) rc = launch_tables<SL_MODEL_MLP, SL_ACT_SOFTPLUS>(c, c.mact, st);
-    else rc = launch_tables<SL_MODEL_MLP, SL_ACT_RELU>(c, c.mact, st);
+    if (model == SL_MODEL_GBM_EXACT) rc = launch_tables<SL_MODEL_GBM_EXACT, 0>(c, 0, space, st);
+    else if (model == SL_MODEL_OU_EXACT) rc = launch_tables<SL_MODEL_OU_EXACT, 0>(c, 0, space, st);
+    else if (c.act == SL_ACT_SOFTPLUS) rc = launch_tables<SL_MODEL_MLP, SL_ACT_SOFTPLUS>(c, c.mact, space, st);
+    else rc = launch_tables<SL_MODEL_MLP, SL_ACT_RELU>(c, c.mact, space, st);
     if (rc) return rc;
     if (total_paths > 0) {
-        rc = launch_paths(a, tab, st);
+        rc = launch_paths(a, tab, space, st);
         if (rc) return rc;
     }
     if (moments) return launch_set_moments(yt, path_offsets, n_sets, total_paths, out_mean, out_var, part, st);

@@ -157,19 +157,22 @@ def test_cdc_argument_checks(lib):
     L = lib
     fake = ctypes.c_void_p(0x1000)  # never dereferenced: every call below is rejected first
     net = sl.sl_net(0x1000, 3, 5, sl.ACT_RELU, sl.PREC_FP32)
-    base = dict(model=sl.MODEL_MLP, net=ctypes.byref(net), mnet=None, theta=fake, p=1, Y0=fake, off=fake,
+    base = dict(model=sl.MODEL_MLP, net=ctypes.byref(net), mnet=None, space=sl.CDC_QUANTILE, theta=fake, p=1,
+                Y0=fake, off=fake,
                 n_sets=1, total=10, T=1.0, n_steps=2, m=5, seed=1, yt=fake, grid=None, mean=None,
                 var=None, ws=fake, ws_bytes=256, stream=None)
 
     def call(**kw):
         a = dict(base, **kw)
         return L.seven_league_cdc_simulate_batched(
-            a["model"], a["net"], a["mnet"], a["theta"], a["p"], a["Y0"], a["off"], a["n_sets"], a["total"],
+            a["model"], a["net"], a["mnet"], a["space"], a["theta"], a["p"], a["Y0"], a["off"], a["n_sets"], a["total"],
             a["T"], a["n_steps"], a["m"], a["seed"], a["yt"], a["grid"], a["mean"], a["var"], a["ws"],
             a["ws_bytes"], a["stream"])
     need = sl.cdc_workspace_size(10, 1, 2)
     assert need >= 256 + 2 * 224 * 4
     assert call() == sl.SL_ERR_WORKSPACE                        # 256 bytes hold no tables
+    assert call(space=sl.CDC_Y) == sl.SL_ERR_WORKSPACE
+    assert call(space=2) == sl.SL_ERR_ARG
     assert call(m=9) == sl.SL_ERR_UNSUPPORTED
     assert call(n_steps=0) == sl.SL_ERR_UNSUPPORTED
     assert call(T=0.0) == sl.SL_ERR_ARG

@@ -52,8 +52,8 @@ def _run(sl, model, net, theta, Y0, offsets, T, n_steps, m, seed, marg=None, gri
     mean = torch.full((n_sets,), float("nan"), dtype=torch.float64, device="cuda") if moments else None
     var = torch.empty_like(mean) if moments else None
     ws = sl.seven_league_cdc_simulate_batched(model, net, _dev(theta), _dev(Y0), _dev(offsets, torch.int64), T,
-                                              n_steps, m, seed, marg_net=marg, out_YT=yt, out_grid=gr,
-                                              out_mean=mean, out_var=var)
+                                              n_steps, m, seed, marg_net=marg, space=sl.CDC_Y, out_YT=yt,
+                                              out_grid=gr, out_mean=mean, out_var=var)
     assert sl.workspace_status(ws) == 0
     tab = sl.cdc_tables(ws, n_sets, n_steps).cpu().numpy()
     out = dict(yt=yt.cpu().numpy()[:total], tab=tab)
@@ -301,8 +301,8 @@ def test_batch_independence_graph_and_grid(sl, orc):
     yt = torch.empty(total, device="cuda")
     mean = torch.empty(300, dtype=torch.float64, device="cuda")
     ws = torch.empty(sl.cdc_workspace_size(total, 300, 12), dtype=torch.uint8, device="cuda")
-    run = lambda: sl.seven_league_cdc_simulate_batched(0, net, th, y0, o, 4.0, 12, 7, 9, out_YT=yt, out_mean=mean,
-                                                       ws=ws, total_paths=total)
+    run = lambda: sl.seven_league_cdc_simulate_batched(0, net, th, y0, o, 4.0, 12, 7, 9, space=sl.CDC_Y, out_YT=yt,
+                                                       out_mean=mean, ws=ws, total_paths=total)
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
@@ -347,7 +347,7 @@ def test_more_than_2_31_paths(sl, orc):
     yt = torch.empty(n, dtype=torch.float32, device="cuda")
     mean = torch.empty(1, dtype=torch.float64, device="cuda")
     ws = sl.seven_league_cdc_simulate_batched(1, None, _dev(th), _dev([1.0]), _dev(off, torch.int64), 1.0, 2, 7, 2,
-                                              out_YT=yt, out_mean=mean)
+                                              space=sl.CDC_Y, out_YT=yt, out_mean=mean)
     assert sl.workspace_status(ws) == 0
     idx = np.concatenate([np.arange(0, 64), np.arange((1 << 31) - 64, (1 << 31) + 64), np.arange(n - 64, n)])
     got = yt[torch.as_tensor(idx, device="cuda")].cpu().numpy()

@@ -10,7 +10,8 @@ collocation points and a trained network) against the exact solution Eq. (6.6).
   is sigma^2 dt instead of sigma^2 (1 - e^{-2 lambda T}) / (2 lambda)); the 7L scheme's does not.
 * Both network forms (FP32 CUDA cores, BF16 tensor cores) meet the same bounds.
 * The 7L-CDC variant (the other column of Table 6.1), with one network trained over the
-  horizons 0.125 .. 2 serving as the marginal and the conditional map: small pathwise error
+  horizons 0.125 .. 2 serving as the marginal and the conditional map, in both interpolation
+  spaces (Y, and the marginal's quantile coordinate): small pathwise error
   against the exact solution on the same normals, within 1.25x (+1e-3) of the 7L scheme's with
   the same network at every step size, and the same variance to 2% of the exact variance.
 """
@@ -102,7 +103,8 @@ def ou_net_horizons(sl):
     return P
 
 
-def test_cdc_pathwise_error(sl, orc, ou_net_horizons):
+@pytest.mark.parametrize("space", [0, 1])
+def test_cdc_pathwise_error(sl, orc, ou_net_horizons, space):
     """The 7L-CDC scheme keeps the accuracy of the 7L scheme with the same network: the network's
     error dominates, the global interpolation in Y adds little (the exact OU map is affine in Y)."""
     n, seed = 20000, 13
@@ -115,12 +117,13 @@ def test_cdc_pathwise_error(sl, orc, ou_net_horizons):
         ref = _run(sl, sl.MODEL_OU_EXACT, None, n, n_steps, seed)
         y7 = _run(sl, sl.MODEL_MLP, net, n, n_steps, seed)
         yt = torch.empty(n, device="cuda")
-        ws = sl.seven_league_cdc_simulate_batched(sl.MODEL_MLP, net, th, y0, off, T, n_steps, M, seed, out_YT=yt)
+        ws = sl.seven_league_cdc_simulate_batched(sl.MODEL_MLP, net, th, y0, off, T, n_steps, M, seed, space=space,
+                                                  out_YT=yt)
         assert sl.workspace_status(ws) == 0
         y = yt.cpu().numpy().astype(np.float64)
         err[n_steps], err7[n_steps] = np.abs(y - ref).mean(), np.abs(y7 - ref).mean()
         dvar[n_steps] = abs(y.var() - y7.var()) / exact_var
-    print("pathwise mean |Y - exact|, 7L-CDC:", err, "7L:", err7, "|Var CDC - Var 7L| / exact:", dvar)
+    print("space", space, "pathwise mean |Y - exact|, 7L-CDC:", err, "7L:", err7, "|Var CDC - Var 7L| / exact:", dvar)
     for k in (16, 4, 2):
         assert err[k] < 0.02 * Y0, k
         assert err[k] <= 1.25 * err7[k] + 1e-3, k

@@ -7,7 +7,8 @@ conditional points are moved into the next step's coordinate by G_{i+1}^{-1}).
   range); a constant G inverts to 0 and a G that does not increase from its first to its last
   point to NaN.
 * The bivariate interpolant reproduces every tensor-product polynomial of degree <= m-1 in each
-  variable (numpy polyval), at and away from the nodes.
+  variable (numpy polyval), at and away from the nodes, for xi inside [x_0, x_{m-1}]; beyond, it
+  is the line in xi through the two outermost node rows.
 * The exact OU map makes G linear and the conditional points affine, so the chain equals the
   (separately pinned) 7L chain path by path; sigma = 0 gives the deterministic growth
   Y0 e^{mu T}; the exact GBM chain stays within the interpolation error of the lognormal
@@ -46,8 +47,26 @@ def test_bivariate_interpolation_reproduces_polynomials(orc, m):
     c = rng.normal(size=(m, m))                      # p(xi, X) = sum_ab c[a, b] xi^a X^b
     p = lambda u, v: sum(c[a, b] * u ** a * v ** b for a in range(m) for b in range(m))
     eta = np.array([[p(x[k], x[j]) for j in range(m)] for k in range(m)])
-    for u, v in [(x[0], x[-1]), (0.3, -1.7), (2.2, 0.9), (-4.1, 3.3)]:
+    for u, v in [(x[0], x[-1]), (0.3 * x[-1], -1.7), (0.8 * x[0], 0.9), (x[-1], 3.3), (0.1, -4.4)]:
         assert orc.cdcq_F(eta, u, v) == pytest.approx(p(u, v), rel=1e-9, abs=1e-9)
+
+
+@pytest.mark.parametrize("m", [2, 5, 7])
+def test_continuation_beyond_the_hull_in_xi(orc, m):
+    """Beyond [x_0, x_{m-1}] the interpolant follows the line in xi through the two outermost
+    node rows: continuous at the edge, zero second differences, the outer rows' slope."""
+    x = hermite_e.hermegauss(m)[0]
+    rng = np.random.default_rng(20 + m)
+    eta = rng.normal(size=(m, m))
+    for X in (-1.3, 0.4, 2.9):
+        for edge, inner, side in ((x[0], x[1], -1.0), (x[-1], x[-2], 1.0)):
+            us = edge + side * np.array([1e-9, 0.5, 1.0, 1.5])
+            v = np.array([orc.cdcq_F(eta, u, X) for u in us])
+            at = orc.cdcq_F(eta, edge, X)
+            assert v[0] == pytest.approx(at, abs=1e-7)
+            assert v[1] - 2 * v[2] + v[3] == pytest.approx(0.0, abs=1e-9)
+            slope = (at - orc.cdcq_F(eta, inner, X)) / (edge - inner)
+            assert (v[3] - at) / (us[3] - edge) == pytest.approx(slope, rel=1e-9)
 
 
 @pytest.mark.parametrize("m", [2, 5, 7])
