@@ -34,10 +34,9 @@ METRIC = "path-steps/s (7L online, BF16-TC vs FP32) at <=2e-3 rel err; EM label 
 UNIT = "path-steps/s"
 WORKLOAD = "GBM 7L online: 16 theta x 1e6 paths x 16 coarse steps, m=7, MLP 4->50x4->7 ReLU"
 ALG_FLOPS_PER_PATH_STEP = 2 * (4 * 50 + 3 * 50 * 50 + 50 * 7)   # 16,100 (biases excluded)
-# 7L-CDC, m = 7, per path-step inside the marginal hull: the products-except-one P_k(Y) of m
-# differences (m subtractions, 3m - 2 multiplications), m Horner evaluations of degree m - 1 in X
-# and the final dot over k (FMA = 2 flops); the normal draw is not counted
-CDC_FLOPS_PER_PATH_STEP = (7 + 3 * 7 - 2) + 2 * 7 * 6 + 2 * 7          # 124
+# 7L-CDC in the marginal's quantile coordinate, m = 7, per path-step inside the hull: m Horner
+# evaluations of degree m - 1 in X and one in xi (FMA = 2 flops); the normal draw is not counted
+CDC_FLOPS_PER_PATH_STEP = 2 * 7 * 6 + 2 * 6                            # 96
 
 # DRAM traffic of the sampler kernel on the default workload, from the committed ncu summary;
 # used only while the kernel's sources are those the counters were taken on.
