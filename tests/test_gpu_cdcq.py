@@ -15,7 +15,8 @@ Horner evaluations against FP64 on the same normals: a few 1e-7 per step over up
   G's coefficients and edges, eta against the oracle's, B from the kernel's own eta -- and the
   paths; a network whose marginal points decrease gives NaN paths (SL_DEV_NONFINITE).
 * Degenerate laws (sigma = 0), ragged and empty sets, one step, batch independence
-  (bit-exact), CUDA graph replay, FP64 set moments, the 16 x 1e6 x 16 workload on sampled paths.
+  (bit-exact), CUDA graph replay, FP64 set moments, the 16 x 1e6 x 16 workload on sampled paths,
+  m = 2..8, 2^31 + 129 paths in one set, 2^20 sets.
 """
 import math
 
@@ -231,3 +232,44 @@ def test_full_size_sampled(sl, orc):
     for s in range(16):
         seg = r["yt"][off[s]:off[s + 1]].astype(np.float64)
         assert r["mean"][s] == pytest.approx(seg.mean(), rel=1e-12)
+
+
+@pytest.mark.parametrize("m", [2, 3, 4, 5, 6, 7, 8])
+def test_every_m(sl, orc, m):
+    th, y0 = [[0.1, 0.3], [0.05, 0.45]], [1.0, 2.0]
+    off = W.offsets_from_counts([700, 1300])
+    r = _run(sl, 1, None, th, y0, off, 1.0, 6, m, 5)
+    _check(orc, r["yt"], orc.cdcq_paths(1, None, th, y0, off, 1.0, 6, m, 5), off, 5, 6, 1.0)
+
+
+def test_more_than_2_31_paths(sl, orc):
+    """One set of 2^31 + 129 paths, 2 steps, exact OU map: sampled paths including the last ones."""
+    n = (1 << 31) + 129
+    off = W.offsets_from_counts([n])
+    th = [[0.5, 0.3, 1.0]]
+    yt = torch.empty(n, dtype=torch.float32, device="cuda")
+    mean = torch.empty(1, dtype=torch.float64, device="cuda")
+    ws = sl.seven_league_cdc_simulate_batched(2, None, _dev(th), _dev([1.5]), _dev(off, torch.int64), 1.0, 2, 7, 2,
+                                              out_YT=yt, out_mean=mean)
+    assert sl.workspace_status(ws) == 0
+    idx = np.concatenate([np.arange(0, 64), np.arange((1 << 31) - 64, (1 << 31) + 64), np.arange(n - 64, n)])
+    got = yt[torch.as_tensor(idx, device="cuda")].cpu().numpy()
+    _check(orc, got, orc.cdcq_paths(2, None, th, [1.5], off, 1.0, 2, 7, 2, idx=idx), off, 2, 2, 1.0, idx=idx)
+    assert np.isfinite(mean.item())
+    del yt
+
+
+def test_many_sets(sl, orc):
+    """2^20 parameter sets with 0 or 1 path each, 3 steps, a network."""
+    n_sets = 1 << 20
+    rng = np.random.default_rng(41)
+    counts = rng.integers(0, 2, n_sets)
+    off = W.offsets_from_counts(counts)
+    th = rng.uniform([0.0, 0.1], [0.2, 0.5], (n_sets, 2)).astype(np.float32)
+    y0 = rng.uniform(0.8, 1.2, n_sets).astype(np.float32)
+    P = W.near_affine_params(4, 7, seed=42)
+    r = _run(sl, 0, sl.make_net(_dev(P), 4, 7), th, y0, off, 1.0, 3, 7, 4, moments=True)
+    sets = np.concatenate([np.nonzero(counts)[0][:40], np.nonzero(counts)[0][-40:]])
+    idx = off[sets]
+    _check(orc, r["yt"][idx], orc.cdcq_paths(0, P, th, y0, off, 1.0, 3, 7, 4, d_in=4, idx=idx), off, 4, 3, 1.0, idx=idx)
+    assert np.array_equal(r["mean"][sets], r["yt"][idx].astype(np.float64)) and np.all(r["mean"][counts == 0] == 0)
