@@ -529,7 +529,28 @@ def main():
         secondary["cir_batched_path_steps_per_s"] = tot_c * cb["n_steps"] / (c_ms * 1e-3)
         secondary["cir_batched_workload"] = ("CIR 4096 theta sets, %d paths (log-uniform 1e3..1e5 per set), "
                                              "32 steps, m=7, one persistent launch in a CUDA graph" % tot_c)
-        del yt_c, ws_c
+        del ws_c
+        # the same batch through the 7L-CDC scheme (quantile coordinate; 4096 x 32 table entries):
+        # timing only, with workloads.near_affine_params (the CIR network is trained for steps of
+        # 0.1..1, not for the horizons up to T = 8 the marginal points need)
+        P_cc = torch.as_tensor(W.near_affine_params(5, 7, seed=0), device=dev)
+        net_cc = sl.make_net(P_cc, 5, 7)
+        ws_cc = torch.empty(sl.cdc_workspace_size(tot_c, 4096, cb["n_steps"]), dtype=torch.uint8, device=dev)
+        run_cc = lambda: sl.seven_league_cdc_simulate_batched(sl.MODEL_MLP, net_cc, th_c, y0_c, off_c, cb["T"],
+                                                              cb["n_steps"], 7, cb["seed"], out_YT=yt_c,
+                                                              out_mean=mean_c, ws=ws_cc, total_paths=tot_c)
+        run_cc()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(3):
+            run_cc()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if sl.workspace_status(ws_cc) == 0:
+            secondary["cdc_cir_batched_path_steps_per_s"] = tot_c * cb["n_steps"] / (e0.elapsed_time(e1) / 3 * 1e-3)
+        else:
+            secondary["cdc_cir_batched_error"] = "device status %d" % sl.workspace_status(ws_cc)
+        del yt_c, ws_cc
         # adjoint: GBM network, 1e6 paths, 64 steps, checkpoint every 8 steps, K = 1, in both
         # network forms (FP32 CUDA cores; BF16 tcgen05)
         n_a = 10 ** 6

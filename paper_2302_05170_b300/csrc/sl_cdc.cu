@@ -372,7 +372,7 @@ size_t tableq_smem_bytes(int model) {
     return (model == SL_MODEL_MLP ? 2 * sizeof(SmemNet) : 0) +
            (static_cast<size_t>(kGroups) * 2 * kBufStride + kBatch * 8 + kBatch * 8 + kBatch * 64 + kBatch * 8) *
                sizeof(float) +
-           static_cast<size_t>(kBatch) * (8 + 64) * sizeof(double) + static_cast<size_t>(kBatch) * sizeof(int);
+           static_cast<size_t>(kBatch) * (8 + 64 + 64) * sizeof(double) + static_cast<size_t>(kBatch) * sizeof(int);
 }
 
 // G_{i+1}^{-1}(y) (flag 1: the nodes coincide, 0; flag 2: G does not increase from its
@@ -380,8 +380,10 @@ size_t tableq_smem_bytes(int model) {
 // outermost nodes; inside, the first root in the first node interval [x_k, x_{k+1}] with
 // zn_k <= y <= zn_{k+1}: the interval is scanned at 32 equal steps for the first point
 // where G >= y (FP32), the root in that cell is refined by Newton in FP32 (bisecting
-// whenever a step leaves the cell that brackets it, 8 steps), then by two Newton steps in
-// FP64 on the FP64 coefficients, clamped to the cell (the root may be one of its ends).
+// whenever a step leaves the cell that brackets it, 8 steps), then by one Newton step on
+// the FP64 coefficients (the residual in FP64, the derivative's reciprocal in FP32: the
+// step is ~1e-7 of the root, so its own 1e-7 error is below FP64 rounding), clamped to the
+// cell (the root may be one of its ends).
 __device__ double quantile_inverse(const float* zn, const float* g32, const double* g64, const double* xg, int m,
                                    int flag, double y) {
     if (flag == 1) return 0.0;
@@ -416,16 +418,14 @@ __device__ double quantile_inverse(const float* zn, const float* g32, const doub
         xi = nx;
     }
     double x = xi;
-    for (int it = 0; it < 2; ++it) {
-        double gv = g64[m - 1], gd = 0.0;
-        for (int ai = m - 2; ai >= 0; --ai) {
-            gd = fma(gd, x, gv);
-            gv = fma(gv, x, g64[ai]);
-        }
-        const double nx = (gd != 0.0) ? x - (gv - y) / gd : x;
-        x = fmin(fmax(nx, dlo), dhi);      // the root lies in the cell (it may be an end)
+    double gv = g64[m - 1];
+    float gd = 0.0f;
+    for (int ai = m - 2; ai >= 0; --ai) {
+        gd = fmaf(gd, static_cast<float>(x), static_cast<float>(gv));
+        gv = fma(gv, x, g64[ai]);
     }
-    return x;
+    const double nx = (gd != 0.0f) ? x - (gv - y) * static_cast<double>(__frcp_rn(gd)) : x;
+    return fmin(fmax(nx, dlo), dhi);      // the root lies in the cell (it may be an end)
 }
 
 template <int MODEL, int ACT, int MACT>
@@ -440,7 +440,8 @@ __global__ void __launch_bounds__(kTabThreads, 2) cdcq_table_kernel(const CdcArg
     float* ths = Cs + kBatch * 64;                 // [kBatch][8]: Y0 of the entry's set, then theta
     double* g64 = reinterpret_cast<double*>(ths + kBatch * 8);   // [kBatch][8] coefficients of G_{i+1}
     double* e64 = g64 + kBatch * 8;                // [kBatch][8][8] eta
-    int* flag = reinterpret_cast<int*>(e64 + kBatch * 64);       // [kBatch]
+    double* r64 = e64 + kBatch * 64;               // [kBatch][8][8] node rows: sum_j eta[k][j] bq[j][b]
+    int* flag = reinterpret_cast<int*>(r64 + kBatch * 64);       // [kBatch]
     const bool one_net = a.mparams == a.params;
     if (MODEL == SL_MODEL_MLP) {
         stage_net(cnet, a.params, a.d_in, a.m);
@@ -537,24 +538,30 @@ __global__ void __launch_bounds__(kTabThreads, 2) cdcq_table_kernel(const CdcArg
             }
         }
         __syncthreads();
-        // (C3) thread (e, a, b): B[a][b] = sum_k bq[k][a] sum_j eta[k][j] bq[j][b]
+        // (C3) thread (e, k, b): the node row R_k[b] = sum_j eta[k][j] bq[j][b] (the monomial
+        // coefficients in X of sum_j eta[k][j] L_j(X))
+        {
+            const int e = threadIdx.x / 64, k = (threadIdx.x / 8) % 8, b = threadIdx.x % 8;
+            const int64_t u = base + e;
+            if (u < n) {
+                double row = 0.0;
+                for (int j = 0; j < m; ++j) row = fma(e64[e * 64 + k * 8 + j], a.bq[j][b], row);
+                r64[e * 64 + k * 8 + b] = row;
+            }
+        }
+        __syncthreads();
+        // (C4) thread (e, a, b): B[a][b] = sum_k bq[k][a] R_k[b]; and the outer node rows
         {
             const int e = threadIdx.x / 64, ai = (threadIdx.x / 8) % 8, b = threadIdx.x % 8;
             const int64_t u = base + e;
             if (u < n) {
                 double acc = 0.0;
-                for (int k = 0; k < m; ++k) {
-                    double row = 0.0;
-                    for (int j = 0; j < m; ++j) row += e64[e * 64 + k * 8 + j] * a.bq[j][b];
-                    acc += a.bq[k][ai] * row;
-                }
+                for (int k = 0; k < m; ++k) acc = fma(a.bq[k][ai], r64[e * 64 + k * 8 + b], acc);
                 float* t = a.tab + u * kTabFloats;
                 t[kQB + ai * 8 + b] = static_cast<float>(acc);
-                if (ai < 4) {                          // node row r of R_0, R_1, R_{m-2}, R_{m-1}
+                if (ai < 4) {                          // R_0, R_1, R_{m-2}, R_{m-1}
                     const int kr = ai < 2 ? ai : m - 4 + ai;
-                    double row = 0.0;
-                    for (int j = 0; j < m; ++j) row += e64[e * 64 + kr * 8 + j] * a.bq[j][b];
-                    t[kQR + ai * 8 + b] = static_cast<float>(row);
+                    t[kQR + ai * 8 + b] = static_cast<float>(r64[e * 64 + kr * 8 + b]);
                 } else if (ai == 4 && b == 0) {
                     for (int z = kQR + 32; z < kTabFloats; ++z) t[z] = 0.0f;
                 }
