@@ -142,9 +142,11 @@ int make_gh_const(int m, GHConst* out) {
     const int rc = gauss_hermite_fp64(m, x, nullptr, b);
     if (rc) return rc;
     memset(out, 0, sizeof(*out));
-    for (int j = 0; j < m; ++j) {
-        out->x[j] = static_cast<float>(x[j]);
-        out->bary[j] = static_cast<float>(b[j]);
+    for (int j = 0; j < SL_MAX_M; ++j) {
+        out->x[j] = (j < m) ? static_cast<float>(x[j]) : 0.0f;
+        out->bary[j] = (j < m) ? static_cast<float>(b[j]) : 0.0f;
+        out->dsc[j] = (j < m) ? 1.0f : 0.0f;
+        out->doff[j] = (j < m) ? -out->x[j] : 1.0f;
     }
     return SL_OK;
 }

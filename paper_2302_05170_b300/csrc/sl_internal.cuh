@@ -27,6 +27,8 @@ int gauss_hermite_fp64(int m, double* x, double* w, double* bary);
 struct GHConst {
     float x[SL_MAX_M];
     float bary[SL_MAX_M];
+    float dsc[SL_MAX_M];    // X - x_j as fmaf(X, dsc_j, doff_j): (1, -x_j) for j < m,
+    float doff[SL_MAX_M];   // (0, 1) for the unused nodes j >= m (a factor 1 in every product)
 };
 int make_gh_const(int m, GHConst* out);
 
@@ -97,9 +99,10 @@ __device__ __forceinline__ float lagrange_eval_m(const float (&y)[SL_MAX_M], flo
 // The Lagrange basis ell_j(X) for a runtime m <= SL_MAX_M (ell_j = 0 for j >= m),
 // so that g_m(X) = sum_j y_j ell_j can be finished with m FMAs once y is known.
 __device__ __forceinline__ void lagrange_basis_m(float X, const GHConst& gh, int m, float (&l)[SL_MAX_M]) {
+    (void)m;   // the unused nodes are folded into gh.dsc / gh.doff
     float d[SL_MAX_M], pre[SL_MAX_M];
 #pragma unroll
-    for (int j = 0; j < SL_MAX_M; ++j) d[j] = (j < m) ? X - gh.x[j] : 1.0f;
+    for (int j = 0; j < SL_MAX_M; ++j) d[j] = fmaf(X, gh.dsc[j], gh.doff[j]);
     pre[0] = 1.0f;
 #pragma unroll
     for (int j = 1; j < SL_MAX_M; ++j) pre[j] = pre[j - 1] * d[j - 1];

@@ -3,7 +3,7 @@
 //
 // The network of Eq. (6.4) is a chain of five GEMMs per coarse step:
 //   layer 1:   [128 paths x K=16]  x [K x N=64]      (features, hi+lo split)
-//   layers 2-4 [128 paths x K=112] x [K x N=64]      (50 activations hi, 1, lo)
+//   layers 2-4 [128 paths x K=112] x [K x N=64]      (50 activations hi + lo, 1)
 //   layer 5:   [128 paths x K=112] x [K x N=16]      (m <= 8 outputs used)
 // A persistent CTA (one per SM) holds S independent path tiles ("slots") of
 // 128 paths.  Warpgroup t (warps 4t..4t+3, TMEM lanes 32*(warp%4)..) owns
@@ -15,15 +15,17 @@
 // Softplus), splits every activation h into BF16 hi + lo (hi = h truncated to
 // BF16, lo = BF16(h - hi)), and writes the next A tile.  Several slots keep
 // independent MMA groups in the tensor pipe at once; the Philox normals and the
-// Lagrange basis of a step are computed while the step's first MMA runs.
+// Lagrange basis of a step are computed while the step's output-layer MMAs run.
 //
 // Numerics: weights and biases are rounded to BF16 (nearest, ties to even);
 // the network's inputs and activations carry ~16 significant bits through the
 // hi+lo split (a single BF16 rounding of every activation gives ~1e-2 per-path
 // error over 16 steps, the split ~1e-5); accumulation is FP32; the state,
-// normals and interpolation are FP32.  Biases ride on a constant-1 input column
-// (column 50 of the hidden inputs, column 2*d_in of the features), so the
-// epilogue adds nothing.
+// normals and interpolation are FP32.  Biases ride on a constant-1 input (K index
+// 98 of the hidden inputs, 2*d_in of the features), so the epilogue adds nothing.
+// The hidden A row keeps each 16-neuron chunk's hi and lo words in 16 adjacent
+// columns (one store per chunk); the features sit in the slot's last 8 columns,
+// written once per tile except Y's word.
 //
 // Synchronisation: the four warps of a slot meet at a named barrier (an AND
 // reduction, so a failed wait stops all four together) once the next A operand
@@ -100,6 +102,7 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_7l_kernel(const SimArgs a) {
         T[j].d_bar = smem_u32(&bars[slot]);
         T[j].bar_id = 1 + slot;
         T[j].dph = 0;
+        tile_init_row(T[j]);
     }
 
     const int64_t n_tiles = (a.total + kTile - 1) / kTile;
@@ -111,10 +114,9 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_7l_kernel(const SimArgs a) {
         for (int j = 0; j < TPW; ++j) {   // a tile past the end computes garbage rows and stores nothing
             tile_begin(T[j], a, base + j, r);
             if (base + j >= n_tiles) T[j].valid = false;
-            if (ok) tile_features(T[j], a);
+            if (ok) tile_features_init(T[j], a);
             ok = tile_sync_issue(T[j], C, 0, ok, issuer);
             if (!ok) break;
-            tile_rng(T[j], a, 0);
         }
         if (!ok) break;
         for (int i = 0; i < a.n_steps; ++i) {
@@ -126,6 +128,8 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_7l_kernel(const SimArgs a) {
                     if (w) tile_hidden_act<ACT>(T[j]);
                     ok = tile_sync_issue(T[j], C, l, w, issuer);
                     if (!ok) break;
+                    // the step's normal and Lagrange basis while the output layer's MMAs run
+                    if (l == 4) tile_rng(T[j], a, i);
                 }
                 if (!ok) break;
             }
@@ -137,7 +141,6 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_7l_kernel(const SimArgs a) {
                 if (i + 1 < a.n_steps) {
                     if (w) tile_features(T[j], a);
                     w = tile_sync_issue(T[j], C, 0, w, issuer);
-                    if (w) tile_rng(T[j], a, i + 1);
                 }
                 ok = ok && w;
             }

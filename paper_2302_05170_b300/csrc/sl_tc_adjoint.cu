@@ -61,8 +61,9 @@ struct AdjTC {
 
 // Transposed weights for the backward chain (BF16, 128B-swizzled, K-major):
 //   B5T[n][j] = B5T[n][8 + j] = W5[j][n]              (n < 50, j < m)
-//   BlT[n][k] = BlT[n][56 + k] = W_l[k][n]            (l = 4, 3, 2; n, k < 50)
-//   B1T[n][k] = B1T[n][56 + k] = W1[k][n]             (n < d_in, k < 50)
+//   BlT[n][k] = W_l[j][n]   (l = 4, 3, 2; n < 50)     k: the hi or lo part of neuron j
+//   B1T[n][k] = W1[j][n]    (n < d_in)                (the hidden A row's K order; 0 at
+//                                                      the bias unit and the padding)
 __device__ void stage_weights_T(unsigned char* sBT, const float* __restrict__ P, int d_in, int m) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int W = SL_WIDTH;
@@ -85,20 +86,18 @@ __device__ void stage_weights_T(unsigned char* sBT, const float* __restrict__ P,
         unsigned char* d = sBT + kB5TBytes + q * kBHTBytes;
         for (int i = tid; i < W * 112; i += nt) {
             const int n = i / 112, k = i % 112;
-            int kk;
-            if (k < W) kk = k;
-            else if (k >= kLoCol && k < kLoCol + W) kk = k - kLoCol;
-            else continue;
+            int kk = 0;
+            const int role = hid_k_role(k, kk);
+            if (role != kKHi && role != kKLo) continue;
             *reinterpret_cast<__nv_bfloat16*>(d + b_elem_off(64, n, k)) = __float2bfloat16_rn(P[offs[q] + kk * W + n]);
         }
     }
     unsigned char* d1 = sBT + kB5TBytes + 3 * kBHTBytes;
     for (int i = tid; i < d_in * 112; i += nt) {
         const int n = i / 112, k = i % 112;
-        int kk;
-        if (k < W) kk = k;
-        else if (k >= kLoCol && k < kLoCol + W) kk = k - kLoCol;
-        else continue;
+        int kk = 0;
+        const int role = hid_k_role(k, kk);
+        if (role != kKHi && role != kKLo) continue;
         *reinterpret_cast<__nv_bfloat16*>(d1 + b_elem_off(16, n, k)) = __float2bfloat16_rn(P[o1 + kk * d_in + n]);
     }
 }
@@ -133,76 +132,26 @@ constexpr int kMaskWordsPerTile = kMaskSteps * 4 * 2 * kTile;
 // next A row) plus the layer's ReLU pattern as bits -- bit j of word 0 for neuron j < 32,
 // bit j of word 1 for neuron 32 + j -- stored to mrow[0] and mrow[kTile].
 __device__ __forceinline__ void tile_hidden_rec(const Tile& T, uint32_t* mrow) {
-    tc_fence_after();
-    uint32_t v[32], v2[16], u[8];
-    tmem_ld32(T.taddr, v);
-    tmem_ld16(T.taddr + 32, v2);
-    tmem_ld8(T.taddr + 48, u);
-    tmem_wait_ld();
     uint32_t m0 = 0u, m1 = 0u;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) m0 |= (static_cast<int32_t>(v[j]) > 0) ? (1u << j) : 0u;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) m1 |= (static_cast<int32_t>(v2[j]) > 0) ? (1u << j) : 0u;
-    m1 |= (static_cast<int32_t>(u[0]) > 0) ? (1u << 16) : 0u;
-    m1 |= (static_cast<int32_t>(u[1]) > 0) ? (1u << 17) : 0u;
+    tile_epilogue(T, [&](int n, uint32_t x0, uint32_t x1, uint32_t& hw, uint32_t& lw) {
+        const uint32_t bits = ((static_cast<int32_t>(x0) > 0) ? 1u : 0u) | ((static_cast<int32_t>(x1) > 0) ? 2u : 0u);
+        if (n < 32) m0 |= bits << n;
+        else m1 |= bits << (n - 32);
+        split_relu(x0, x1, hw, lw);
+    });
     mrow[0] = m0;
     mrow[kTile] = m1;
-    const uint32_t at = T.taddr + 64;
-    uint32_t hw[16], lw[16];
-#pragma unroll
-    for (int i2 = 0; i2 < 16; ++i2) split_relu(v[2 * i2], v[2 * i2 + 1], hw[i2], lw[i2]);
-    tmem_st16(at, hw);
-    uint32_t h9[9], l9[9];
-#pragma unroll
-    for (int i2 = 0; i2 < 9; ++i2)
-        split_relu((i2 < 8) ? v2[2 * i2] : u[0], (i2 < 8) ? v2[2 * i2 + 1] : u[1], h9[i2], l9[i2]);
-    const uint32_t gb[16] = {h9[0], h9[1], h9[2], h9[3], h9[4], h9[5], h9[6], h9[7],
-                             h9[8], 0x00003F80u, 0u, 0u, lw[0], lw[1], lw[2], lw[3]};
-    const uint32_t gc[16] = {lw[4], lw[5], lw[6], lw[7], lw[8], lw[9], lw[10], lw[11],
-                             lw[12], lw[13], lw[14], lw[15], l9[0], l9[1], l9[2], l9[3]};
-    const uint32_t gd[8] = {l9[4], l9[5], l9[6], l9[7], l9[8], 0u, 0u, 0u};
-    tmem_st16(at + 16, gb);
-    tmem_st16(at + 32, gc);
-    tmem_st8(at + 48, gd);
-    tmem_wait_st();
-    tc_fence_before();
 }
 
 // Backward epilogue: dh (accumulator columns 0..49) masked by the recorded ReLU pattern
 // (m0: neurons 0..31, m1: neurons 32..49), split into BF16 hi + lo (no ReLU: cotangents
-// have either sign) and written as the next A row (hi 0..24, 25..27 = 0, lo 28..52).
+// have either sign) and written as the next A row (the hidden A row's layout; the bias
+// unit meets a zero row of the transposed weights).
 __device__ __forceinline__ void tile_backward_bits(const Tile& T, uint32_t m0, uint32_t m1) {
-    tc_fence_after();
-    uint32_t v[32], v2[16], u[8];
-    tmem_ld32(T.taddr, v);
-    tmem_ld16(T.taddr + 32, v2);
-    tmem_ld8(T.taddr + 48, u);
-    tmem_wait_ld();
-    const uint32_t at = T.taddr + 64;
-    uint32_t hw[16], lw[16];
-#pragma unroll
-    for (int i2 = 0; i2 < 16; ++i2)
-        split_rn((m0 >> (2 * i2)) & 1u ? v[2 * i2] : 0u, (m0 >> (2 * i2 + 1)) & 1u ? v[2 * i2 + 1] : 0u, hw[i2],
-                 lw[i2]);
-    tmem_st16(at, hw);
-    uint32_t h9[9], l9[9];
-#pragma unroll
-    for (int i2 = 0; i2 < 9; ++i2) {
-        const uint32_t ra = (i2 < 8) ? v2[2 * i2] : u[0];
-        const uint32_t rb = (i2 < 8) ? v2[2 * i2 + 1] : u[1];
-        split_rn((m1 >> (2 * i2)) & 1u ? ra : 0u, (m1 >> (2 * i2 + 1)) & 1u ? rb : 0u, h9[i2], l9[i2]);
-    }
-    const uint32_t gb[16] = {h9[0], h9[1], h9[2], h9[3], h9[4], h9[5], h9[6], h9[7],
-                             h9[8], 0u, 0u, 0u, lw[0], lw[1], lw[2], lw[3]};
-    const uint32_t gc[16] = {lw[4], lw[5], lw[6], lw[7], lw[8], lw[9], lw[10], lw[11],
-                             lw[12], lw[13], lw[14], lw[15], l9[0], l9[1], l9[2], l9[3]};
-    const uint32_t gd[8] = {l9[4], l9[5], l9[6], l9[7], l9[8], 0u, 0u, 0u};
-    tmem_st16(at + 16, gb);
-    tmem_st16(at + 32, gc);
-    tmem_st8(at + 48, gd);
-    tmem_wait_st();
-    tc_fence_before();
+    tile_epilogue(T, [&](int n, uint32_t x0, uint32_t x1, uint32_t& hw, uint32_t& lw) {
+        const uint32_t mb = (n < 32) ? (m0 >> n) : (m1 >> (n - 32));
+        split_rn((mb & 1u) ? x0 : 0u, (mb & 2u) ? x1 : 0u, hw, lw);
+    });
 }
 
 // The accumulator row's columns 0..49 as FP32 values (the cotangent dh of a layer).
@@ -227,37 +176,12 @@ __device__ __forceinline__ void tile_acc50(const Tile& T, float (&d)[SL_WIDTH]) 
 // overflows), split into BF16 hi + lo and written as the next A row (layout of
 // tile_backward_bits).
 __device__ __forceinline__ void tile_backward_sp(const Tile& T, const float (&dh)[SL_WIDTH]) {
-    tc_fence_after();
-    uint32_t v[32], v2[16], u[8];
-    tmem_ld32(T.taddr, v);
-    tmem_ld16(T.taddr + 32, v2);
-    tmem_ld8(T.taddr + 48, u);
-    tmem_wait_ld();
     auto dz = [&](int j, uint32_t zb) {
         return __float_as_uint(dh[j] * __frcp_rn(1.0f + __expf(-__uint_as_float(zb))));
     };
-    const uint32_t at = T.taddr + 64;
-    uint32_t hw[16], lw[16];
-#pragma unroll
-    for (int i2 = 0; i2 < 16; ++i2) split_rn(dz(2 * i2, v[2 * i2]), dz(2 * i2 + 1, v[2 * i2 + 1]), hw[i2], lw[i2]);
-    tmem_st16(at, hw);
-    uint32_t h9[9], l9[9];
-#pragma unroll
-    for (int i2 = 0; i2 < 9; ++i2) {
-        const uint32_t ra = (i2 < 8) ? v2[2 * i2] : u[0];
-        const uint32_t rb = (i2 < 8) ? v2[2 * i2 + 1] : u[1];
-        split_rn(dz(32 + 2 * i2, ra), dz(33 + 2 * i2, rb), h9[i2], l9[i2]);
-    }
-    const uint32_t gb[16] = {h9[0], h9[1], h9[2], h9[3], h9[4], h9[5], h9[6], h9[7],
-                             h9[8], 0u, 0u, 0u, lw[0], lw[1], lw[2], lw[3]};
-    const uint32_t gc[16] = {lw[4], lw[5], lw[6], lw[7], lw[8], lw[9], lw[10], lw[11],
-                             lw[12], lw[13], lw[14], lw[15], l9[0], l9[1], l9[2], l9[3]};
-    const uint32_t gd[8] = {l9[4], l9[5], l9[6], l9[7], l9[8], 0u, 0u, 0u};
-    tmem_st16(at + 16, gb);
-    tmem_st16(at + 32, gc);
-    tmem_st8(at + 48, gd);
-    tmem_wait_st();
-    tc_fence_before();
+    tile_epilogue(T, [&](int n, uint32_t x0, uint32_t x1, uint32_t& hw, uint32_t& lw) {
+        split_rn(dz(n, x0), dz(n + 1, x1), hw, lw);
+    });
 }
 
 // Cotangent of the collocation points, c_j = lambda * ell_j(X), as the A row
@@ -389,6 +313,7 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
     T.d_bar = smem_u32(&bars[wg]);
     T.bar_id = 1 + wg;
     T.dph = 0;
+    tile_init_row(T);
     uint32_t* tmask = masks + wg * mask_words_per_tile<ACT>() + r;   // word (step, layer l, half h) at ((step*4 + l-1)*2 + h)*128
 
     int64_t n_list = static_cast<int64_t>(*A.count);
@@ -410,6 +335,7 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
             valid = false;
         }
         tile_begin_listed(T, a, g, valid);
+        tile_features_init(T, a);
         if (T.valid) T.valid = path_in_set(a.offsets, T.s, g, a.status);
         int blk = -1;
         float lam = valid ? 1.0f : 0.0f;

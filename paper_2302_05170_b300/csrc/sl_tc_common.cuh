@@ -19,9 +19,30 @@ constexpr int kB1Bytes = 64 * kRowBytes;                 // layer 1: 64 rows x (
 constexpr int kBHBytes = 2 * 64 * kRowBytes;             // hidden: 64 rows x 112 cols
 constexpr int kB5Bytes = 2 * 16 * kRowBytes;             // output: 16 rows x 112 cols
 constexpr int kBBytes = kB1Bytes + 3 * kBHBytes + kB5Bytes;
-constexpr int kLoCol = 56;                               // first column of the lo half
-constexpr int kBiasCol = 50;                             // constant-1 column
 constexpr uint64_t kTimeoutNs = 1000000000ull;           // bounded waits: 1 s
+
+// Hidden A row: 112 BF16 values (K) in 56 tensor-memory columns, two per column, the even K
+// index in the low half.  Chunk c = 0, 1, 2 covers neurons 16c .. 16c+15: columns 16c .. 16c+7
+// hold the hi pairs (neurons 16c+2p, 16c+2p+1 in column 16c+p), columns 16c+8 .. 16c+15 the lo
+// pairs.  Column 48 holds the hi pair of neurons 48, 49, column 49 = {1, 0} (the bias unit),
+// column 50 the lo pair of neurons 48, 49, columns 51..55 = 0.  So an epilogue stores each chunk
+// with one 16-column store straight from the split's outputs, and columns 49, 51..55 never
+// change (tile_init_row writes them once).  The B tiles of the hidden and output layers (and the
+// transposed ones of the adjoint) follow the same K order (hid_k_role).
+enum KRole { kKNone = 0, kKHi = 1, kKLo = 2, kKBias = 3 };
+// The layer-1 A row (the features, K = 16) sits in the slot's last eight columns (120..127,
+// after the accumulator 0..63 and the hidden A row 64..119), where no epilogue overwrites it:
+// its constant words (dt, theta, the bias unit) are written once per tile, Y's word per step.
+constexpr uint32_t kFeatCol = 120;
+constexpr uint32_t kBiasWord = 0x00003F80u;              // {1.0, 0} as BF16x2
+__host__ __device__ constexpr int hid_k_role(int k, int& n) {
+    if (k < 96) {
+        n = 16 * (k >> 5) + (k & 15);
+        return (k & 16) ? kKLo : kKHi;
+    }
+    n = 48 + (k & 1);
+    return (k == 96 || k == 97) ? kKHi : (k == 100 || k == 101) ? kKLo : (k == 98) ? kKBias : kKNone;
+}
 
 // ----------------------------------------------------------------------------
 // PTX wrappers
@@ -115,14 +136,20 @@ __device__ __forceinline__ void mma_commit_w(uint32_t mbar) {
 // The seven K-steps of one layer (K = 112) from tensor-memory A, then the
 // commit, in one block with a single elect.sync: A column of step k is
 // a_tmem + 8k; B descriptor of step k is db + 2k (k < 4) or db + b_atom1 + 2(k-4).
+// The descriptors' start-address field (bits 0..13) stays below 2^14 for every address of
+// shared memory, so the K-step offsets are added to the low word alone.
 __device__ __forceinline__ void mma7_ta_commit(uint32_t d_tmem, uint32_t a_tmem, uint64_t db,
-                                               uint64_t b_atom1, uint32_t idesc, uint32_t mbar) {
+                                               uint32_t b_atom1, uint32_t idesc, uint32_t mbar) {
     asm volatile(
         "{\n.reg .pred e, pf, pt;\n.reg .b64 b1, b2, b3, b4, b5, b6;\n.reg .b32 a1, a2, a3, a4, a5, a6;\n"
+        ".reg .b32 dl, dh, l1, l2, l3, l4, l5, l6;\n"
         "elect.sync _|e, 0xffffffff;\n"
         "setp.ne.b32 pf, %3, %3;\nsetp.eq.b32 pt, %3, %3;\n"
-        "add.s64 b1, %2, 2;\nadd.s64 b2, %2, 4;\nadd.s64 b3, %2, 6;\n"
-        "add.s64 b4, %2, %4;\nadd.s64 b5, b4, 2;\nadd.s64 b6, b4, 4;\n"
+        "mov.b64 {dl, dh}, %2;\n"
+        "add.u32 l1, dl, 2;\nadd.u32 l2, dl, 4;\nadd.u32 l3, dl, 6;\n"
+        "add.u32 l4, dl, %4;\nadd.u32 l5, l4, 2;\nadd.u32 l6, l4, 4;\n"
+        "mov.b64 b1, {l1, dh};\nmov.b64 b2, {l2, dh};\nmov.b64 b3, {l3, dh};\n"
+        "mov.b64 b4, {l4, dh};\nmov.b64 b5, {l5, dh};\nmov.b64 b6, {l6, dh};\n"
         "add.u32 a1, %1, 8;\nadd.u32 a2, %1, 16;\nadd.u32 a3, %1, 24;\n"
         "add.u32 a4, %1, 32;\nadd.u32 a5, %1, 40;\nadd.u32 a6, %1, 48;\n"
         "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, pf;\n"
@@ -133,7 +160,7 @@ __device__ __forceinline__ void mma7_ta_commit(uint32_t d_tmem, uint32_t a_tmem,
         "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [a5], b5, %3, pt;\n"
         "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [a6], b6, %3, pt;\n"
         "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%5];\n}" ::"r"(d_tmem),
-        "r"(a_tmem), "l"(db), "r"(idesc), "l"(b_atom1), "r"(mbar)
+        "r"(a_tmem), "l"(db), "r"(idesc), "r"(b_atom1), "r"(mbar)
         : "memory");
 }
 
@@ -174,6 +201,14 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
                  : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
                    "=r"(v[6]), "=r"(v[7])
                  : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t (&v)[2]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(v[0]), "=r"(v[1]) : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_st1(uint32_t taddr, uint32_t v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
@@ -275,7 +310,8 @@ __device__ __forceinline__ uint32_t b_elem_off(int rows, int n, int k) {
 
 // Stage the network's weights as BF16 B tiles.
 //   B1[n][2i] = B1[n][2i+1] = W1[n][i] (i < d_in), B1[n][2 d_in] = b1[n]
-//   Bl[n][k] = Wl[n][k], Bl[n][50] = bl[n], Bl[n][56+k] = Wl[n][k] (k < 50)
+//   Bl[n][k] = Wl[n][j] where K index k holds neuron j's hi or lo part, bl[n] at the bias
+//   unit's k, 0 elsewhere (the hidden A row's K order, hid_k_role)
 __device__ inline void stage_weights(unsigned char* sB, const float* __restrict__ P, int d_in, int m) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int W = SL_WIDTH;
@@ -301,11 +337,10 @@ __device__ inline void stage_weights(unsigned char* sB, const float* __restrict_
         const float* bl = p + n_out * W;
         for (int i = tid; i < n_out * 112; i += nt) {
             const int n = i / 112, k = i % 112;
-            float v;
-            if (k < W) v = Wl[n * W + k];
-            else if (k == kBiasCol) v = bl[n];
-            else if (k >= kLoCol && k < kLoCol + W) v = Wl[n * W + (k - kLoCol)];
-            else continue;
+            int j = 0;
+            const int role = hid_k_role(k, j);
+            if (role == kKNone) continue;
+            const float v = (role == kKBias) ? bl[n] : Wl[n * W + j];
             *reinterpret_cast<__nv_bfloat16*>(dst + b_elem_off(rows, n, k)) = __float2bfloat16_rn(v);
         }
         p = bl + n_out;
@@ -367,18 +402,30 @@ __device__ __forceinline__ void tile_begin(Tile& T, const SimArgs& a, int64_t ti
     T.z4 = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// Layer-1 A row: features [Y, dt, theta] as (hi, lo) BF16 pairs, then the constant 1.
-__device__ __forceinline__ void tile_features(Tile& T, const SimArgs& a) {
+// x as the BF16 pair (hi, lo) of one layer-1 A word: hi = x truncated, lo = BF16(x - hi).
+__device__ __forceinline__ uint32_t feature_word(float x) {
+    const float hi = __uint_as_float(__float_as_uint(x) & 0xFFFF0000u);
+    return pack_rn(hi, x - hi);
+}
+
+// Layer-1 A row of a new tile: features [Y, dt, theta] as (hi, lo) BF16 pairs, then the
+// constant 1 (columns kFeatCol..kFeatCol+7).
+__device__ __forceinline__ void tile_features_init(Tile& T, const SimArgs& a) {
     T.feat[0] = T.Y;
     uint32_t fw[8];
 #pragma unroll
-    for (int k = 0; k < SL_MAX_DIN_TC; ++k) {
-        const float hi = __uint_as_float(__float_as_uint(T.feat[k]) & 0xFFFF0000u);
-        const uint32_t wv = pack_rn(hi, T.feat[k] - hi);
-        fw[k] = (k < a.d_in) ? wv : ((k == a.d_in) ? 0x00003F80u : 0u);   // 1.0 after the features
-    }
-    fw[7] = (a.d_in == SL_MAX_DIN_TC) ? 0x00003F80u : 0u;
-    tmem_st8(T.taddr + 64, fw);
+    for (int k = 0; k < SL_MAX_DIN_TC; ++k)
+        fw[k] = (k < a.d_in) ? feature_word(T.feat[k]) : ((k == a.d_in) ? kBiasWord : 0u);   // 1.0 after the features
+    fw[7] = (a.d_in == SL_MAX_DIN_TC) ? kBiasWord : 0u;
+    tmem_st8(T.taddr + kFeatCol, fw);
+    tmem_wait_st();
+    tc_fence_before();
+}
+
+// Layer-1 A row of the next step: only Y's word changes.
+__device__ __forceinline__ void tile_features(Tile& T, const SimArgs& a) {
+    (void)a;
+    tmem_st1(T.taddr + kFeatCol, feature_word(T.Y));
     tmem_wait_st();
     tc_fence_before();
 }
@@ -391,7 +438,7 @@ __device__ __forceinline__ bool tile_sync_issue(const Tile& T, const IssueConst&
         constexpr uint32_t kIdesc64 = idesc_bf16(128, 64), kIdesc16 = idesc_bf16(128, 16);
         tc_fence_after();
         if (l == 0) {
-            mma1_ta_commit(T.d_tmem, T.d_tmem + 64, C.db0, kIdesc64, T.d_bar);
+            mma1_ta_commit(T.d_tmem, T.d_tmem + kFeatCol, C.db0, kIdesc64, T.d_bar);
         } else {
             const uint64_t db = (l == 1) ? C.db1 : (l == 2) ? C.db2 : (l == 3) ? C.db3 : C.db4;
             mma7_ta_commit(T.d_tmem, T.d_tmem + 64, db, (l < 4) ? (64 * kRowBytes) >> 4 : (16 * kRowBytes) >> 4,
@@ -414,37 +461,50 @@ __device__ __forceinline__ bool tile_wait(Tile& T, volatile int* abort_flag, uns
     return __all_sync(0xffffffffu, w);
 }
 
-// Hidden-layer epilogue: accumulator row -> activation -> BF16 hi + lo -> next A row.
-// A row (BF16 words): hi 0..24 (columns 0..49), word 25 = {1.0, 0} (bias unit),
-// 26..27 = 0, lo 28..52, 53..55 = 0.
-template <int ACT>
-__device__ __forceinline__ void tile_hidden_act(const Tile& T) {
+// The constant columns of the tile's hidden A row (49 = bias unit, 51..55 = 0), once per
+// kernel before the first MMA (the features' wait::st orders it before the issue).
+__device__ __forceinline__ void tile_init_row(const Tile& T) {
+    const uint32_t c[8] = {0u, kBiasWord, 0u, 0u, 0u, 0u, 0u, 0u};
+    tmem_st8(T.taddr + 64 + 48, c);
+}
+
+// Epilogue frame: the accumulator's columns 0..49 (one FP32 value per neuron) are loaded,
+// f(n, x_n, x_{n+1}, hi_word, lo_word) turns each pair of neurons into a hi and a lo BF16x2
+// word, and the words are stored as the next hidden A row (16 columns per chunk).
+template <class F>
+__device__ __forceinline__ void tile_epilogue(const Tile& T, F&& f) {
     tc_fence_after();
-    uint32_t v[32], v2[16], u[8];
-    tmem_ld32(T.taddr, v);
+    uint32_t v0[16], v1[16], v2[16], v3[2];
+    tmem_ld16(T.taddr, v0);
+    tmem_ld16(T.taddr + 16, v1);
     tmem_ld16(T.taddr + 32, v2);
-    tmem_ld8(T.taddr + 48, u);
+    tmem_ld2(T.taddr + 48, v3);
     tmem_wait_ld();
     const uint32_t at = T.taddr + 64;
-    uint32_t hw[16], lw[16];
+    uint32_t w[16];
 #pragma unroll
-    for (int i2 = 0; i2 < 16; ++i2)     // columns 0..31 -> hi words 0..15, lo words 28..43
-        split_act<ACT>(v[2 * i2], v[2 * i2 + 1], hw[i2], lw[i2]);
-    tmem_st16(at, hw);
-    uint32_t h9[9], l9[9];
+    for (int p = 0; p < 8; ++p) f(2 * p, v0[2 * p], v0[2 * p + 1], w[p], w[8 + p]);
+    tmem_st16(at, w);
 #pragma unroll
-    for (int i2 = 0; i2 < 9; ++i2)      // columns 32..49 -> hi words 16..24, lo words 44..52
-        split_act<ACT>((i2 < 8) ? v2[2 * i2] : u[0], (i2 < 8) ? v2[2 * i2 + 1] : u[1], h9[i2], l9[i2]);
-    const uint32_t gb[16] = {h9[0], h9[1], h9[2], h9[3], h9[4], h9[5], h9[6], h9[7],
-                             h9[8], 0x00003F80u, 0u, 0u, lw[0], lw[1], lw[2], lw[3]};
-    const uint32_t gc[16] = {lw[4], lw[5], lw[6], lw[7], lw[8], lw[9], lw[10], lw[11],
-                             lw[12], lw[13], lw[14], lw[15], l9[0], l9[1], l9[2], l9[3]};
-    const uint32_t gd[8] = {l9[4], l9[5], l9[6], l9[7], l9[8], 0u, 0u, 0u};
-    tmem_st16(at + 16, gb);
-    tmem_st16(at + 32, gc);
-    tmem_st8(at + 48, gd);
+    for (int p = 0; p < 8; ++p) f(16 + 2 * p, v1[2 * p], v1[2 * p + 1], w[p], w[8 + p]);
+    tmem_st16(at + 16, w);
+#pragma unroll
+    for (int p = 0; p < 8; ++p) f(32 + 2 * p, v2[2 * p], v2[2 * p + 1], w[p], w[8 + p]);
+    tmem_st16(at + 32, w);
+    uint32_t h, l;
+    f(48, v3[0], v3[1], h, l);
+    tmem_st1(at + 48, h);
+    tmem_st1(at + 50, l);
     tmem_wait_st();
     tc_fence_before();
+}
+
+// Hidden-layer epilogue: accumulator row -> activation -> BF16 hi + lo -> next A row.
+template <int ACT>
+__device__ __forceinline__ void tile_hidden_act(const Tile& T) {
+    tile_epilogue(T, [](int, uint32_t x0, uint32_t x1, uint32_t& hw, uint32_t& lw) {
+        split_act<ACT>(x0, x1, hw, lw);
+    });
 }
 
 __device__ __forceinline__ void tile_hidden(const Tile& T) { tile_hidden_act<SL_ACT_RELU>(T); }
