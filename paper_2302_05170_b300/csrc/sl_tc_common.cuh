@@ -275,25 +275,12 @@ __device__ __forceinline__ uint32_t pack_rn(float lo_elem, float hi_elem) {
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi_elem), "f"(lo_elem));
     return d;
 }
-// Activation of a pair as BF16 hi + lo: ReLU (fused into the conversions) or Softplus.
-template <int ACT>
-__device__ __forceinline__ void split_act(uint32_t a, uint32_t b, uint32_t& hw, uint32_t& lw);
-
 // x as BF16 hi + lo for a pair (a, b), no ReLU (cotangents have either sign).
 __device__ __forceinline__ void split_rn(uint32_t a, uint32_t b, uint32_t& hw, uint32_t& lw) {
     asm("cvt.rz.bf16x2.f32 %0, %1, %2;" : "=r"(hw) : "f"(__uint_as_float(b)), "f"(__uint_as_float(a)));
     float la, lb;
     sub_f32x2(a, b, hw << 16, hw & 0xFFFF0000u, la, lb);
     lw = pack_rn(la, lb);
-}
-template <>
-__device__ __forceinline__ void split_act<SL_ACT_RELU>(uint32_t a, uint32_t b, uint32_t& hw, uint32_t& lw) {
-    split_relu(a, b, hw, lw);
-}
-template <>
-__device__ __forceinline__ void split_act<SL_ACT_SOFTPLUS>(uint32_t a, uint32_t b, uint32_t& hw, uint32_t& lw) {
-    split_rn(__float_as_uint(softplus_fast(__uint_as_float(a))), __float_as_uint(softplus_fast(__uint_as_float(b))),
-             hw, lw);
 }
 
 // Byte offset of 16-byte chunk `c` (0..7) of row `r` inside a 128B-swizzled atom.
@@ -468,11 +455,12 @@ __device__ __forceinline__ void tile_init_row(const Tile& T) {
     tmem_st8(T.taddr + 64 + 48, c);
 }
 
-// Epilogue frame: the accumulator's columns 0..49 (one FP32 value per neuron) are loaded,
+// Epilogue frame: the accumulator's columns 0..49 (one FP32 value per neuron) are loaded and
+// mapped by pre (all fifty first, so that a long-latency activation has them all in flight),
 // f(n, x_n, x_{n+1}, hi_word, lo_word) turns each pair of neurons into a hi and a lo BF16x2
 // word, and the words are stored as the next hidden A row (16 columns per chunk).
-template <class F>
-__device__ __forceinline__ void tile_epilogue(const Tile& T, F&& f) {
+template <class Pre, class F>
+__device__ __forceinline__ void tile_epilogue(const Tile& T, Pre&& pre, F&& f) {
     tc_fence_after();
     uint32_t v0[16], v1[16], v2[16], v3[2];
     tmem_ld16(T.taddr, v0);
@@ -480,6 +468,14 @@ __device__ __forceinline__ void tile_epilogue(const Tile& T, F&& f) {
     tmem_ld16(T.taddr + 32, v2);
     tmem_ld2(T.taddr + 48, v3);
     tmem_wait_ld();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        v0[k] = pre(v0[k]);
+        v1[k] = pre(v1[k]);
+        v2[k] = pre(v2[k]);
+    }
+    v3[0] = pre(v3[0]);
+    v3[1] = pre(v3[1]);
     const uint32_t at = T.taddr + 64;
     uint32_t w[16];
 #pragma unroll
@@ -499,12 +495,24 @@ __device__ __forceinline__ void tile_epilogue(const Tile& T, F&& f) {
     tc_fence_before();
 }
 
+template <class F>
+__device__ __forceinline__ void tile_epilogue(const Tile& T, F&& f) {
+    tile_epilogue(T, [](uint32_t x) { return x; }, f);
+}
+
 // Hidden-layer epilogue: accumulator row -> activation -> BF16 hi + lo -> next A row.
+// ReLU is fused into the split's conversions; Softplus is applied to the whole row first.
 template <int ACT>
 __device__ __forceinline__ void tile_hidden_act(const Tile& T) {
-    tile_epilogue(T, [](int, uint32_t x0, uint32_t x1, uint32_t& hw, uint32_t& lw) {
-        split_act<ACT>(x0, x1, hw, lw);
-    });
+    if constexpr (ACT == SL_ACT_SOFTPLUS) {
+        tile_epilogue(
+            T, [](uint32_t x) { return __float_as_uint(softplus_fast(__uint_as_float(x))); },
+            [](int, uint32_t x0, uint32_t x1, uint32_t& hw, uint32_t& lw) { split_rn(x0, x1, hw, lw); });
+    } else {
+        tile_epilogue(T, [](int, uint32_t x0, uint32_t x1, uint32_t& hw, uint32_t& lw) {
+            split_relu(x0, x1, hw, lw);
+        });
+    }
 }
 
 __device__ __forceinline__ void tile_hidden(const Tile& T) { tile_hidden_act<SL_ACT_RELU>(T); }
