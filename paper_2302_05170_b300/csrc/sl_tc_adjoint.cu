@@ -128,29 +128,41 @@ __device__ __forceinline__ bool tile_sync_issue_T(const Tile& T, const IssueCons
 constexpr int kMaskSteps = 8;
 constexpr int kMaskWordsPerTile = kMaskSteps * 4 * 2 * kTile;
 
+// ReLU pattern of a hidden layer as 64 bits (two words): the pair of neurons (n, n+1),
+// n = 32h + 2p + 16c' (h = word, c' = 0 or 1 the chunk inside the word, p = 0..7; the last
+// pair, neurons 48 and 49, is p = 8 of word 1), owns bits q = p + 8c' (neuron n) and 16 + q
+// (neuron n+1) of word h.
+__device__ __forceinline__ constexpr int relu_bit(int n) { return ((n & 15) >> 1) + 8 * ((n >> 4) & 1); }
+
 // Hidden epilogue of a recorded forward step: the sampler's epilogue (ReLU, BF16 hi + lo,
-// next A row) plus the layer's ReLU pattern as bits -- bit j of word 0 for neuron j < 32,
-// bit j of word 1 for neuron 32 + j -- stored to mrow[0] and mrow[kTile].
+// next A row) plus the layer's ReLU pattern (relu_bit), stored to mrow[0] and mrow[kTile].
+// A neuron's bit is "its truncated BF16 hi part is nonzero", i.e. z >= 2^-126: the pair's
+// hi word plus 0x7FFF7FFF carries each nonzero half into that half's top bit (halves are at
+// most 0x7F80 after the ReLU, so nothing carries across), and one shift and one masked OR
+// move the two bits into place.
 __device__ __forceinline__ void tile_hidden_rec(const Tile& T, uint32_t* mrow) {
     uint32_t m0 = 0u, m1 = 0u;
     tile_epilogue(T, [&](int n, uint32_t x0, uint32_t x1, uint32_t& hw, uint32_t& lw) {
-        const uint32_t bits = ((static_cast<int32_t>(x0) > 0) ? 1u : 0u) | ((static_cast<int32_t>(x1) > 0) ? 2u : 0u);
-        if (n < 32) m0 |= bits << n;
-        else m1 |= bits << (n - 32);
         split_relu(x0, x1, hw, lw);
+        const int q = relu_bit(n);
+        const uint32_t t = (hw + 0x7FFF7FFFu) >> (15 - q);
+        const uint32_t sel = (1u << q) | (1u << (16 + q));
+        if (n < 32) m0 |= t & sel;
+        else m1 |= t & sel;
     });
     mrow[0] = m0;
     mrow[kTile] = m1;
 }
 
 // Backward epilogue: dh (accumulator columns 0..49) masked by the recorded ReLU pattern
-// (m0: neurons 0..31, m1: neurons 32..49), split into BF16 hi + lo (no ReLU: cotangents
-// have either sign) and written as the next A row (the hidden A row's layout; the bias
-// unit meets a zero row of the transposed weights).
+// (m0: neurons 0..31, m1: neurons 32..49, bits as relu_bit), split into BF16 hi + lo (no
+// ReLU: cotangents have either sign) and written as the next A row (the hidden A row's
+// layout; the bias unit meets a zero row of the transposed weights).
 __device__ __forceinline__ void tile_backward_bits(const Tile& T, uint32_t m0, uint32_t m1) {
     tile_epilogue(T, [&](int n, uint32_t x0, uint32_t x1, uint32_t& hw, uint32_t& lw) {
-        const uint32_t mb = (n < 32) ? (m0 >> n) : (m1 >> (n - 32));
-        split_rn((mb & 1u) ? x0 : 0u, (mb & 2u) ? x1 : 0u, hw, lw);
+        const uint32_t w = (n < 32) ? m0 : m1;
+        const int q = relu_bit(n);
+        split_rn((w & (1u << q)) ? x0 : 0u, (w & (1u << (16 + q))) ? x1 : 0u, hw, lw);
     });
 }
 
