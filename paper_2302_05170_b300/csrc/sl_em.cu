@@ -6,7 +6,8 @@
 // memory traffic is the 4-byte terminal sample.  Select: one CTA per segment,
 // exact radix select over the order-preserving 32-bit keys (4 passes of 8
 // bits, all requested ranks at once, one histogram per distinct prefix),
-// with warp-aggregated shared-memory histogram updates (__match_any_sync).
+// with warp-aggregated shared-memory histogram updates (__match_any_sync) and
+// the segment read as float4 where it is 16-byte aligned.
 #include <math.h>
 
 #include "sl_internal.cuh"
@@ -95,6 +96,12 @@ segmented_select_kernel(const float* __restrict__ values, const int64_t* __restr
         prefix[tid] = 0u;
         rem[tid] = ranks.r[tid];
     }
+    // [a, a + n) = head [a, a4) + body of n4 float4 at 16-byte aligned addresses + tail [e4, a + n)
+    const int64_t mis = static_cast<int64_t>((reinterpret_cast<uintptr_t>(values) >> 2) & 3u);
+    const int64_t a4 = min(a + ((4 - ((mis + a) & 3)) & 3), a + n);
+    const int64_t e4 = max(a4, a + n - ((mis + a + n) & 3));
+    const int64_t n4 = (e4 - a4) >> 2;
+    const int head = static_cast<int>(a4 - a), tail = static_cast<int>(a + n - e4);
     __syncthreads();
     for (int pass = 0; pass < 4; ++pass) {
         const int shift = 24 - 8 * pass;
@@ -115,19 +122,41 @@ segmented_select_kernel(const float* __restrict__ values, const int64_t* __restr
         const int ng = n_groups;
         for (int i = tid; i < ng * 256; i += kSelThreads) hist[i >> 8][i & 255] = 0u;
         __syncthreads();
-        for (int64_t base = 0; base < n; base += kSelThreads) {
-            const int64_t idx = base + tid;
-            const bool in = idx < n;
-            const uint32_t key = in ? float_key(__ldg(values + a + idx)) : 0u;
-            const uint32_t digit = (key >> shift) & 255u;
-            for (int g = 0; g < ng; ++g) {
-                const bool hit = in && ((key & hi_mask) == gprefix[g]);
-                const unsigned act = __ballot_sync(0xffffffffu, hit);
-                if (hit) {
-                    const unsigned peers = __match_any_sync(act, digit);
-                    if (lane == __ffs(peers) - 1) atomicAdd(&hist[g][digit], __popc(peers));
-                }
+        // One value (warp-converged call): its group g (the rank prefix it extends; none when it
+        // matches no prefix), then one shared-memory add per distinct (g, digit) of the warp.
+        auto count = [&](float v, bool in) {
+            const uint32_t key = float_key(v);
+            int g = -1;
+            if (in) {
+                const uint32_t hk = key & hi_mask;
+                for (int j = 0; j < ng; ++j)
+                    if (hk == gprefix[j]) {
+                        g = j;
+                        break;
+                    }
             }
+            const unsigned act = __ballot_sync(0xffffffffu, g >= 0);
+            if (g >= 0) {
+                const uint32_t digit = (key >> shift) & 255u;
+                const unsigned peers = __match_any_sync(act, (static_cast<uint32_t>(g) << 8) | digit);
+                if (lane == __ffs(peers) - 1) atomicAdd(&hist[g][digit], __popc(peers));
+            }
+        };
+        // Aligned body as float4 loads (four values per thread per round); the unaligned head
+        // [a, a4) and tail [e4, a + n), at most three values each, by warp 0.
+        for (int64_t base = 0; base < n4; base += kSelThreads) {
+            const int64_t c = base + tid;
+            const bool in = c < n4;
+            const float4 v4 = in ? __ldg(reinterpret_cast<const float4*>(values + a4) + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+            count(v4.x, in);
+            count(v4.y, in);
+            count(v4.z, in);
+            count(v4.w, in);
+        }
+        if (warp == 0) {
+            const int64_t idx = (lane < head) ? a + lane : e4 + (lane - head);
+            const bool in = lane < head + tail;
+            count(in ? __ldg(values + idx) : 0.0f, in);
         }
         __syncthreads();
         if (warp < nk && group_of[warp] >= 0) {   // warp j resolves rank j's digit

@@ -4,7 +4,8 @@
   truncation): FP32 against FP64 on the same Philox normals, per path within
   1e-5 of |a - b| / (|b| + s) (s = the row's start value or long-run level).
 * Segmented order statistics: bit-exact against the oracle's sort on ragged
-  segments (empty, length 1, ties, NaN for ranks past the end).
+  segments (empty, length 1, ties, NaN for ranks past the end), short segments at
+  every alignment and a base pointer off a 16-byte boundary.
 * Labels: the GPU's empirical quantiles differ from the oracle's by at most
   the largest per-path sample difference of the row (order statistics are
   1-Lipschitz in the sup norm), and equal the select of the GPU's own samples.
@@ -66,6 +67,27 @@ def test_select_bit_exact(sl, orc, ties):
     v[:50] = -0.0 if ties else v[:50]
     ranks = np.array([0, 1, 7, 100, 2499, 4999])
     got = sl.segmented_select(_dev(v), _dev(off, torch.int64), ranks).cpu().numpy()
+    want = orc.order_statistics(v, off, ranks)
+    assert np.array_equal(np.isnan(got), np.isnan(want))
+    fin = ~np.isnan(want)
+    assert np.array_equal(got[fin], want[fin].astype(np.float32))
+
+
+@pytest.mark.parametrize("shift", [0, 1, 2, 3])
+def test_select_short_and_misaligned(sl, orc, shift):
+    """Segments of every length 0..41 at every 4-value alignment, read from a base pointer
+    `shift` values past a 16-byte boundary: the select's unaligned head and tail, the aligned
+    float4 body and segments with no body at all."""
+    rng = np.random.default_rng(7 + shift)
+    lens = np.concatenate([np.arange(42), np.arange(42)[::-1], rng.integers(0, 9, 40)])
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    v = rng.standard_normal(int(off[-1])).astype(np.float32)
+    v[rng.integers(0, v.size, 30)] = 0.5                      # ties
+    ranks = np.array([0, 1, 2, 3, 5, 8, 20, 40])
+    buf = torch.zeros(v.size + 8, dtype=torch.float32, device="cuda")
+    view = buf[shift:shift + v.size]
+    view.copy_(_dev(v))
+    got = sl.segmented_select(view, _dev(off, torch.int64), ranks).cpu().numpy()
     want = orc.order_statistics(v, off, ranks)
     assert np.array_equal(np.isnan(got), np.isnan(want))
     fin = ~np.isnan(want)
