@@ -28,17 +28,29 @@ __device__ __forceinline__ float sqrt_approx(float x) {
     return y;
 }
 
+// -2 log u for u in (0, 1): the fast base-2 logarithm (absolute error near 2^-22), except within
+// 2^-7 of 1, where -log(1 - t) = t + t^2/2 + t^3/3 + t^4/4 + O(t^5) in t = 1 - u (exact in FP32)
+// keeps the small result's relative accuracy (the series' remainder is below 1e-9 of it).
+__device__ __forceinline__ float minus_2log(float u) {
+    const float t = 1.0f - u;
+    float lg;
+    asm("lg2.approx.f32 %0, %1;" : "=f"(lg) : "f"(u));
+    const float ser = 2.0f * t * fmaf(t, fmaf(t, fmaf(t, 0.25f, 0.333333333f), 0.5f), 1.0f);
+    return t < 0.0078125f ? ser : -1.38629436f * lg;
+}
+
 // The EM stage's normals 4*block .. 4*block+3: the same Philox4x32-10 words and Box-Muller
 // pairs as normal4 (radius sqrt(-2 log u0), angle 2 pi u1; (cos, sin)), with the fast
-// sine/cosine (absolute error about 2^-21 on [-pi, pi], so the angle is taken as
-// 2 pi (u1 - 1/2), exact in FP32, and both results negated) and the approximate square root:
-// about 20 instructions fewer per pair in a loop that is bound by instruction issue.
+// logarithm (minus_2log), the fast sine/cosine (absolute error about 2^-21 on [-pi, pi], so
+// the angle is taken as 2 pi (u1 - 1/2), exact in FP32, and both results negated) and the
+// approximate square root: about 25 instructions fewer per pair in a loop that is bound by
+// instruction issue.
 __device__ __forceinline__ float4 normal4_em(uint64_t seed, uint32_t tag, uint32_t set, uint32_t path,
                                              uint32_t block) {
     const uint4 w = philox4x32_10(make_uint4(block, path, set, tag), static_cast<uint32_t>(seed),
                                   static_cast<uint32_t>(seed >> 32));
-    const float r0 = sqrt_approx(-2.0f * logf(word_to_uniform(w.x)));
-    const float r1 = sqrt_approx(-2.0f * logf(word_to_uniform(w.z)));
+    const float r0 = sqrt_approx(minus_2log(word_to_uniform(w.x)));
+    const float r1 = sqrt_approx(minus_2log(word_to_uniform(w.z)));
     float s0, c0, s1, c1;
     __sincosf(6.28318530717958648f * (word_to_uniform(w.y) - 0.5f), &s0, &c0);
     __sincosf(6.28318530717958648f * (word_to_uniform(w.w) - 0.5f), &s1, &c1);
@@ -59,6 +71,8 @@ em_terminal_kernel(const float* __restrict__ theta, const float* __restrict__ Yi
     float Y = __ldg(Yi + r);
     const float dtau = __ldg(dt + r) / static_cast<float>(n_fine);
     const float sq = sqrtf(dtau);
+    // the drift and diffusion coefficients with the step folded in
+    const float t0dt = t0 * dtau, t1sq = t1 * sq, t2dt = t2 * dtau, t2sq = t2 * sq;
     for (int k = 0; k < n_fine; k += 4) {
         const float4 z = normal4_em(seed, 1u, static_cast<uint32_t>(r), static_cast<uint32_t>(q),
                                     static_cast<uint32_t>(k >> 2));
@@ -66,19 +80,14 @@ em_terminal_kernel(const float* __restrict__ theta, const float* __restrict__ Yi
         for (int u = 0; u < 4; ++u) {
             if (k + u < n_fine) {
                 const float X = pick4(z, u);
-                float a, b;
-                if (SDE == SL_SDE_GBM) {            // (mu, sigma)
-                    a = t0 * Y;
-                    b = t1 * Y;
-                } else if (SDE == SL_SDE_OU) {      // (Ybar, sigma, lambda), Eq. 6.5
-                    a = -t2 * (Y - t0);
-                    b = t1;
+                if (SDE == SL_SDE_GBM) {            // (mu, sigma): a = mu Y, b = sigma Y
+                    Y = fmaf(t1sq * Y, X, fmaf(t0dt, Y, Y));
+                } else if (SDE == SL_SDE_OU) {      // (Ybar, sigma, lambda), Eq. 6.5: a = -lambda (Y - Ybar), b = sigma
+                    Y = fmaf(t1sq, X, fmaf(-t2dt, Y - t0, Y));
                 } else {                            // CIR (kappa, ybar, gamma), full truncation
-                    const float yp = fmaxf(Y, 0.0f);
-                    a = t0 * (t1 - yp);
-                    b = t2 * sqrt_approx(yp);
+                    const float yp = fmaxf(Y, 0.0f);   // a = kappa (ybar - Y+), b = gamma sqrt(Y+)
+                    Y = fmaf(t2sq * sqrt_approx(yp), X, fmaf(t0dt, t1 - yp, Y));
                 }
-                Y = fmaf(b * sq, X, fmaf(a, dtau, Y));
             }
         }
     }
