@@ -23,6 +23,7 @@
 #include <math.h>
 
 #include "sl_check.cuh"
+#include "sl_fastnormal.cuh"
 #include "sl_internal.cuh"
 #include "sl_simt_net.cuh"
 
@@ -718,8 +719,8 @@ __device__ __forceinline__ void cdc_paths(const SimArgs& a, const float* __restr
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
             if ((i & 3) == 0)
-                z4[p] = normal4(a.seed, 0u, static_cast<uint32_t>(s), static_cast<uint32_t>(q[p]),
-                                static_cast<uint32_t>(i >> 2));
+                z4[p] = normal4_fast(a.seed, 0u, static_cast<uint32_t>(s), static_cast<uint32_t>(q[p]),
+                                     static_cast<uint32_t>(i >> 2));
             X[p] = pick4(z4[p], i & 3);
         }
         const float* t = ts + static_cast<int64_t>(i) * kTabFloats;

@@ -4,7 +4,7 @@
 //
 // EM: one thread per path, the whole fine-step loop in registers; the only
 // memory traffic is the 4-byte terminal sample; the normals' Box-Muller uses the
-// fast sine/cosine and approximate square root (normal4_em).  Select: one CTA per segment,
+// fast logarithm, sine/cosine and square root (normal4_fast).  Select: one CTA per segment,
 // exact radix select over the order-preserving 32-bit keys (4 passes of 8
 // bits, all requested ranks at once, one histogram per distinct prefix),
 // with warp-aggregated shared-memory histogram updates (__match_any_sync) and
@@ -12,6 +12,7 @@
 #include <math.h>
 
 #include "sl_internal.cuh"
+#include "sl_fastnormal.cuh"
 
 namespace sl {
 namespace {
@@ -19,43 +20,6 @@ namespace {
 constexpr int kEmThreads = 256;
 constexpr int kSelThreads = 512;
 constexpr int kMaxK = 16;
-
-// Square root on the special-function unit (relative error near one ulp; the EM update's
-// other FP32 roundings are of the same size).
-__device__ __forceinline__ float sqrt_approx(float x) {
-    float y;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// -2 log u for u in (0, 1): the fast base-2 logarithm (absolute error near 2^-22), except within
-// 2^-7 of 1, where -log(1 - t) = t + t^2/2 + t^3/3 + t^4/4 + O(t^5) in t = 1 - u (exact in FP32)
-// keeps the small result's relative accuracy (the series' remainder is below 1e-9 of it).
-__device__ __forceinline__ float minus_2log(float u) {
-    const float t = 1.0f - u;
-    float lg;
-    asm("lg2.approx.f32 %0, %1;" : "=f"(lg) : "f"(u));
-    const float ser = 2.0f * t * fmaf(t, fmaf(t, fmaf(t, 0.25f, 0.333333333f), 0.5f), 1.0f);
-    return t < 0.0078125f ? ser : -1.38629436f * lg;
-}
-
-// The EM stage's normals 4*block .. 4*block+3: the same Philox4x32-10 words and Box-Muller
-// pairs as normal4 (radius sqrt(-2 log u0), angle 2 pi u1; (cos, sin)), with the fast
-// logarithm (minus_2log), the fast sine/cosine (absolute error about 2^-21 on [-pi, pi], so
-// the angle is taken as 2 pi (u1 - 1/2), exact in FP32, and both results negated) and the
-// approximate square root: about 25 instructions fewer per pair in a loop that is bound by
-// instruction issue.
-__device__ __forceinline__ float4 normal4_em(uint64_t seed, uint32_t tag, uint32_t set, uint32_t path,
-                                             uint32_t block) {
-    const uint4 w = philox4x32_10(make_uint4(block, path, set, tag), static_cast<uint32_t>(seed),
-                                  static_cast<uint32_t>(seed >> 32));
-    const float r0 = sqrt_approx(minus_2log(word_to_uniform(w.x)));
-    const float r1 = sqrt_approx(minus_2log(word_to_uniform(w.z)));
-    float s0, c0, s1, c1;
-    __sincosf(6.28318530717958648f * (word_to_uniform(w.y) - 0.5f), &s0, &c0);
-    __sincosf(6.28318530717958648f * (word_to_uniform(w.w) - 0.5f), &s1, &c1);
-    return make_float4(-r0 * c0, -r0 * s0, -r1 * c1, -r1 * s1);
-}
 
 template <int SDE>
 __global__ void __launch_bounds__(kEmThreads)
@@ -74,7 +38,7 @@ em_terminal_kernel(const float* __restrict__ theta, const float* __restrict__ Yi
     // the drift and diffusion coefficients with the step folded in
     const float t0dt = t0 * dtau, t1sq = t1 * sq, t2dt = t2 * dtau, t2sq = t2 * sq;
     for (int k = 0; k < n_fine; k += 4) {
-        const float4 z = normal4_em(seed, 1u, static_cast<uint32_t>(r), static_cast<uint32_t>(q),
+        const float4 z = normal4_fast(seed, 1u, static_cast<uint32_t>(r), static_cast<uint32_t>(q),
                                     static_cast<uint32_t>(k >> 2));
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
