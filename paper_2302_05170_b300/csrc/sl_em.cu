@@ -37,23 +37,30 @@ em_terminal_kernel(const float* __restrict__ theta, const float* __restrict__ Yi
     const float sq = sqrtf(dtau);
     // the drift and diffusion coefficients with the step folded in
     const float t0dt = t0 * dtau, t1sq = t1 * sq, t2dt = t2 * dtau, t2sq = t2 * sq;
-    for (int k = 0; k < n_fine; k += 4) {
-        const float4 z = normal4_fast(seed, 1u, static_cast<uint32_t>(r), static_cast<uint32_t>(q),
-                                    static_cast<uint32_t>(k >> 2));
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (k + u < n_fine) {
-                const float X = pick4(z, u);
-                if (SDE == SL_SDE_GBM) {            // (mu, sigma): a = mu Y, b = sigma Y
-                    Y = fmaf(t1sq * Y, X, fmaf(t0dt, Y, Y));
-                } else if (SDE == SL_SDE_OU) {      // (Ybar, sigma, lambda), Eq. 6.5: a = -lambda (Y - Ybar), b = sigma
-                    Y = fmaf(t1sq, X, fmaf(-t2dt, Y - t0, Y));
-                } else {                            // CIR (kappa, ybar, gamma), full truncation
-                    const float yp = fmaxf(Y, 0.0f);   // a = kappa (ybar - Y+), b = gamma sqrt(Y+)
-                    Y = fmaf(t2sq * sqrt_approx(yp), X, fmaf(t0dt, t1 - yp, Y));
-                }
-            }
+    auto step = [&](float X) {
+        if (SDE == SL_SDE_GBM) {            // (mu, sigma): a = mu Y, b = sigma Y
+            Y = fmaf(t1sq * Y, X, fmaf(t0dt, Y, Y));
+        } else if (SDE == SL_SDE_OU) {      // (Ybar, sigma, lambda), Eq. 6.5: a = -lambda (Y - Ybar), b = sigma
+            Y = fmaf(t1sq, X, fmaf(-t2dt, Y - t0, Y));
+        } else {                            // CIR (kappa, ybar, gamma), full truncation
+            const float yp = fmaxf(Y, 0.0f);   // a = kappa (ybar - Y+), b = gamma sqrt(Y+)
+            Y = fmaf(t2sq * sqrt_approx(yp), X, fmaf(t0dt, t1 - yp, Y));
         }
+    };
+    // whole blocks of four fine steps (one Philox call each), then the remainder
+    const int n4 = n_fine >> 2;
+    for (int k = 0; k < n4; ++k) {
+        const float4 z = normal4_fast(seed, 1u, static_cast<uint32_t>(r), static_cast<uint32_t>(q),
+                                      static_cast<uint32_t>(k));
+        step(z.x);
+        step(z.y);
+        step(z.z);
+        step(z.w);
+    }
+    if (n_fine & 3) {
+        const float4 z = normal4_fast(seed, 1u, static_cast<uint32_t>(r), static_cast<uint32_t>(q),
+                                      static_cast<uint32_t>(n4));
+        for (int u = 0; u < (n_fine & 3); ++u) step(pick4(z, u));
     }
     if (SDE == SL_SDE_CIR) Y = fmaxf(Y, 0.0f);
     out[static_cast<int64_t>(r) * n_paths + q] = Y;

@@ -26,21 +26,30 @@ __device__ __forceinline__ float minus_2log(float u) {
     return t < 0.0078125f ? ser : -1.38629436f * lg;
 }
 
+// The uniform ((w >> 9) + 1/2) 2^-23 of word_to_uniform without an integer-to-float conversion:
+// 1 + (w >> 9) 2^-23 is the float with those mantissa bits, and subtracting 1 - 2^-24 (exact in
+// FP32) is exact by Sterbenz's lemma, so it gives word_to_uniform's value bit for bit.
+constexpr float kOneMinusHalfUlp = 0.99999994039535522f;   // 1 - 2^-24
+constexpr float kTwoPi = 6.28318530717958648f;
+constexpr float kTwoPiHalfUlp = 3.74507028e-07f;            // 2 pi 2^-24
+__device__ __forceinline__ float uniform_bits(uint32_t w) { return __uint_as_float(0x3F800000u | (w >> 9)); }
+
 // Normals 4*block .. 4*block+3 for the issue-bound kernels (the EM stage, the 7L-CDC
 // paths): the same Philox4x32-10 words and Box-Muller pairs as normal4 (radius
 // sqrt(-2 log u0), angle 2 pi u1; (cos, sin)), with the fast logarithm (minus_2log), the fast
 // sine/cosine (absolute error about 2^-21 on [-pi, pi], so the angle is taken as
-// 2 pi (u1 - 1/2), exact in FP32, and both results negated) and the approximate square root:
+// 2 pi (u1 - 1/2) and both results negated) and the approximate square root:
 // about 25 instructions fewer per pair than normal4.
 __device__ __forceinline__ float4 normal4_fast(uint64_t seed, uint32_t tag, uint32_t set, uint32_t path,
                                                uint32_t block) {
     const uint4 w = philox4x32_10(make_uint4(block, path, set, tag), static_cast<uint32_t>(seed),
                                   static_cast<uint32_t>(seed >> 32));
-    const float r0 = sqrt_approx(minus_2log(word_to_uniform(w.x)));
-    const float r1 = sqrt_approx(minus_2log(word_to_uniform(w.z)));
+    const float r0 = sqrt_approx(minus_2log(uniform_bits(w.x) - kOneMinusHalfUlp));
+    const float r1 = sqrt_approx(minus_2log(uniform_bits(w.z) - kOneMinusHalfUlp));
     float s0, c0, s1, c1;
-    __sincosf(6.28318530717958648f * (word_to_uniform(w.y) - 0.5f), &s0, &c0);
-    __sincosf(6.28318530717958648f * (word_to_uniform(w.w) - 0.5f), &s1, &c1);
+    // angle 2 pi (u - 1/2) = 2 pi ((1 + m 2^-23) - 3/2) + 2 pi 2^-24, the difference exact
+    __sincosf(fmaf(kTwoPi, uniform_bits(w.y) - 1.5f, kTwoPiHalfUlp), &s0, &c0);
+    __sincosf(fmaf(kTwoPi, uniform_bits(w.w) - 1.5f, kTwoPiHalfUlp), &s1, &c1);
     return make_float4(-r0 * c0, -r0 * s0, -r1 * c1, -r1 * s1);
 }
 
