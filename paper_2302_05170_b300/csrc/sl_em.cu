@@ -2,7 +2,7 @@
 // fine-step Euler-Maruyama terminal samples (Eq. 6.2) and their empirical
 // quantiles at levels Phi(x_j), the collocation labels y_j | (theta, Y_i, dt).
 //
-// EM: one thread per path, the whole fine-step loop in registers; the only
+// EM: two paths per thread, the whole fine-step loop in registers; the only
 // memory traffic is the 4-byte terminal sample; the normals' Box-Muller uses the
 // fast logarithm, sine/cosine and square root (normal4_fast).  Select: one CTA per segment,
 // exact radix select over the order-preserving 32-bit keys (4 passes of 8
@@ -21,23 +21,27 @@ constexpr int kEmThreads = 256;
 constexpr int kSelThreads = 512;
 constexpr int kMaxK = 16;
 
+// Two paths per thread (q and q + kEmThreads of the CTA's 2 kEmThreads): their independent
+// step chains interleave, which keeps the issue slots busier than one chain per thread.
+constexpr int kEmPaths = 2;
+
 template <int SDE>
 __global__ void __launch_bounds__(kEmThreads)
 em_terminal_kernel(const float* __restrict__ theta, const float* __restrict__ Yi,
                    const float* __restrict__ dt, int64_t n_paths, int n_fine, uint64_t seed,
                    float* __restrict__ out) {
     const int r = blockIdx.y;
-    const int64_t q = static_cast<int64_t>(blockIdx.x) * kEmThreads + threadIdx.x;
-    if (q >= n_paths) return;
+    const int64_t q0 = static_cast<int64_t>(blockIdx.x) * (kEmPaths * kEmThreads) + threadIdx.x;
+    if (q0 >= n_paths) return;
     constexpr int P = (SDE == SL_SDE_GBM) ? 2 : 3;
     const float t0 = __ldg(theta + r * P), t1 = __ldg(theta + r * P + 1);
     const float t2 = (P == 3) ? __ldg(theta + r * P + 2) : 0.0f;
-    float Y = __ldg(Yi + r);
+    const float y0 = __ldg(Yi + r);
     const float dtau = __ldg(dt + r) / static_cast<float>(n_fine);
     const float sq = sqrtf(dtau);
     // the drift and diffusion coefficients with the step folded in
     const float t0dt = t0 * dtau, t1sq = t1 * sq, t2dt = t2 * dtau, t2sq = t2 * sq;
-    auto step = [&](float X) {
+    auto step = [&](float& Y, float X) {
         if (SDE == SL_SDE_GBM) {            // (mu, sigma): a = mu Y, b = sigma Y
             Y = fmaf(t1sq * Y, X, fmaf(t0dt, Y, Y));
         } else if (SDE == SL_SDE_OU) {      // (Ybar, sigma, lambda), Eq. 6.5: a = -lambda (Y - Ybar), b = sigma
@@ -47,23 +51,37 @@ em_terminal_kernel(const float* __restrict__ theta, const float* __restrict__ Yi
             Y = fmaf(t2sq * sqrt_approx(yp), X, fmaf(t0dt, t1 - yp, Y));
         }
     };
-    // whole blocks of four fine steps (one Philox call each), then the remainder
+    float Y[kEmPaths];
+    uint32_t qq[kEmPaths];
+#pragma unroll
+    for (int p = 0; p < kEmPaths; ++p) {
+        Y[p] = y0;
+        qq[p] = static_cast<uint32_t>(q0 + p * kEmThreads);   // a path past the end runs and is not stored
+    }
+    // whole blocks of four fine steps (one Philox call per path each), then the remainder
     const int n4 = n_fine >> 2;
     for (int k = 0; k < n4; ++k) {
-        const float4 z = normal4_fast(seed, 1u, static_cast<uint32_t>(r), static_cast<uint32_t>(q),
-                                      static_cast<uint32_t>(k));
-        step(z.x);
-        step(z.y);
-        step(z.z);
-        step(z.w);
+#pragma unroll
+        for (int p = 0; p < kEmPaths; ++p) {
+            const float4 z = normal4_fast(seed, 1u, static_cast<uint32_t>(r), qq[p], static_cast<uint32_t>(k));
+            step(Y[p], z.x);
+            step(Y[p], z.y);
+            step(Y[p], z.z);
+            step(Y[p], z.w);
+        }
     }
     if (n_fine & 3) {
-        const float4 z = normal4_fast(seed, 1u, static_cast<uint32_t>(r), static_cast<uint32_t>(q),
-                                      static_cast<uint32_t>(n4));
-        for (int u = 0; u < (n_fine & 3); ++u) step(pick4(z, u));
+#pragma unroll
+        for (int p = 0; p < kEmPaths; ++p) {
+            const float4 z = normal4_fast(seed, 1u, static_cast<uint32_t>(r), qq[p], static_cast<uint32_t>(n4));
+            for (int u = 0; u < (n_fine & 3); ++u) step(Y[p], pick4(z, u));
+        }
     }
-    if (SDE == SL_SDE_CIR) Y = fmaxf(Y, 0.0f);
-    out[static_cast<int64_t>(r) * n_paths + q] = Y;
+#pragma unroll
+    for (int p = 0; p < kEmPaths; ++p) {
+        const int64_t q = q0 + p * kEmThreads;
+        if (q < n_paths) out[static_cast<int64_t>(r) * n_paths + q] = (SDE == SL_SDE_CIR) ? fmaxf(Y[p], 0.0f) : Y[p];
+    }
 }
 
 struct RankList {
@@ -203,7 +221,7 @@ segmented_select_kernel(const float* __restrict__ values, const int64_t* __restr
 
 int launch_em(int sde, const float* theta, const float* Yi, const float* dt, int n_rows,
               int64_t n_paths, int n_fine, uint64_t seed, float* out, cudaStream_t st) {
-    const dim3 grid(static_cast<unsigned>((n_paths + kEmThreads - 1) / kEmThreads), n_rows);
+    const dim3 grid(static_cast<unsigned>((n_paths + kEmPaths * kEmThreads - 1) / (kEmPaths * kEmThreads)), n_rows);
     if (sde == SL_SDE_GBM)
         em_terminal_kernel<SL_SDE_GBM><<<grid, kEmThreads, 0, st>>>(theta, Yi, dt, n_paths, n_fine, seed, out);
     else if (sde == SL_SDE_OU)
