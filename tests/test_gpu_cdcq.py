@@ -259,6 +259,29 @@ def test_more_than_2_31_paths(sl, orc):
     del yt
 
 
+@pytest.mark.parametrize("model", [1, 2])
+def test_exact_models_many_entries(sl, orc, model):
+    """12,000 (set, step) entries with the exact maps (every CTA of the table kernel takes
+    several rounds): the tables and sampled paths against the oracle."""
+    n_sets, n_steps, m = 1000, 12, 7
+    rng = np.random.default_rng(43 + model)
+    counts = rng.integers(1, 4, n_sets)
+    off = W.offsets_from_counts(counts)
+    if model == 1:
+        th = rng.uniform([0.0, 0.1], [0.2, 0.5], (n_sets, 2)).astype(np.float32)
+        y0 = rng.uniform(0.8, 1.2, n_sets).astype(np.float32)
+    else:
+        th = rng.uniform([0.0, 0.1, 0.5], [1.0, 0.5, 2.0], (n_sets, 3)).astype(np.float32)
+        y0 = rng.uniform(-0.5, 1.5, n_sets).astype(np.float32)
+    r = _run(sl, model, None, th, y0, off, 3.0, n_steps, m, 5)
+    sets = np.concatenate([np.arange(30), np.arange(n_sets - 30, n_sets)])
+    zn, eta = orc.cdcq_tables(model, None, th, y0, 3.0, n_steps, m, sets=sets)
+    _tables_vs_oracle(r["tab"][sets], zn, eta, m)
+    idx = off[sets]
+    _check(orc, r["yt"][idx], orc.cdcq_paths(model, None, th, y0, off, 3.0, n_steps, m, 5, idx=idx), off, 5, n_steps,
+           1.0, idx=idx)
+
+
 def test_many_sets(sl, orc):
     """2^20 parameter sets with 0 or 1 path each, 3 steps, a network."""
     n_sets = 1 << 20
