@@ -224,6 +224,7 @@ static void lagrange_basis(int m, const double* xn, double X, double* l) {
  * Softplus), the output layer is linear.
  * ---------------------------------------------------------------------- */
 #define ORC_MAX_W 128
+#define ORC_MAX_DEG 16   /* polynomial degrees of the 7L-CDC inverse (m - 1 <= 15) */
 
 int64_t orc_n_params(int d_in, int width, int n_hidden, int m) {
     int64_t n = (int64_t)width * d_in + width;
@@ -900,11 +901,14 @@ int orc_cdc_paths(int model, const double* P, const double* Pm, int d_in, int wi
  * does not depend on xi_0 (taken as 0).  If the nodes at t_{i+1} all coincide,
  * G_{i+1} is constant: eta = 0 and Y_{i+1} = z^(i+1)_0.  G must increase from
  * its first to its last node (z_0 < z_{m-1}); the inverse inside the hull is
- * the first root of G(xi) = y in the first node interval [x_k, x_{k+1}] with
- * z_k <= y <= z_{k+1} (one exists whenever z_0 <= y <= z_{m-1}): the interval
- * is scanned at 32 equal steps for the first point where G >= y, and the root
- * in that cell is found by 60 bisections (for a G that increases, the one
- * root; a G that wiggles inside a node interval can cross y more than once).
+ * the smallest root of G(xi) = y in the first node interval [x_k, x_{k+1}]
+ * with z_k <= y <= z_{k+1} (one exists whenever z_0 <= y <= z_{m-1}).  For a
+ * G that increases it is the one root; a G that wiggles inside a node interval
+ * can cross y several times, and the definition takes the first crossing, at
+ * whatever distance the later ones lie.  It is found without any grid: the
+ * roots of G' split the interval into pieces on which G is monotone (Rolle),
+ * and the first piece on which G - y reaches zero holds the root, found there
+ * by bisection.
  * With the exact OU map (G linear, C affine in z and x_j) the chain equals the
  * 7L chain exactly.
  * ---------------------------------------------------------------------- */
@@ -917,9 +921,82 @@ double orc_cdcq_G(int m, const double* xn, const double* z, double xi) {
     return orc_lagrange(m, xn, z, xi);
 }
 
-/* G^{-1}(y): the continuation lines beyond [z_0, z_{m-1}], bisection inside;
- * NaN if G does not increase from its first to its last node; 0 if all nodes
- * coincide. */
+/* Monomial coefficients c[0..m-1] of the interpolant through (xn[k], z[k]):
+ * each Lagrange basis polynomial prod_{l != k} (xi - x_l) / (x_k - x_l)
+ * multiplied out, weighted by z_k and summed. */
+static void lagrange_monomials(int m, const double* xn, const double* z, double* c) {
+    for (int a = 0; a < m; ++a) c[a] = 0.0;
+    for (int k = 0; k < m; ++k) {
+        double b[ORC_MAX_DEG + 1] = {1.0}, den = 1.0;
+        int deg = 0;
+        for (int l = 0; l < m; ++l) {
+            if (l == k) continue;
+            b[deg + 1] = 0.0;
+            for (int a = deg + 1; a >= 1; --a) b[a] = b[a - 1] - xn[l] * b[a];
+            b[0] = -xn[l] * b[0];
+            ++deg;
+            den *= xn[k] - xn[l];
+        }
+        for (int a = 0; a < m; ++a) c[a] += z[k] * b[a] / den;
+    }
+}
+
+static double poly_at(int n, const double* c, double x) {
+    double v = 0.0;
+    for (int a = n; a >= 0; --a) v = v * x + c[a];
+    return v;
+}
+
+/* Bisection for the root of f on [lo, hi], given f(lo) < 0 < f(hi) or
+ * f(lo) > 0 > f(hi), until the midpoint no longer moves. */
+static double bisect_poly(int n, const double* c, double lo, double hi) {
+    const int neg_lo = poly_at(n, c, lo) < 0.0;
+    for (int it = 0; it < 2000; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if ((poly_at(n, c, mid) < 0.0) == neg_lo) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+/* The real roots in [a, b] of the degree-n polynomial c, ascending.  Between
+ * consecutive roots of the derivative the polynomial is monotone (Rolle), so
+ * each such piece holds at most one root: a piece end where it vanishes, or a
+ * sign change inside, found by bisection. */
+static int poly_roots_in(int n, const double* c, double a, double b, double* r) {
+    if (n <= 0) return 0;
+    if (n == 1) {
+        if (c[1] == 0.0) return 0;
+        double t = -c[0] / c[1];
+        if (t >= a && t <= b) { r[0] = t; return 1; }
+        return 0;
+    }
+    double d[ORC_MAX_DEG], cr[ORC_MAX_DEG], cut[ORC_MAX_DEG + 2];
+    for (int i = 1; i <= n; ++i) d[i - 1] = i * c[i];
+    int ncr = poly_roots_in(n - 1, d, a, b, cr), nc = 0, nr = 0;
+    cut[nc++] = a;
+    for (int i = 0; i < ncr; ++i)
+        if (cr[i] > cut[nc - 1] && cr[i] < b) cut[nc++] = cr[i];
+    cut[nc++] = b;
+    for (int s = 0; s + 1 < nc; ++s) {
+        double lo = cut[s], hi = cut[s + 1], flo = poly_at(n, c, lo), fhi = poly_at(n, c, hi);
+        double t;
+        if (flo == 0.0) t = lo;
+        else if (fhi != 0.0 && (flo < 0.0) != (fhi < 0.0)) t = bisect_poly(n, c, lo, hi);
+        else continue;
+        if (nr == 0 || t > r[nr - 1]) r[nr++] = t;
+    }
+    if (poly_at(n, c, b) == 0.0 && (nr == 0 || b > r[nr - 1])) r[nr++] = b;
+    return nr;
+}
+
+/* G^{-1}(y): the continuation lines beyond [z_0, z_{m-1}]; inside, the
+ * smallest root of G(xi) = y in the first node interval [x_k, x_{k+1}] with
+ * z_k <= y <= z_{k+1}.  G - y is negative at x_k (unless y = z_k, when x_k is
+ * the root) and not negative at x_{k+1}; the roots of G' cut the interval into
+ * monotone pieces, and the first piece whose far end has G - y >= 0 holds the
+ * root (bisection on G's plain Lagrange form).  NaN if G does not increase
+ * from its first to its last node; 0 if all nodes coincide. */
 double orc_cdcq_Ginv(int m, const double* xn, const double* z, double y) {
     int same = 1;
     for (int k = 1; k < m; ++k)
@@ -930,15 +1007,28 @@ double orc_cdcq_Ginv(int m, const double* xn, const double* z, double y) {
     if (y > z[m - 1]) return xn[m - 1] + (y - z[m - 1]) * (xn[m - 1] - xn[m - 2]) / (z[m - 1] - z[m - 2]);
     int k = 0;
     while (k < m - 2 && !(z[k] <= y && y <= z[k + 1])) ++k;
-    double h = (xn[k + 1] - xn[k]) / 32.0;
-    int c = 1;
-    while (c < 32 && orc_lagrange(m, xn, z, xn[k] + c * h) < y) ++c;
-    double lo = xn[k] + (c - 1) * h, hi = c < 32 ? xn[k] + c * h : xn[k + 1];
-    for (int it = 0; it < 60; ++it) {
-        double mid = 0.5 * (lo + hi);
-        if (orc_lagrange(m, xn, z, mid) < y) lo = mid; else hi = mid;
+    if (y == z[k]) return xn[k];
+    double c[ORC_MAX_DEG + 1], d[ORC_MAX_DEG], cr[ORC_MAX_DEG], cut[ORC_MAX_DEG + 2];
+    lagrange_monomials(m, xn, z, c);
+    for (int i = 1; i < m; ++i) d[i - 1] = i * c[i];
+    int ncr = poly_roots_in(m - 2, d, xn[k], xn[k + 1], cr), nc = 0;
+    cut[nc++] = xn[k];
+    for (int i = 0; i < ncr; ++i)
+        if (cr[i] > cut[nc - 1] && cr[i] < xn[k + 1]) cut[nc++] = cr[i];
+    cut[nc++] = xn[k + 1];
+    for (int s = 0; s + 1 < nc; ++s) {
+        double lo = cut[s], hi = cut[s + 1];
+        double fhi = (s + 2 == nc) ? z[k + 1] - y : orc_lagrange(m, xn, z, hi) - y;
+        if (fhi < 0.0) continue;              /* G - y < 0 on the whole piece */
+        if (fhi == 0.0) return hi;
+        for (int it = 0; it < 2000; ++it) {   /* G - y < 0 at lo, > 0 at hi */
+            double mid = 0.5 * (lo + hi);
+            if (mid <= lo || mid >= hi) break;
+            if (orc_lagrange(m, xn, z, mid) < y) lo = mid; else hi = mid;
+        }
+        return 0.5 * (lo + hi);
     }
-    return 0.5 * (lo + hi);
+    return xn[k + 1];                         /* not reached: G - y >= 0 at x_{k+1} */
 }
 
 /* sum_k sum_j eta[k*m + j] L_k(xi) L_j(X) (plain Lagrange definition) for xi in

@@ -6,6 +6,10 @@ conditional points are moved into the next step's coordinate by G_{i+1}^{-1}).
   (a quantile map) G^{-1} inverts it (G^{-1}(z_k) = x_k, G(G^{-1}(y)) = y inside and outside the
   range); a constant G inverts to 0 and a G that does not increase from its first to its last
   point to NaN.
+* Where G wiggles inside a node interval, G^{-1}(y) is the smallest root of G = y in the first
+  node interval that brackets y, however close the next crossings lie: a cubic that crosses y
+  twice within 1/32 of a node interval, and random wiggling interpolants, against numpy's
+  polynomial roots (companion-matrix eigenvalues) and a dense sign scan.
 * The bivariate interpolant reproduces every tensor-product polynomial of degree <= m-1 in each
   variable (numpy polyval), at and away from the nodes, for xi inside [x_0, x_{m-1}]; beyond, it
   is the line in xi through the two outermost node rows.
@@ -38,6 +42,78 @@ def test_G_and_inverse(orc, m):
     assert orc.cdcq_Ginv(z, lo) == pytest.approx(x[0] + (lo - z[0]) * (x[1] - x[0]) / (z[1] - z[0]), rel=1e-12)
     assert math.isnan(orc.cdcq_Ginv(z[::-1].copy(), 0.5))
     assert orc.cdcq_Ginv(np.full(m, 0.7), 3.0) == 0.0
+
+
+def _first_bracket(z, y):
+    k = 0
+    while k < len(z) - 2 and not (z[k] <= y <= z[k + 1]):
+        k += 1
+    return k
+
+
+def _smallest_root_numpy(x, z, y, k):
+    """Smallest real root of G - y in [x_k, x_{k+1}] from the companion-matrix eigenvalues of
+    the interpolating polynomial (numpy), polished by Newton in FP64."""
+    from numpy.polynomial import polynomial as Pn
+    c = Pn.polyfit(x, z, len(x) - 1)
+    c[0] -= y
+    r = Pn.polyroots(c)
+    r = r[np.abs(r.imag) < 1e-7].real
+    r = r[(r >= x[k] - 1e-9) & (r <= x[k + 1] + 1e-9)]
+    t = float(r.min())
+    dc = Pn.polyder(c)
+    for _ in range(3):
+        t -= Pn.polyval(t, c) / Pn.polyval(t, dc)
+    return t
+
+
+def test_inverse_takes_the_first_of_two_close_crossings(orc):
+    """G(xi) = y* + (xi - r1)(xi - r2)(xi - r3) through 4 Gauss-Hermite points: r1 and r2 lie in
+    the same 1/32 of the node interval [x_1, x_2], so G exceeds y* only between them and a
+    scan of that interval at 32 steps sees G < y* at every point before r3."""
+    x = hermite_e.hermegauss(4)[0]
+    r1, r2, r3, ys = 0.10, 0.135, 0.62, 20.0
+    z = ys + (x - r1) * (x - r2) * (x - r3)
+    assert z[0] < z[1] < ys < z[2] < z[3]
+    h = (x[2] - x[1]) / 32
+    c1, c2 = np.floor((r1 - x[1]) / h), np.floor((r2 - x[1]) / h)
+    assert c1 == c2                                 # both crossings inside one cell of the scan
+    scan = [orc.cdcq_G(z, x[1] + c * h) for c in range(33)]
+    assert all(v < ys for v in scan[: int(np.ceil((r3 - x[1]) / h))])
+    got = orc.cdcq_Ginv(z, ys)
+    assert got == pytest.approx(r1, abs=1e-12)
+    assert got == pytest.approx(_smallest_root_numpy(x, z, ys, 1), abs=1e-12)
+    # just above the bump's top the first crossing is r3's; just below r1's level, r1's
+    crit = np.roots(np.polyder(np.poly([r1, r2, r3])))
+    top = ys + float(np.polyval(np.poly([r1, r2, r3]), crit[(crit > r1) & (crit < r2)][0]))
+    assert orc.cdcq_Ginv(z, top + 1e-9) > r2
+    assert orc.cdcq_Ginv(z, ys - 1e-9) < r1
+
+
+@pytest.mark.parametrize("m", [4, 5, 7, 8])
+def test_inverse_of_wiggling_maps(orc, m):
+    """Random interpolants that increase from the first to the last node but wiggle between:
+    G^{-1}(y) is numpy's smallest root in the first bracketing interval, G(G^{-1}(y)) = y, and a
+    dense scan finds no crossing before it."""
+    from numpy.polynomial import polynomial as Pn
+    x = hermite_e.hermegauss(m)[0]
+    rng = np.random.default_rng(500 + m)
+    n_wiggly = 0
+    for trial in range(60):
+        z = np.cumsum(rng.uniform(-0.4, 1.0, size=m)) + rng.normal(size=m) * 0.3
+        if not z[-1] > z[0]:
+            continue
+        c = Pn.polyfit(x, z, m - 1)
+        for y in rng.uniform(z[0], z[-1], size=8):
+            k = _first_bracket(z, y)
+            got = orc.cdcq_Ginv(z, y)
+            assert x[k] <= got <= x[k + 1]
+            assert orc.cdcq_G(z, got) == pytest.approx(y, abs=1e-10 * (1 + abs(y)))
+            assert got == pytest.approx(_smallest_root_numpy(x, z, y, k), abs=1e-8)
+            g = Pn.polyval(np.linspace(x[k], got, 4001)[:-1], c)
+            assert np.all(g < y + 1e-12)
+            n_wiggly += int(np.any(np.diff(Pn.polyval(np.linspace(x[k], x[k + 1], 400), c)) < 0))
+    assert n_wiggly > 20                            # the sample does exercise non-monotone intervals
 
 
 @pytest.mark.parametrize("m", [2, 4, 7])
