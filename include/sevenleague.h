@@ -224,9 +224,9 @@ int sl_tc_get_pipeline(void);
  *     is the marginal collocation map of t_i; a path carries xi_i (xi_0 = 0)
  *     with Y_i = G_i(xi_i);
  *   - eta[k][j] = G_{i+1}^{-1}(C[k][j]) (beyond [z_0, z_{m-1}] the lines;
- *     inside, the first root in the first node interval [x_k, x_{k+1}] with
- *     z_k <= y <= z_{k+1}: the first of 32 equal cells of that interval where
- *     G reaches y, and the root in it); xi_{i+1} = sum_k sum_j eta[k][j]
+ *     inside, the smallest root of G = y in the first node interval
+ *     [x_k, x_{k+1}] with z_k <= y <= z_{k+1}, however close later crossings
+ *     lie; see sl_cdcq_inverse); xi_{i+1} = sum_k sum_j eta[k][j]
  *     L_k(xi_i) L_j(X) for xi_i in [x_0, x_{m-1}] (beyond, the line in xi
  *     through the two outermost node rows sum_j eta[k][j] L_j(X)),
  *     Gauss-Hermite points in both variables (as well conditioned as g_m);
@@ -279,6 +279,29 @@ int seven_league_cdc_simulate_batched(int model, const sl_net* net, const sl_net
                                       float T, int n_steps, int m, uint64_t seed, float* out_YT,
                                       float* out_grid, double* out_mean, double* out_var, void* ws,
                                       size_t ws_bytes, void* stream);
+
+/*
+ * G^{-1} of the quantile-coordinate 7L-CDC scheme (the step that moves the
+ * conditional points into the next step's coordinate, eta = G^{-1}(C)) on
+ * caller-given marginal nodes, by the table kernel's own device routine.
+ * zn: device FP32 [n_maps][m], the nodes z_k of each map G(xi) = sum_k z_k
+ * L_k(xi) through the Gauss-Hermite points (continued beyond them by the
+ * lines through the two outermost nodes); y: device FP64 [n_maps][n_y];
+ * out: device FP64 [n_maps][n_y], G^{-1}(y) of its row's map.  Inside
+ * [z_0, z_{m-1}] the result is the smallest root of G = y in the first node
+ * interval with z_k <= y <= z_{k+1}: the sign variations of the Bernstein
+ * coefficients (FP64) of G - y on that interval isolate it (one variation:
+ * one root; more: a left-first search over dyadic sub-intervals, down to
+ * 2^-40 of the interval, for the first with one), then it is refined in FP32
+ * and by one FP64 Newton step.  Roots closer together than 2^-40 of a node
+ * interval, and a G that comes within rounding of y without crossing it,
+ * are the cases where the choice can differ from the exact first root.
+ * Nodes that all coincide give 0; a G that does not increase from its
+ * first to its last node gives NaN.  Asynchronous on `stream`; allocates
+ * nothing.  SL_ERR_UNSUPPORTED for m outside [2, 8], SL_ERR_ARG for
+ * negative counts or NULL pointers, SL_ERR_CUDA if the launch fails.
+ */
+int sl_cdcq_inverse(int m, const float* zn, int n_maps, const double* y, int n_y, double* out, void* stream);
 
 /* ------------------------------------------------------------------------
  * Offline stage (Algorithm I, step 1).
@@ -338,8 +361,14 @@ int em_collocation_labels(int sde, const float* theta, const float* Yi, const fl
  *  - every call uses the same array, so calls whose work overlaps on the GPU
  *    (different streams, or different host threads) race; order them on one
  *    stream.  The array keeps the previous call's contents; the call clears
- *    its status word and overwrites every sample it reads.
- * Arguments, results and errors are otherwise those of em_collocation_labels.
+ *    its status word and overwrites every sample it reads;
+ *  - the device status word (SL_DEV_* bits: a negative segment length, a
+ *    non-finite sample) lives in the array, which no caller can address, so
+ *    those bits are not reported: a caller that needs them uses
+ *    em_collocation_labels with its own workspace and sl_workspace_status.
+ * Arguments are checked as em_collocation_labels checks them (SL_ERR_ARG,
+ * SL_ERR_UNSUPPORTED) before the size limit (SL_ERR_WORKSPACE); results and
+ * the other errors are those of em_collocation_labels.
  */
 int em_collocation_labels_noalloc(int sde, const float* theta, const float* Yi, const float* dt,
                                   int n_rows, int64_t n_paths, int n_fine, int m, uint64_t seed,

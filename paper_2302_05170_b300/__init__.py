@@ -48,6 +48,7 @@ EXPORTED = [
     "sl_mlp_forward", "sl_mse_grad", "sl_adam_step", "sl_train", "sl_adjoint_workspace_size",
     "seven_league_adjoint", "em_collocation_labels_noalloc", "sl_em_labels_noalloc_max_samples",
     "sl_selftest_wait_timeout", "sl_cdc_workspace_size", "seven_league_cdc_simulate_batched",
+    "sl_cdcq_inverse",
 ]
 
 
@@ -123,6 +124,7 @@ def load(path: str = LIB_PATH):
         _i, ctypes.POINTER(sl_net), ctypes.POINTER(sl_net), _i, _vp, _i, _vp, _vp, _i, _i64, _f, _i, _i, _u64,
         _vp, _vp, _vp, _vp, _vp, _sz, _vp]
     L.em_collocation_labels_noalloc.argtypes = [_i, _vp, _vp, _vp, _i, _i64, _i, _i, _u64, _vp, _vp]
+    L.sl_cdcq_inverse.argtypes = [_i, _vp, _i, _vp, _i, _vp, _vp]
     L.sl_em_labels_noalloc_max_samples.restype = _sz
     L.sl_tc_set_pipeline.argtypes = [_i]
     L.sl_tc_get_pipeline.restype = _i
@@ -315,6 +317,20 @@ def seven_league_cdc_simulate_batched(model, net, theta, Y0, path_offsets, T, n_
         _ptr(out_grid, torch.float32, "out_grid"), _ptr(out_mean, torch.float64, "out_mean"),
         _ptr(out_var, torch.float64, "out_var"), _ptr(ws), ws.numel(), _stream(stream)))
     return ws
+
+
+def cdcq_inverse(zn, y, out=None, stream=None):
+    """G^{-1} of the quantile-coordinate 7L-CDC scheme (see include/sevenleague.h): zn FP32
+    [n_maps, m] marginal nodes, y FP64 [n_maps, n_y]; returns FP64 [n_maps, n_y]."""
+    torch = _torch()
+    L = load()
+    n_maps, m = zn.shape
+    n_y = y.shape[1]
+    if out is None:
+        out = torch.empty((n_maps, n_y), dtype=torch.float64, device=zn.device)
+    _check(L.sl_cdcq_inverse(m, _ptr(zn, torch.float32, "zn"), n_maps, _ptr(y, torch.float64, "y"), n_y,
+                             _ptr(out, torch.float64, "out"), _stream(stream)))
+    return out
 
 
 def cdc_tables(ws, n_sets, n_steps):

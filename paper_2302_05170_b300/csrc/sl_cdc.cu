@@ -22,6 +22,9 @@
 // all FP32 ALU work.
 #include <math.h>
 
+#include <cstring>
+#include <mutex>
+
 #include "sl_check.cuh"
 #include "sl_fastnormal.cuh"
 #include "sl_internal.cuh"
@@ -66,6 +69,9 @@ struct CdcArgs {
     GHConst gh;
     double bq[SL_MAX_M][SL_MAX_M];   // b_j q_j[a]: monomial coefficients of b_j Q_j (FP64, zero past m)
     double xg[SL_MAX_M];             // the Gauss-Hermite points in FP64
+    // tb[k][i][l]: Bernstein coefficient i of the interpolant through (x_l, z_l) on node interval
+    // k, per unit of z_l (FP64): G_{i+1}'s coefficients are linear in its nodes
+    double tb[SL_MAX_M - 1][SL_MAX_M][SL_MAX_M];
 };
 
 // Collocation points of the exact models over the horizon h from Y:
@@ -376,17 +382,127 @@ size_t tableq_smem_bytes(int model) {
            static_cast<size_t>(kBatch) * (8 + 64 + 64) * sizeof(double) + static_cast<size_t>(kBatch) * sizeof(int);
 }
 
+// Bernstein coefficient i of G_{i+1} on the node interval [x_k, x_{k+1}] (n = m - 1,
+// G(x_k + h t) = sum_i bern[i] C(n, i) t^i (1 - t)^(n - i), h = x_{k+1} - x_k): linear in the
+// nodes, sum_l zn[l] tb[k][i][l] with tb from the host (FP64).  The end coefficients are G's
+// values at the nodes, set to the nodes themselves.
+__device__ __forceinline__ double interval_bernstein(const float* zn, const double (&tbk)[SL_MAX_M][SL_MAX_M],
+                                                    int m, int k, int i) {
+    if (i == 0) return zn[k];
+    if (i == m - 1) return zn[k + 1];
+    double acc = 0.0;
+#pragma unroll
+    for (int l = 0; l < SL_MAX_M; ++l)
+        if (l < m) acc = fma(static_cast<double>(zn[l]), tbk[i][l], acc);
+    return acc;
+}
+
+// Sign variations of c[0..n], zeros skipped: by the Bernstein form of Descartes' rule an upper
+// bound on the roots in the open interval, of the same parity, and exact when it is 0 or 1.
+__device__ __forceinline__ int sign_variations(const double (&c)[SL_MAX_M], int n) {
+    int v = 0, last = 0;
+#pragma unroll
+    for (int i = 0; i < SL_MAX_M; ++i) {
+        const int sg = i <= n ? (c[i] > 0.0) - (c[i] < 0.0) : 0;
+        if (sg != 0) {
+            if (last != 0 && sg != last) ++v;
+            last = sg;
+        }
+    }
+    return v;
+}
+
+// The Bernstein coefficients of the restriction of c (over [0, 1]) to [t0, t1]: de Casteljau at
+// t1 keeps the left part, then at t0 / t1 the right part of that.
+__device__ void bernstein_restrict(const double (&c)[SL_MAX_M], int n, double t0, double t1,
+                                   double (&out)[SL_MAX_M]) {
+    double w[SL_MAX_M], l[SL_MAX_M];
+#pragma unroll
+    for (int i = 0; i < SL_MAX_M; ++i) w[i] = c[i];
+    l[0] = w[0];
+#pragma unroll
+    for (int r = 1; r < SL_MAX_M; ++r) {
+#pragma unroll
+        for (int i = 0; i < SL_MAX_M - r; ++i)
+            if (i <= n - r) w[i] = fma(t1, w[i + 1] - w[i], w[i]);
+        l[r] = w[0];
+    }
+    const double s = t1 > 0.0 ? t0 / t1 : 0.0;
+#pragma unroll
+    for (int i = 0; i < SL_MAX_M; ++i) w[i] = l[i];
+#pragma unroll
+    for (int i = 0; i < SL_MAX_M; ++i)
+        if (i == n) out[i] = w[i];
+#pragma unroll
+    for (int r = 1; r < SL_MAX_M; ++r) {
+#pragma unroll
+        for (int i = 0; i < SL_MAX_M - r; ++i)
+            if (i <= n - r) w[i] = fma(s, w[i + 1] - w[i], w[i]);
+#pragma unroll
+        for (int i = 0; i < SL_MAX_M; ++i)
+            if (i == n - r) out[i] = w[i];
+    }
+}
+
+// The sub-interval [t0, t1] of [0, 1] that holds the smallest root of c = bern - y (Bernstein
+// coefficients over [0, 1], c[0] < 0):
+// depth-first over the dyadic intervals, left first, skipping those without a sign variation,
+// until one has exactly one (a single root inside) or a root sits at an end of one without
+// roots inside (t0 = t1).  Intervals still with two or more variations at depth kMaxDepth
+// (roots closer than 2^-kMaxDepth of the node interval, or a touch within rounding) end the
+// search there.  The visit count is bounded.  Only maps that wiggle inside a node interval
+// come here.
+constexpr int kMaxDepth = 40;
+__device__ __noinline__ void isolate_first_root(const double* bern, double y, int n, double& t0, double& t1) {
+    double c[SL_MAX_M];
+#pragma unroll
+    for (int i = 0; i < SL_MAX_M; ++i) c[i] = i <= n ? bern[i] - y : 0.0;
+    uint64_t idx = 0;                       // interval idx of depth d: [idx 2^-d, (idx + 1) 2^-d]
+    int d = 0;
+    double sub[SL_MAX_M];
+#pragma unroll 1
+    for (int visit = 0; visit < 16 * kMaxDepth; ++visit) {
+        const double w = ldexp(1.0, -d);
+        const double a = static_cast<double>(idx) * w, b = a + w;
+        bernstein_restrict(c, n, a, b, sub);
+        if (sub[0] == 0.0) { t0 = t1 = a; return; }
+        const int v = sign_variations(sub, n);
+        if (v == 1 || (v >= 2 && d == kMaxDepth)) { t0 = a; t1 = b; return; }
+        double last = 0.0;
+#pragma unroll
+        for (int i = 0; i < SL_MAX_M; ++i)
+            if (i == n) last = sub[i];
+        if (v == 0 && last == 0.0) { t0 = t1 = b; return; }   // no root inside, one at the right end
+        if (v >= 2) {                      // descend to the left child
+            ++d;
+            idx <<= 1;
+            continue;
+        }
+        while (d > 0 && (idx & 1)) {       // no root here: the next interval to the right
+            idx >>= 1;
+            --d;
+        }
+        if (d == 0) break;
+        ++idx;
+    }
+    t0 = 0.0;                               // not reached for c[0] < 0 <= c[n]
+    t1 = 1.0;
+}
+
 // G_{i+1}^{-1}(y) (flag 1: the nodes coincide, 0; flag 2: G does not increase from its
 // first to its last node, NaN).  Beyond [zn_0, zn_{m-1}] the lines through the two
-// outermost nodes; inside, the first root in the first node interval [x_k, x_{k+1}] with
-// zn_k <= y <= zn_{k+1}: the interval is scanned at 32 equal steps for the first point
-// where G >= y (FP32), the root in that cell is refined by Newton in FP32 (bisecting
-// whenever a step leaves the cell that brackets it, 8 steps), then by one Newton step on
-// the FP64 coefficients (the residual in FP64, the derivative's reciprocal in FP32: the
-// step is ~1e-7 of the root, so its own 1e-7 error is below FP64 rounding), clamped to the
-// cell (the root may be one of its ends).
-__device__ double quantile_inverse(const float* zn, const float* g32, const double* g64, const double* xg, int m,
-                                   int flag, double y) {
+// outermost nodes; inside, the smallest root of G = y in the first node interval
+// [x_k, x_{k+1}] with zn_k <= y <= zn_{k+1}.  The sign variations of G - y's Bernstein
+// coefficients on that interval (bern: FP64, per entry and interval) isolate it: one variation
+// means one root in the whole interval; more (G wiggles) start a left-first search for the
+// first sub-interval with one.  Inside that bracket, where G - y < 0 left of the root and > 0
+// right of it: a scan at 32 equal steps for the first point where G >= y (FP32), Newton in FP32
+// in that cell (bisecting whenever a step leaves it, 8 steps), then Newton steps on the FP64
+// coefficients (residual and derivative in FP64, the derivative's reciprocal in FP32: each step
+// then carries a relative error of ~1e-7 of itself), kept inside the bracket, until a step moves
+// the root by less than 2^-22 of its size (at most four).
+__device__ double quantile_inverse(const float* zn, const float* g32, const double* g64, const double* bern,
+                                   const double* xg, int m, int flag, double y) {
     if (flag == 1) return 0.0;
     if (flag == 2) return __longlong_as_double(0x7ff8000000000000LL);
     const double z0 = zn[0], z1 = zn[1], zl = zn[m - 1], zl1 = zn[m - 2];
@@ -394,17 +510,32 @@ __device__ double quantile_inverse(const float* zn, const float* g32, const doub
     if (y > zl) return xg[m - 1] + (y - zl) * (xg[m - 1] - xg[m - 2]) / (zl - zl1);
     int k = 0;
     while (k < m - 2 && !(static_cast<double>(zn[k]) <= y && y <= static_cast<double>(zn[k + 1]))) ++k;
+    if (y == static_cast<double>(zn[k])) return xg[k];
+    const int n = m - 1;
+    double c[SL_MAX_M];
+#pragma unroll
+    for (int i = 0; i < SL_MAX_M; ++i) c[i] = i <= n ? bern[k * 8 + i] - y : 0.0;
+    double blo = xg[k], bhi = xg[k + 1];
+    const int v = sign_variations(c, n);
+    if (v == 0) return xg[k + 1];            // G - y < 0 up to x_{k+1}, where it is 0
+    if (v >= 2) {
+        double t0, t1;
+        isolate_first_root(bern + k * 8, y, n, t0, t1);
+        const double h = xg[k + 1] - xg[k];
+        blo = xg[k] + t0 * h;
+        bhi = xg[k] + t1 * h;
+        if (t0 == t1) return blo;
+    }
     const float yf = static_cast<float>(y);
-    auto g32at = [&](float v) {
+    auto g32at = [&](float u) {
         float gv = g32[m - 1];
-        for (int ai = m - 2; ai >= 0; --ai) gv = fmaf(gv, v, g32[ai]);
+        for (int ai = m - 2; ai >= 0; --ai) gv = fmaf(gv, u, g32[ai]);
         return gv;
     };
-    const double h = (xg[k + 1] - xg[k]) / 32.0;
-    int c = 1;
-    while (c < 32 && g32at(static_cast<float>(xg[k] + c * h)) < yf) ++c;
-    const double dlo = xg[k] + (c - 1) * h, dhi = c < 32 ? xg[k] + c * h : xg[k + 1];
-    float lo = static_cast<float>(dlo), hi = static_cast<float>(dhi);
+    const double h = (bhi - blo) / 32.0;
+    int cc = 1;
+    while (cc < 32 && g32at(static_cast<float>(blo + cc * h)) < yf) ++cc;
+    float lo = static_cast<float>(blo + (cc - 1) * h), hi = static_cast<float>(cc < 32 ? blo + cc * h : bhi);
     float xi = 0.5f * (lo + hi);
     for (int it = 0; it < 8; ++it) {
         float gv = g32[m - 1], gd = 0.0f;
@@ -418,15 +549,24 @@ __device__ double quantile_inverse(const float* zn, const float* g32, const doub
         if (!(nx > lo && nx < hi)) nx = 0.5f * (lo + hi);
         xi = nx;
     }
-    double x = xi;
-    double gv = g64[m - 1];
-    float gd = 0.0f;
-    for (int ai = m - 2; ai >= 0; --ai) {
-        gd = fmaf(gd, static_cast<float>(x), static_cast<float>(gv));
-        gv = fma(gv, x, g64[ai]);
+    double x = fmin(fmax(static_cast<double>(xi), blo), bhi);
+    for (int it = 0; it < 4; ++it) {
+        double gv = g64[m - 1], gd = 0.0;
+        for (int ai = m - 2; ai >= 0; --ai) {
+            gd = fma(gd, x, gv);
+            gv = fma(gv, x, g64[ai]);
+        }
+        const float gdf = static_cast<float>(gd);
+        if (gdf == 0.0f) break;
+        const double nx = fmin(fmax(x - (gv - y) * static_cast<double>(__frcp_rn(gdf)), blo), bhi);
+        // Newton converges quadratically: after a step of 2^-22 of the root or less, the next
+        // would move it by ~|G''/G'| 2^-44 (FP64 is slow here: a warp's FP64 FMA holds the unit
+        // for tens of cycles, so the refinement stops as soon as it can)
+        const bool done = fabs(nx - x) <= 0x1p-22 * (1.0 + fabs(x));
+        x = nx;
+        if (done) break;
     }
-    const double nx = (gd != 0.0f) ? x - (gv - y) * static_cast<double>(__frcp_rn(gd)) : x;
-    return fmin(fmax(nx, dlo), dhi);      // the root lies in the cell (it may be an end)
+    return x;
 }
 
 template <int MODEL, int ACT, int MACT>
@@ -442,6 +582,7 @@ __global__ void __launch_bounds__(kTabThreads, 2) cdcq_table_kernel(const CdcArg
     double* g64 = reinterpret_cast<double*>(ths + kBatch * 8);   // [kBatch][8] coefficients of G_{i+1}
     double* e64 = g64 + kBatch * 8;                // [kBatch][8][8] eta
     double* r64 = e64 + kBatch * 64;               // [kBatch][8][8] node rows: sum_j eta[k][j] bq[j][b]
+                                                   // (before C3: G's Bernstein coefficients per node interval)
     int* flag = reinterpret_cast<int*>(r64 + kBatch * 64);       // [kBatch]
     const bool one_net = a.mparams == a.params;
     if (MODEL == SL_MODEL_MLP) {
@@ -524,6 +665,14 @@ __global__ void __launch_bounds__(kTabThreads, 2) cdcq_table_kernel(const CdcArg
             }
         }
         __syncthreads();
+        // (C1b) thread (e, k, i): Bernstein coefficient i of G_{i+1} on node interval k (kept in
+        // the space of the node rows, which are formed only after C2)
+        if (threadIdx.x < kBatch * 56) {
+            const int e = threadIdx.x / 56, k = (threadIdx.x / 8) % 7, ci = threadIdx.x % 8;
+            if (base + e < n && flag[e] == 0 && k < m - 1 && ci < m)
+                r64[e * 64 + k * 8 + ci] = interval_bernstein(zns + e * 8, a.tb[k], m, k, ci);
+        }
+        __syncthreads();
         // (C2) thread (e, k, j): eta[k][j] = G_{i+1}^{-1}(C[k][j])
         {
             const int e = threadIdx.x / 64, k = (threadIdx.x / 8) % 8, j = threadIdx.x % 8;
@@ -532,7 +681,8 @@ __global__ void __launch_bounds__(kTabThreads, 2) cdcq_table_kernel(const CdcArg
                 double v = 0.0;
                 if (k < m && j < m) {
                     float* t = a.tab + u * kTabFloats;
-                    v = quantile_inverse(zns + e * 8, t + kQGm, g64 + e * 8, a.xg, m, flag[e], Cs[e * 64 + k * 8 + j]);
+                    v = quantile_inverse(zns + e * 8, t + kQGm, g64 + e * 8, r64 + e * 64, a.xg, m, flag[e],
+                                         Cs[e * 64 + k * 8 + j]);
                 }
                 e64[e * 64 + k * 8 + j] = v;
                 a.tab[u * kTabFloats + kQEta + k * 8 + j] = static_cast<float>(v);
@@ -567,6 +717,52 @@ __global__ void __launch_bounds__(kTabThreads, 2) cdcq_table_kernel(const CdcArg
                     for (int z = kQR + 32; z < kTabFloats; ++z) t[z] = 0.0f;
                 }
             }
+        }
+        __syncthreads();
+    }
+}
+
+// G^{-1} on caller-given marginal nodes: the table kernel's own steps C1, C1b and C2 for one
+// node set per CTA (monomial coefficients of G in FP64 and FP32, Bernstein coefficients per
+// node interval, then quantile_inverse for each requested y).
+struct InvArgs {
+    const float* zn;     // [n_maps][m]
+    const double* y;     // [n_maps][n_y]
+    double* out;         // [n_maps][n_y]
+    int n_maps, n_y, m;
+    double bq[SL_MAX_M][SL_MAX_M];
+    double xg[SL_MAX_M];
+    double tb[SL_MAX_M - 1][SL_MAX_M][SL_MAX_M];
+};
+
+__global__ void __launch_bounds__(128) cdcq_inverse_kernel(const InvArgs a) {
+    __shared__ float zs[8], g32[8];
+    __shared__ double g64[8], bern[64];
+    __shared__ int flag;
+    const int m = a.m;
+    for (int map = blockIdx.x; map < a.n_maps; map += gridDim.x) {
+        if (threadIdx.x < 8) zs[threadIdx.x] = threadIdx.x < m ? a.zn[static_cast<int64_t>(map) * m + threadIdx.x] : 0.0f;
+        __syncthreads();
+        if (threadIdx.x < 8) {
+            double acc = 0.0;
+            for (int k = 0; k < m; ++k) acc += static_cast<double>(zs[k]) * a.bq[k][threadIdx.x];
+            g64[threadIdx.x] = acc;
+            g32[threadIdx.x] = static_cast<float>(acc);
+        }
+        if (threadIdx.x == 0) {
+            bool same = true;
+            for (int k = 1; k < m; ++k) same = same && zs[k] == zs[0];
+            flag = same ? 1 : (zs[m - 1] > zs[0] ? 0 : 2);
+        }
+        __syncthreads();
+        if (threadIdx.x < 56 && flag == 0) {
+            const int k = threadIdx.x / 8, ci = threadIdx.x % 8;
+            if (k < m - 1 && ci < m) bern[k * 8 + ci] = interval_bernstein(zs, a.tb[k], m, k, ci);
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < a.n_y; j += blockDim.x) {
+            const int64_t o = static_cast<int64_t>(map) * a.n_y + j;
+            a.out[o] = quantile_inverse(zs, g32, g64, bern, a.xg, m, flag, a.y[o]);
         }
         __syncthreads();
     }
@@ -890,6 +1086,64 @@ int gh_monomials(int m, double (&bq)[SL_MAX_M][SL_MAX_M], double (&xg)[SL_MAX_M]
     return SL_OK;
 }
 
+// tb[k][i][l]: Bernstein coefficient i, on node interval k ([x_k, x_{k+1}] mapped to [0, 1]), of
+// the Lagrange basis polynomial L_l through the FP64 Gauss-Hermite points (zero past m): the
+// monomial coefficients of L_l (bq[l][a] / b_l times b_l, i.e. bq[l]), a Taylor shift to x_k,
+// the powers of h = x_{k+1} - x_k, then bern_i = sum_{j <= i} C(i, j) / C(n, j) q_j.
+void interval_tables(int m, const double (&bq)[SL_MAX_M][SL_MAX_M], const double (&xg)[SL_MAX_M],
+                     double (&tb)[SL_MAX_M - 1][SL_MAX_M][SL_MAX_M]) {
+    const int n = m - 1;
+    double binom[SL_MAX_M][SL_MAX_M] = {};
+    for (int i = 0; i < SL_MAX_M; ++i) {
+        binom[i][0] = 1.0;
+        for (int j = 1; j <= i; ++j) binom[i][j] = binom[i - 1][j - 1] + (j < i ? binom[i - 1][j] : 0.0);
+    }
+    for (int k = 0; k < SL_MAX_M - 1; ++k)
+        for (int i = 0; i < SL_MAX_M; ++i)
+            for (int l = 0; l < SL_MAX_M; ++l) tb[k][i][l] = 0.0;
+    for (int k = 0; k < n; ++k) {
+        const double x0 = xg[k], h = xg[k + 1] - xg[k];
+        for (int l = 0; l < m; ++l) {
+            double q[SL_MAX_M];
+            for (int a = 0; a < m; ++a) q[a] = bq[l][a];      // sum_l z_l bq[l][a]: G's coefficients
+            for (int i = 0; i < n; ++i)
+                for (int j = n - 1; j >= i; --j) q[j] += x0 * q[j + 1];
+            double hp = 1.0;
+            for (int j = 0; j <= n; ++j) {
+                q[j] *= hp;
+                hp *= h;
+            }
+            for (int i = 0; i <= n; ++i) {
+                double acc = 0.0;
+                for (int j = 0; j <= i; ++j) acc += binom[i][j] / binom[n][j] * q[j];
+                tb[k][i][l] = acc;
+            }
+        }
+    }
+}
+
+// The per-m host constants of the tables (bq, xg, tb), computed once per m and copied out.
+int cdc_host_tables(int m, double (&bq)[SL_MAX_M][SL_MAX_M], double (&xg)[SL_MAX_M],
+                    double (&tb)[SL_MAX_M - 1][SL_MAX_M][SL_MAX_M]) {
+    struct Entry {
+        std::once_flag once;
+        int rc = SL_ERR_UNSUPPORTED;
+        double bq[SL_MAX_M][SL_MAX_M], xg[SL_MAX_M], tb[SL_MAX_M - 1][SL_MAX_M][SL_MAX_M];
+    };
+    static Entry cache[SL_MAX_M + 1];
+    if (m < SL_MIN_M || m > SL_MAX_M) return set_error(SL_ERR_UNSUPPORTED, "m=%d", m);
+    Entry& e = cache[m];
+    std::call_once(e.once, [&] {
+        e.rc = gh_monomials(m, e.bq, e.xg);
+        if (e.rc == SL_OK) interval_tables(m, e.bq, e.xg, e.tb);
+    });
+    if (e.rc != SL_OK) return set_error(e.rc, "Gauss-Hermite points for m=%d", m);
+    memcpy(bq, e.bq, sizeof(bq));
+    memcpy(xg, e.xg, sizeof(xg));
+    memcpy(tb, e.tb, sizeof(tb));
+    return SL_OK;
+}
+
 size_t table_bytes(int n_sets, int n_steps) {
     return align256(static_cast<size_t>(n_sets) * static_cast<size_t>(n_steps) * kTabFloats * sizeof(float));
 }
@@ -966,7 +1220,7 @@ int seven_league_cdc_simulate_batched(int model, const sl_net* net, const sl_net
     c.tab = tab;
     rc = make_gh_const(m, &c.gh);
     if (rc) return rc;
-    rc = gh_monomials(m, c.bq, c.xg);
+    rc = cdc_host_tables(m, c.bq, c.xg, c.tb);
     if (rc) return rc;
 
     SimArgs a{};
@@ -998,6 +1252,25 @@ int seven_league_cdc_simulate_batched(int model, const sl_net* net, const sl_net
     }
     if (moments) return launch_set_moments(yt, path_offsets, n_sets, total_paths, out_mean, out_var, part, st);
     return SL_OK;
+}
+
+int sl_cdcq_inverse(int m, const float* zn, int n_maps, const double* y, int n_y, double* out, void* stream) {
+    if (m < SL_MIN_M || m > SL_MAX_M) return set_error(SL_ERR_UNSUPPORTED, "m=%d outside [%d,%d]", m, SL_MIN_M, SL_MAX_M);
+    if (n_maps < 0 || n_y < 0) return set_error(SL_ERR_ARG, "n_maps=%d n_y=%d", n_maps, n_y);
+    if (n_maps == 0 || n_y == 0) return SL_OK;
+    if (!zn || !y || !out) return set_error(SL_ERR_ARG, "zn / y / out == NULL");
+    InvArgs a{};
+    a.zn = zn;
+    a.y = y;
+    a.out = out;
+    a.n_maps = n_maps;
+    a.n_y = n_y;
+    a.m = m;
+    int rc = cdc_host_tables(m, a.bq, a.xg, a.tb);
+    if (rc) return rc;
+    const int grid = n_maps < 65535 ? n_maps : 65535;
+    cdcq_inverse_kernel<<<grid, 128, 0, static_cast<cudaStream_t>(stream)>>>(a);
+    return cuda_error(cudaGetLastError(), "cdcq_inverse launch");
 }
 
 }  // extern "C"

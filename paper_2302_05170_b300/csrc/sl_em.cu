@@ -231,6 +231,18 @@ int launch_em(int sde, const float* theta, const float* Yi, const float* dt, int
     return cuda_error(cudaGetLastError(), "em_terminal launch");
 }
 
+int launch_select(const float* values, const int64_t* seg_off, int64_t uniform_len, int n_seg,
+                  const int64_t* ranks, int n_k, float* out, unsigned* status, cudaStream_t st) {
+    RankList rl{};
+    rl.n = n_k;
+    for (int j = 0; j < n_k; ++j) rl.r[j] = ranks[j];
+    segmented_select_kernel<<<n_seg, kSelThreads, 0, st>>>(values, seg_off, uniform_len, rl, out, status);
+    return cuda_error(cudaGetLastError(), "segmented_select launch");
+}
+
+}  // namespace
+
+// Argument checks shared by the label entry points (also the allocation-free one).
 int check_em_args(int sde, const float* theta, const float* Yi, const float* dt, int n_rows,
                   int64_t n_paths, int n_fine) {
     if (sde != SL_SDE_GBM && sde != SL_SDE_OU && sde != SL_SDE_CIR)
@@ -243,16 +255,6 @@ int check_em_args(int sde, const float* theta, const float* Yi, const float* dt,
     return SL_OK;
 }
 
-int launch_select(const float* values, const int64_t* seg_off, int64_t uniform_len, int n_seg,
-                  const int64_t* ranks, int n_k, float* out, unsigned* status, cudaStream_t st) {
-    RankList rl{};
-    rl.n = n_k;
-    for (int j = 0; j < n_k; ++j) rl.r[j] = ranks[j];
-    segmented_select_kernel<<<n_seg, kSelThreads, 0, st>>>(values, seg_off, uniform_len, rl, out, status);
-    return cuda_error(cudaGetLastError(), "segmented_select launch");
-}
-
-}  // namespace
 }  // namespace sl
 
 using namespace sl;

@@ -31,6 +31,9 @@ struct GHConst {
     float doff[SL_MAX_M];   // (0, 1) for the unused nodes j >= m (a factor 1 in every product)
 };
 int make_gh_const(int m, GHConst* out);
+// Euler-Maruyama label arguments (sde, pointers, sizes): SL_OK or the error code.
+int check_em_args(int sde, const float* theta, const float* Yi, const float* dt, int n_rows, int64_t n_paths,
+                  int n_fine);
 
 // ---------------------------------------------------------------------------
 // Device side

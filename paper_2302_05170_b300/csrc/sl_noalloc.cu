@@ -62,7 +62,14 @@ size_t sl_em_labels_noalloc_max_samples(void) { return (kNoAllocBytes - kStatusB
 int em_collocation_labels_noalloc(int sde, const float* theta, const float* Yi, const float* dt, int n_rows,
                                   int64_t n_paths, int n_fine, int m, uint64_t seed, float* labels,
                                   void* stream) {
-    if (n_rows < 0 || n_paths < 1) return set_error(SL_ERR_ARG, "n_rows < 0 or n_paths < 1");
+    // the arguments first, as em_collocation_labels checks them, then the buffer's size
+    int rc = check_em_args(sde, theta, Yi, dt, n_rows, n_paths, n_fine);
+    if (rc) return rc;
+    if (!labels) return set_error(SL_ERR_ARG, "labels == NULL");
+    if (n_paths < 1) return set_error(SL_ERR_ARG, "n_paths < 1");
+    int64_t ranks[SL_MAX_M];
+    rc = sl_quantile_ranks(m, n_paths, ranks);
+    if (rc) return rc;
     const size_t need = sl_em_labels_workspace_size(n_rows, n_paths, m);
     if (need > kNoAllocBytes)
         return set_error(SL_ERR_WORKSPACE,
@@ -70,7 +77,7 @@ int em_collocation_labels_noalloc(int sde, const float* theta, const float* Yi, 
                          "use em_collocation_labels with a caller workspace",
                          static_cast<long long>(n_rows) * n_paths, sl_em_labels_noalloc_max_samples());
     void* ws = nullptr;
-    const int rc = noalloc_address(&ws);
+    rc = noalloc_address(&ws);
     if (rc) return rc;
     // em_collocation_labels clears the status word and overwrites every sample it reads.
     return em_collocation_labels(sde, theta, Yi, dt, n_rows, n_paths, n_fine, m, seed, labels, ws,

@@ -14,6 +14,11 @@ Horner evaluations against FP64 on the same normals: a few 1e-7 per step over up
 * Networks (ReLU, Softplus, a separate marginal network): the tables -- nodes of t_{i+1},
   G's coefficients and edges, eta against the oracle's, B from the kernel's own eta -- and the
   paths; a network whose marginal points decrease gives NaN paths (SL_DEV_NONFINITE).
+* G^{-1} (sl_cdcq_inverse, the table kernel's routine) against the oracle's smallest root in
+  the first bracketing node interval: a cubic that crosses y twice within 1/32 of a node
+  interval, random wiggling maps (m = 4..8), monotone maps, values at and beyond the nodes,
+  coinciding and decreasing nodes; and in the tables, with a hand-built network that puts a
+  conditional point on that double crossing.
 * Degenerate laws (sigma = 0), ragged and empty sets, one step, batch independence
   (bit-exact), CUDA graph replay, FP64 set moments, the 16 x 1e6 x 16 workload on sampled paths,
   m = 2..8, 2^31 + 129 paths in one set, 2^20 sets.
@@ -296,3 +301,84 @@ def test_many_sets(sl, orc):
     idx = off[sets]
     _check(orc, r["yt"][idx], orc.cdcq_paths(0, P, th, y0, off, 1.0, 3, 7, 4, d_in=4, idx=idx), off, 4, 3, 1.0, idx=idx)
     assert np.array_equal(r["mean"][sets], r["yt"][idx].astype(np.float64)) and np.all(r["mean"][counts == 0] == 0)
+
+
+def _double_crossing_nodes():
+    """Nodes of G(xi) = 20 + (xi - 0.1)(xi - 0.135)(xi - 0.62) at the 4 Gauss-Hermite points:
+    G exceeds 20 only on (0.1, 0.135), inside one 1/32 of the node interval [x_1, x_2]."""
+    from numpy.polynomial import hermite_e
+    x = hermite_e.hermegauss(4)[0]
+    return (20.0 + (x - 0.1) * (x - 0.135) * (x - 0.62)).astype(np.float32)
+
+
+def test_inverse_first_of_two_close_crossings(sl, orc):
+    z = _double_crossing_nodes()
+    ys = np.array([[20.0, 20.0 - 1e-5, 19.5, 20.5, float(z[1]), float(z[2]), float(z[0]) - 1.0, float(z[3]) + 3.0]])
+    got = sl.cdcq_inverse(_dev(z[None, :]), _dev(ys, torch.float64)).cpu().numpy()[0]
+    want = np.array([orc.cdcq_Ginv(z.astype(np.float64), y) for y in ys[0]])
+    assert abs(want[0] - 0.1) < 1e-5 and abs(got[0] - 0.1) < 1e-5      # the first crossing, not 0.62
+    assert np.allclose(got, want, rtol=0, atol=1e-9), (got, want)
+
+
+@pytest.mark.parametrize("m", [4, 5, 6, 7, 8])
+def test_inverse_of_wiggling_maps(sl, orc, m):
+    """Random FP32 node sets that increase from first to last but wiggle between, 64 values of y
+    each inside and around the range: the kernel's G^{-1} against the oracle's."""
+    rng = np.random.default_rng(900 + m)
+    zs, n_maps = [], 0
+    while n_maps < 200:
+        z = (np.cumsum(rng.uniform(-0.4, 1.0, size=m)) + rng.normal(size=m) * 0.3).astype(np.float32)
+        if z[-1] > z[0]:
+            zs.append(z)
+            n_maps += 1
+    zs = np.array(zs)
+    ys = np.concatenate([rng.uniform(zs[:, :1] - 0.5, zs[:, -1:] + 0.5, size=(n_maps, 56)),
+                         zs[:, :m].astype(np.float64), np.zeros((n_maps, 8 - m))], axis=1)
+    ys = ys[:, :64]
+    got = sl.cdcq_inverse(_dev(zs), _dev(ys, torch.float64)).cpu().numpy()
+    want = np.array([[orc.cdcq_Ginv(zs[i].astype(np.float64), y) for y in ys[i]] for i in range(n_maps)])
+    err = np.abs(got - want)
+    print("max |xi - oracle|:", err.max())
+    assert err.max() <= 1e-9
+
+
+def test_inverse_degenerate_maps(sl, orc):
+    zs = np.array([[0.7, 0.7, 0.7, 0.7, 0.7], [2.0, 1.0, 0.5, 0.2, 0.1], [0.0, 0.5, 1.0, 1.5, 2.0]], np.float32)
+    ys = np.array([[3.0, 0.7], [0.5, 1.0], [0.75, 2.5]])
+    got = sl.cdcq_inverse(_dev(zs), _dev(ys, torch.float64)).cpu().numpy()
+    assert np.array_equal(got[0], [0.0, 0.0]) and np.all(np.isnan(got[1]))
+    want = [orc.cdcq_Ginv(zs[2].astype(np.float64), y) for y in ys[2]]
+    assert np.allclose(got[2], want, rtol=0, atol=1e-12)
+
+
+def _passthrough_net(m, d_in, a, b5):
+    """H_j(Y, .) = b5_j + a_j max(Y, 0): unit 0 of every hidden layer carries Y, the rest are 0."""
+    P = np.zeros(sum([50 * d_in + 50] + [50 * 50 + 50] * 3 + [m * 50 + m]), np.float32)
+    off = 0
+    P[off + 0] = 1.0                       # W1[0][0]: the Y feature
+    off += 50 * d_in + 50
+    for _ in range(3):
+        P[off + 0] = 1.0                   # W_l[0][0]
+        off += 50 * 50 + 50
+    for j in range(m):
+        P[off + j * 50] = a[j]             # W5[j][0]
+    P[off + m * 50:off + m * 50 + m] = b5
+    return P
+
+
+def test_tables_take_the_first_of_two_close_crossings(sl, orc):
+    """A network with H_j(Y) = b5_j + a_j Y (Y > 0): the marginal nodes of every t_i > 0 are the
+    double-crossing nodes z, and the conditional point C[3][1] = H_1(z_3) = 20, so at step 1
+    eta[3][1] = G^{-1}(20) must be the first crossing (0.1), as in the oracle."""
+    m, d_in, y0 = 4, 3, 1.0
+    z = _double_crossing_nodes().astype(np.float64)
+    a = np.zeros(m)
+    a[1] = (20.0 - z[1]) / (z[3] - y0)
+    b5 = z - a * y0
+    P = _passthrough_net(m, d_in, a.astype(np.float32), b5.astype(np.float32))
+    th, y0s, off = [[0.0]], [y0], W.offsets_from_counts([256])
+    r = _run(sl, 0, sl.make_net(_dev(P), d_in, m), th, y0s, off, 1.0, 2, m, 3)
+    zn, eta = orc.cdcq_tables(0, P, th, y0s, 1.0, 2, m, d_in=d_in)
+    ge = r["tab"][0, 1, 24:88].reshape(8, 8)[:m, :m].astype(np.float64)
+    assert abs(eta[0, 1, 3, 1] - 0.1) < 1e-3 and abs(ge[3, 1] - 0.1) < 1e-3
+    assert np.abs(ge - eta[0, 1]).max() <= 1e-3          # y moves by an FP32 rounding, xi by ~1/G'

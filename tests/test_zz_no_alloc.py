@@ -5,8 +5,11 @@ allocator, or the memory budget is fixed up front) use
 em_collocation_labels_noalloc, which runs on the library's own fixed device
 buffer instead of a caller workspace.  Checked here through the C ABI: two
 calls in a row give the labels of em_collocation_labels (the existing entry
-point, with a caller workspace) within the labels tests' tolerance (1e-5
-relative), and sizes beyond the buffer are rejected before any work.
+point, with a caller workspace) bit for bit -- the same kernels on the same
+inputs -- and so does a third call after a call of the same size with another
+seed has overwritten every sample of the shared buffer; sizes beyond the
+buffer are rejected before any work, and bad arguments with the argument
+errors of em_collocation_labels, not with the size error.
 
 This file is collected last on purpose: it is independent of the other GPU
 tests and passes alone in a fresh process as well as after them.
@@ -29,19 +32,18 @@ def test_noalloc_matches_workspace_entry_point(sl):
     th, yi, dt = W.cir_label_rows(24, seed=21)
     n_paths, n_fine, m = 50_000, 100, 7
     assert 24 * n_paths <= sl.em_labels_noalloc_max_samples()
-    ref = sl.em_collocation_labels(2, _dev(th), _dev(yi), _dev(dt), n_paths, n_fine, m, 5).cpu().numpy()
+    args = (_dev(th), _dev(yi), _dev(dt), n_paths, n_fine, m)
+    ref = sl.em_collocation_labels(2, *args, 5).cpu().numpy()
     for _ in range(2):   # the shared buffer keeps the previous call's contents
-        got = sl.em_collocation_labels_noalloc(2, _dev(th), _dev(yi), _dev(dt), n_paths, n_fine, m, 5)
+        got = sl.em_collocation_labels_noalloc(2, *args, 5)
         torch.cuda.synchronize()
-        got = got.cpu().numpy()
-        scale = np.maximum(th[:, 1], yi)[:, None]
-        assert np.all(np.abs(got - ref) <= TOL * (np.abs(ref) + scale))
-    # a different problem in between, then the first one again
-    th2, yi2, dt2 = W.cir_label_rows(3, seed=22)
-    other = sl.em_collocation_labels_noalloc(1, _dev(th2), _dev(yi2), _dev(dt2), 1000, 10, 5, 9).cpu().numpy()
-    assert np.all(np.isfinite(other))
-    again = sl.em_collocation_labels_noalloc(2, _dev(th), _dev(yi), _dev(dt), n_paths, n_fine, m, 5).cpu().numpy()
-    assert np.all(np.abs(again - ref) <= TOL * (np.abs(ref) + np.maximum(th[:, 1], yi)[:, None]))
+        assert np.array_equal(got.cpu().numpy(), ref)
+    # the same rows with another seed overwrite every sample of the buffer, then the first again
+    other = sl.em_collocation_labels_noalloc(2, *args, 6).cpu().numpy()
+    ref6 = sl.em_collocation_labels(2, *args, 6).cpu().numpy()
+    assert np.array_equal(other, ref6) and not np.array_equal(other, ref)
+    again = sl.em_collocation_labels_noalloc(2, *args, 5).cpu().numpy()
+    assert np.array_equal(again, ref)
 
 
 def test_noalloc_rejects_oversize(sl):
@@ -50,3 +52,10 @@ def test_noalloc_rejects_oversize(sl):
     with pytest.raises(sl.SLError) as e:
         sl.em_collocation_labels_noalloc(2, _dev(th), _dev(yi), _dev(dt), n_paths, 100, 7, 5)
     assert e.value.status == sl.SL_ERR_WORKSPACE
+    # argument errors come first, even for sizes beyond the buffer
+    with pytest.raises(sl.SLError) as e:
+        sl.em_collocation_labels_noalloc(7, _dev(th), _dev(yi), _dev(dt), n_paths, 100, 7, 5)
+    assert e.value.status == sl.SL_ERR_ARG
+    with pytest.raises(sl.SLError) as e:
+        sl.em_collocation_labels_noalloc(2, _dev(th), _dev(yi), _dev(dt), n_paths, 100, 11, 5)
+    assert e.value.status == sl.SL_ERR_UNSUPPORTED
