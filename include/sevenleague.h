@@ -195,6 +195,33 @@ int sl_tc_get_slots(void);
 int sl_tc_set_pipeline(int tiles_per_warpgroup);
 int sl_tc_get_pipeline(void);
 
+/* Bytes of workspace seven_league_simulate_range needs for n_paths paths. */
+size_t sl_simulate_range_workspace_size(int64_t n_paths, int n_sets);
+
+/*
+ * One contiguous range of a batched call, for splitting a batch across GPUs or
+ * calls (the method's paths are independent: Algorithm I steps 4 and 7 run
+ * per path).  theta, Y0 and path_offsets describe the WHOLE batch exactly as
+ * for seven_league_simulate_batched; this call runs its flat paths
+ * first_path .. first_path + n_paths - 1 (first_path + n_paths must not
+ * exceed path_offsets[n_sets]).  Each path keeps its set and its index within
+ * the set, hence its Philox normals, so out_YT[k] (device FP32 [n_paths]) is
+ * bit for bit out_YT[first_path + k] of the whole call, in both network forms;
+ * out_grid (or NULL): [(n_steps+1)][n_paths].  Per set, over the set's paths
+ * inside the range: out_count (device int64 [n_sets] or NULL) their number,
+ * out_mean / out_var (device FP64 [n_sets] or NULL) their mean and unbiased
+ * variance (0 for fewer than one / two paths), deterministic as in the batched
+ * call; a caller combining ranges weights them by the counts.  Workspace:
+ * sl_simulate_range_workspace_size(n_paths, n_sets).  Errors as
+ * seven_league_simulate_batched; SL_ERR_ARG for a negative first_path or
+ * n_paths.  Allocates nothing.
+ */
+int seven_league_simulate_range(int model, const sl_net* net, const float* theta, int p, const float* Y0,
+                                const int64_t* path_offsets, int n_sets, int64_t first_path, int64_t n_paths,
+                                float T, int n_steps, int m, uint64_t seed, float* out_YT, float* out_grid,
+                                double* out_mean, double* out_var, int64_t* out_count, void* ws,
+                                size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------------------------------
  * The 7L-CDC variant (timed beside the 7L scheme in Table 6.1; the remark
  * after Algorithm I): step 3's network evaluation per path is replaced by a

@@ -48,7 +48,7 @@ EXPORTED = [
     "sl_mlp_forward", "sl_mse_grad", "sl_adam_step", "sl_train", "sl_adjoint_workspace_size",
     "seven_league_adjoint", "em_collocation_labels_noalloc", "sl_em_labels_noalloc_max_samples",
     "sl_selftest_wait_timeout", "sl_cdc_workspace_size", "seven_league_cdc_simulate_batched",
-    "sl_cdcq_inverse",
+    "sl_cdcq_inverse", "sl_simulate_range_workspace_size", "seven_league_simulate_range",
 ]
 
 
@@ -99,6 +99,11 @@ def load(path: str = LIB_PATH):
         _vp, _vp, _vp, _vp, _vp, _sz, _vp]
     L.seven_league_simulate.argtypes = [_i, _vp, _i, _f, _f, _i, _i, ctypes.POINTER(sl_net), _i64,
                                         _u64, _vp, _vp]
+    L.sl_simulate_range_workspace_size.argtypes = [_i64, _i]
+    L.sl_simulate_range_workspace_size.restype = _sz
+    L.seven_league_simulate_range.argtypes = [
+        _i, ctypes.POINTER(sl_net), _vp, _i, _vp, _vp, _i, _i64, _i64, _f, _i, _i, _u64,
+        _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
     L.sl_em_terminal.argtypes = [_i, _vp, _vp, _vp, _i, _i64, _i, _u64, _vp, _vp]
     L.sl_select_workspace_size.argtypes = [_i, _i]
     L.sl_select_workspace_size.restype = _sz
@@ -272,6 +277,32 @@ def seven_league_simulate_batched(model, net, theta, Y0, path_offsets, T, n_step
         n_steps, m, seed, _ptr(out_YT, torch.float32, "out_YT"),
         _ptr(out_grid, torch.float32, "out_grid"), _ptr(out_mean, torch.float64, "out_mean"),
         _ptr(out_var, torch.float64, "out_var"), _ptr(ws), ws.numel(), _stream(stream)))
+    return ws
+
+
+def simulate_range_workspace_size(n_paths, n_sets):
+    return int(load().sl_simulate_range_workspace_size(int(n_paths), n_sets))
+
+
+def seven_league_simulate_range(model, net, theta, Y0, path_offsets, T, n_steps, m, seed, first_path, n_paths,
+                                out_YT=None, out_grid=None, out_mean=None, out_var=None, out_count=None,
+                                ws=None, stream=None):
+    """Flat paths first_path .. first_path + n_paths - 1 of the batch that theta, Y0 and
+    path_offsets describe (see include/sevenleague.h): the same per-path values as the whole
+    batched call, plus per-set count / mean / variance over the range.  Returns the workspace."""
+    torch = _torch()
+    L = load()
+    n_sets = path_offsets.numel() - 1
+    p = theta.shape[1] if theta.dim() == 2 else theta.numel() // max(n_sets, 1)
+    if ws is None:
+        ws = _workspace(L.sl_simulate_range_workspace_size(int(n_paths), n_sets), theta.device)
+    netp = ctypes.byref(net) if net is not None else None
+    _check(L.seven_league_simulate_range(
+        model, netp, _ptr(theta, torch.float32, "theta"), p, _ptr(Y0, torch.float32, "Y0"),
+        _ptr(path_offsets, torch.int64, "path_offsets"), n_sets, int(first_path), int(n_paths), float(T),
+        n_steps, m, seed, _ptr(out_YT, torch.float32, "out_YT"), _ptr(out_grid, torch.float32, "out_grid"),
+        _ptr(out_mean, torch.float64, "out_mean"), _ptr(out_var, torch.float64, "out_var"),
+        _ptr(out_count, torch.int64, "out_count"), _ptr(ws), ws.numel(), _stream(stream)))
     return ws
 
 

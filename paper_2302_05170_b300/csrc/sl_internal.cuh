@@ -160,7 +160,8 @@ struct SimArgs {
     float y0_scalar;
     const int64_t* offsets;   // [n_sets+1] or NULL -> one set of `total` paths
     int n_sets;
-    int64_t total;
+    int64_t total;            // paths this call runs (outputs are indexed 0 .. total-1)
+    int64_t first;            // flat index, in the batch `offsets` describes, of the call's first path
     float dt;
     int n_steps;
     uint64_t seed;
@@ -179,5 +180,8 @@ int launch_set_moments(const float* y, const int64_t* offsets, int n_sets, int64
                        double* mean, double* var, void* part, cudaStream_t s, int mean_stride = 1,
                        const double* scale = nullptr);
 size_t set_moments_scratch_bytes(int n_sets);
+// local[s] = clamp(offsets[s] - first, 0, n) for s <= n_sets; count[s] = local[s+1] - local[s] (or NULL).
+int launch_range_offsets(const int64_t* offsets, int n_sets, int64_t first, int64_t n, int64_t* local,
+                         int64_t* count, cudaStream_t st);
 
 }  // namespace sl

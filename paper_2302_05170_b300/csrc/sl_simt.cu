@@ -32,11 +32,12 @@ __global__ void __launch_bounds__(256) simt_7l_kernel(const SimArgs a) {
     for (int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < a.total;
          g += stride) {
         int s = 0;
-        int64_t q = g;
+        const int64_t gg = a.first + g;   // index in the whole batch (g: in this call)
+        int64_t q = gg;
         if (a.offsets) {
-            s = owning_set(a.offsets, a.n_sets, g);
-            q = g - __ldg(a.offsets + s);
-            if (!path_in_set(a.offsets, s, g, a.status)) continue;
+            s = owning_set(a.offsets, a.n_sets, gg);
+            q = gg - __ldg(a.offsets + s);
+            if (!path_in_set(a.offsets, s, gg, a.status)) continue;
         }
         const float* th = a.theta + static_cast<int64_t>(s) * a.p;
         float Y = a.Y0 ? __ldg(a.Y0 + s) : a.y0_scalar;
@@ -172,6 +173,17 @@ __global__ void set_moments_final(const float* __restrict__ y, const int64_t* __
     if (var) var[s] = n > 1 ? fmax(s2 - s1 * s1 / nn, 0.0) / (nn - 1.0) : 0.0;
 }
 
+// The offsets of a range call's own paths: set s covers the call's outputs
+// [clamp(off[s] - first), clamp(off[s+1] - first)) with clamp to [0, n], and count[s] is their number.
+__global__ void range_offsets_kernel(const int64_t* __restrict__ off, int n_sets, int64_t first, int64_t n,
+                                     int64_t* __restrict__ local, int64_t* __restrict__ count) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s > n_sets) return;
+    auto clip = [&](int64_t v) { v -= first; return v < 0 ? int64_t(0) : (v > n ? n : v); };
+    local[s] = clip(off[s]);
+    if (count && s < n_sets) count[s] = clip(off[s + 1]) - clip(off[s]);
+}
+
 int moments_chunks(int n_sets) {
     int R = 4096 / (n_sets > 0 ? n_sets : 1);
     return R < 1 ? 1 : (R > 64 ? 64 : R);
@@ -185,6 +197,12 @@ int launch_simt_7l(int model, int m, const SimArgs& a, cudaStream_t st) {
     if (model == SL_MODEL_OU_EXACT) return launch_one<SL_MODEL_OU_EXACT, 0>(a, st);
     if (a.act == SL_ACT_SOFTPLUS) return launch_one<SL_MODEL_MLP, SL_ACT_SOFTPLUS>(a, st);
     return launch_one<SL_MODEL_MLP, SL_ACT_RELU>(a, st);
+}
+
+int launch_range_offsets(const int64_t* offsets, int n_sets, int64_t first, int64_t n, int64_t* local,
+                         int64_t* count, cudaStream_t st) {
+    range_offsets_kernel<<<(n_sets + 1 + 255) / 256, 256, 0, st>>>(offsets, n_sets, first, n, local, count);
+    return cuda_error(cudaGetLastError(), "range_offsets launch");
 }
 
 size_t set_moments_scratch_bytes(int n_sets) {

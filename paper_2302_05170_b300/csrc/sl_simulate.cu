@@ -126,6 +126,80 @@ int seven_league_simulate_batched(int model, const sl_net* net, const float* the
     return SL_OK;
 }
 
+size_t sl_simulate_range_workspace_size(int64_t n_paths, int n_sets) {
+    if (n_sets < 1) n_sets = 1;
+    return sl_simulate_workspace_size(n_paths, n_sets) + align256(static_cast<size_t>(n_sets + 1) * sizeof(int64_t));
+}
+
+int seven_league_simulate_range(int model, const sl_net* net, const float* theta, int p, const float* Y0,
+                                const int64_t* path_offsets, int n_sets, int64_t first_path, int64_t n_paths,
+                                float T, int n_steps, int m, uint64_t seed, float* out_YT, float* out_grid,
+                                double* out_mean, double* out_var, int64_t* out_count, void* ws,
+                                size_t ws_bytes, void* stream) {
+    int rc = check_common(model, net, theta, p, T, n_steps, m);
+    if (rc) return rc;
+    if (n_sets < 1 || n_sets > SL_MAX_SETS) return set_error(SL_ERR_ARG, "n_sets=%d", n_sets);
+    if (first_path < 0 || n_paths < 0) return set_error(SL_ERR_ARG, "first_path / n_paths < 0");
+    if (first_path + n_paths > (int64_t(1) << 40)) return set_error(SL_ERR_UNSUPPORTED, "paths beyond 2^40");
+    if (!Y0 || !path_offsets) return set_error(SL_ERR_ARG, "Y0 / path_offsets == NULL");
+    if (!out_YT && !out_grid && !out_mean && !out_var && !out_count)
+        return set_error(SL_ERR_ARG, "no output requested");
+    if (!ws) return set_error(SL_ERR_WORKSPACE, "ws == NULL");
+    const bool moments = out_mean || out_var;
+    const size_t need = kStatusBytes +
+                        ((moments && !out_YT) ? align256(static_cast<size_t>(n_paths) * 4) : 0) +
+                        align256(static_cast<size_t>(n_sets + 1) * sizeof(int64_t)) +
+                        (moments ? set_moments_scratch_bytes(n_sets) : 0);
+    if (ws_bytes < need)
+        return set_error(SL_ERR_WORKSPACE, "workspace %zu bytes < %zu required", ws_bytes, need);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned char* w = static_cast<unsigned char*>(ws);
+    unsigned* status = reinterpret_cast<unsigned*>(w);
+    size_t off = kStatusBytes;
+    float* yt = out_YT;
+    if (moments && !out_YT) {
+        yt = reinterpret_cast<float*>(w + off);
+        off += align256(static_cast<size_t>(n_paths) * 4);
+    }
+    int64_t* local = reinterpret_cast<int64_t*>(w + off);
+    off += align256(static_cast<size_t>(n_sets + 1) * sizeof(int64_t));
+    void* part = w + off;
+
+    SimArgs a{};
+    if (model == SL_MODEL_MLP) {
+        a.params = net->params;
+        a.d_in = net->d_in;
+        a.act = net->act;
+    }
+    a.theta = theta;
+    a.p = p;
+    a.Y0 = Y0;
+    a.offsets = path_offsets;
+    a.n_sets = n_sets;
+    a.total = n_paths;
+    a.first = first_path;
+    a.dt = T / static_cast<float>(n_steps);
+    a.n_steps = n_steps;
+    a.seed = seed;
+    a.out_YT = yt;
+    a.out_grid = out_grid;
+    a.status = status;
+    a.m = m;
+    rc = make_gh_const(m, &a.gh);
+    if (rc) return rc;
+    rc = cuda_error(cudaMemsetAsync(status, 0, kStatusBytes, st), "status clear");
+    if (rc) return rc;
+    if (n_paths > 0) {
+        rc = dispatch(model, net, m, a, st);
+        if (rc) return rc;
+    }
+    if (!moments && !out_count) return SL_OK;
+    rc = launch_range_offsets(path_offsets, n_sets, first_path, n_paths, local, out_count, st);
+    if (rc) return rc;
+    if (moments) return launch_set_moments(yt, local, n_sets, n_paths, out_mean, out_var, part, st);
+    return SL_OK;
+}
+
 int seven_league_simulate(int model, const float* theta, int p, float Y0, float T, int n_steps,
                           int m, const sl_net* weights, int64_t n_paths, uint64_t seed,
                           float* out, void* stream) {

@@ -351,7 +351,7 @@ __device__ __forceinline__ bool bar_and(int id, bool v) {
 
 // Per-thread state of one path tile (128 paths; this thread owns row `r`).
 struct Tile {
-    int64_t g;        // flat path index of this thread's row
+    int64_t g;        // path index of this thread's row within the call (its output index)
     int s;            // owning parameter set
     uint32_t q;       // path index within the set (Philox counter)
     bool valid;       // row holds a real path
@@ -375,11 +375,12 @@ __device__ __forceinline__ void tile_begin(Tile& T, const SimArgs& a, int64_t ti
     T.g = tile * kTile + r;
     T.valid = T.g < a.total;
     T.s = 0;
-    int64_t qq = T.g;
+    const int64_t gg = a.first + (T.valid ? T.g : a.total - 1);   // index in the whole batch
+    int64_t qq = gg;
     if (a.offsets) {
-        T.s = owning_set(a.offsets, a.n_sets, T.valid ? T.g : a.total - 1);
-        qq = T.g - __ldg(a.offsets + T.s);
-        if (T.valid) T.valid = path_in_set(a.offsets, T.s, T.g, a.status);
+        T.s = owning_set(a.offsets, a.n_sets, gg);
+        qq = gg - __ldg(a.offsets + T.s);
+        if (T.valid) T.valid = path_in_set(a.offsets, T.s, gg, a.status);
     }
     T.q = static_cast<uint32_t>(qq);
     const float* th = a.theta + static_cast<int64_t>(T.s) * a.p;

@@ -1,10 +1,11 @@
 """The benchmark's multi-rank bookkeeping on CPU (gloo, world size 2).
 
-Under torchrun every rank runs its own copy of the workload with its own
-Philox key (no collective on the data path); the job's time is the slowest
-rank's, and the reported rate counts the units of all ranks.  Checked with
-two CPU processes: the max-over-ranks reduction, the whole-job rate and the
-per-rank seeds.
+Under torchrun the job (16 parameter sets per rank) is split across the ranks
+by path count; the job's time is the slowest rank's, and the reported rate
+counts the units of all ranks.  Checked with two CPU processes: the
+max-over-ranks reduction, the whole-job rate, and each rank's share of the
+job's flat path list (contiguous, equal, covering it once).  The split call
+itself is checked in tests/test_sharding.py and tests/test_gpu_sharding.py.
 """
 import os
 import socket
@@ -32,7 +33,8 @@ def _worker(rank, world, port, q):
         t_max = bench.max_over_ranks(local_seconds)
         rate = bench.whole_job_rate(1000, world, t_max)
         ws, rk, lr = bench._dist()
-        q.put((rank, t_max, rate, bench.rank_seed(1, rk), ws))
+        from paper_2302_05170_b300 import sharding
+        q.put((rank, t_max, rate, sharding.rank_range(16 * world * 10 ** 6, ws, rk), ws))
     finally:
         dist.destroy_process_group()
 
@@ -48,11 +50,11 @@ def test_two_rank_aggregation():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    for rank, t_max, rate, seed, ws in out:
+    for rank, t_max, rate, share, ws in out:
         assert ws == 2
         assert t_max == pytest.approx(2.5)
         assert rate == pytest.approx(2 * 1000 / 2.5)
-    assert [o[3] for o in out] == [1, 2]
+    assert [o[3] for o in out] == [(0, 16 * 10 ** 6), (16 * 10 ** 6, 16 * 10 ** 6)]
 
 
 def test_single_rank_defaults(monkeypatch):
