@@ -20,6 +20,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import re
 import subprocess
@@ -39,6 +40,32 @@ ALG_FLOPS_PER_PATH_STEP = 2 * (4 * 50 + 3 * 50 * 50 + 50 * 7)   # 16,100 (biases
 # 7L-CDC in the marginal's quantile coordinate, m = 7, per path-step inside the hull: m Horner
 # evaluations of degree m - 1 in X and one in xi (FMA = 2 flops); the normal draw is not counted
 CDC_FLOPS_PER_PATH_STEP = 2 * 7 * 6 + 2 * 6                            # 96
+# network training of the bench (pipeline.train_network keywords): features and labels normalised
+# for training, 4e5 Euler-Maruyama paths per label row, and a BF16 finish, so that the FP32 and the
+# tensor-core forms evaluate the same (BF16-valued) trained network
+TRAIN_RECIPE = dict(normalize=True, n_paths=400_000, bf16_steps=10_000)
+# step sizes of the networks used at dt = 1/64 (the adjoint workload: T = 1 in 64 steps)
+ADJ_DTS = (1 / 64, 1 / 32, 1 / 16, 1 / 8, 1 / 4, 1 / 2, 1.0)
+
+
+def take(t, idx):
+    """Values of a device tensor at the flat indices idx (numpy FP64)."""
+    import torch
+    return t[torch.as_tensor(idx, device=t.device)].double().cpu().numpy()
+
+
+def sample_idx(offsets, per_set, seed=12):
+    """A bounded sample of flat path indices: per_set paths of every set (its first and last
+    included), for the FP64 oracle checks."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for s in range(len(offsets) - 1):
+        a, b = int(offsets[s]), int(offsets[s + 1])
+        if b <= a:
+            continue
+        k = min(per_set, b - a)
+        out.append(np.unique(np.concatenate([[a, b - 1], rng.integers(a, b, k)])))
+    return np.concatenate(out) if out else np.zeros(0, np.int64)
 
 # DRAM traffic of the sampler kernel on the default workload, from the committed ncu summary;
 # used only while the kernel's sources are those the counters were taken on.
@@ -197,6 +224,45 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_oracle_checks(checks):
+    """FP64-oracle error of each secondary result on its bounded sample (the cpu_baseline leg):
+    per result the max, 99.99th percentile and mean of |a - b| / (|b| + s) over the sampled paths
+    (s: the state's scale), or, for the adjoints, per component (value, d/dY0, d/dtheta) with s =
+    the component's mean |b|, and the share of paths within 2e-3."""
+    import oracle
+    out = {}
+    for c in checks:
+        k = c["kind"]
+        if k in ("paths", "cdcq", "cdc"):
+            f = {"paths": oracle.seven_league_paths, "cdcq": oracle.cdcq_paths, "cdc": oracle.cdc_paths}[k]
+            want = f(oracle.MODEL_MLP, c["P"], c["theta"], c["Y0"], c["offsets"], c["T"], c["n_steps"], c["m"],
+                     c["seed"], idx=c["idx"], d_in=c["d_in"], act=c["act"])
+            e = np.abs(c["got"] - want) / (np.abs(want) + c["scale"])
+            out[c["name"]] = {"max": float(e.max()), "p9999": float(np.percentile(e, 99.99)), "mean": float(e.mean()),
+                              "n_paths": int(len(e))}
+        elif k == "labels":
+            th = np.asarray(c["theta"])
+            want = oracle.em_labels(2, th, c["Yi"], c["dt"], c["n_paths"], c["n_fine"], c["m"], c["seed"],
+                                    n_rows=c["rows"])
+            s = np.maximum(th[:c["rows"], 1], np.asarray(c["Yi"])[:c["rows"]])[:, None]
+            e = np.abs(c["got"] - want) / (np.abs(want) + s)
+            out[c["name"]] = {"max": float(e.max()), "mean": float(e.mean()), "n_labels": int(e.size)}
+        elif k == "adjoint":
+            _, val, gr = oracle.seven_league_payoff_grad(oracle.MODEL_MLP, c["P"], c["theta"], c["Y0"], c["offsets"],
+                                                         c["T"], c["n_steps"], c["m"], c["seed"], c["K"],
+                                                         idx=c["idx"], d_in=c["d_in"], act=c["act"])
+            want = np.vstack([val[None, :], gr.T])
+            res = {}
+            for comp, name in enumerate(["value", "dY0"] + ["dtheta%d" % i for i in range(want.shape[0] - 2)]):
+                b = want[comp]
+                e = np.abs(c["got"][comp] - b) / (np.abs(b) + np.abs(b).mean() + 1e-12)
+                res[name] = {"max": float(e.max()), "p999": float(np.percentile(e, 99.9)),
+                             "within_2e-3": float((e <= 2e-3).mean())}
+            res["n_paths"] = int(want.shape[1])
+            out[c["name"]] = res
+    return out
+
+
 def run_labels_only(args, torch, sl, W, local):
     """Offline stage alone: em_collocation_labels on the CIR label workload."""
     sl.load()
@@ -267,12 +333,14 @@ def main():
 
     if args.weights == "trained":
         from paper_2302_05170_b300 import pipeline
-        P_tr, losses_tr, _ = pipeline.train_gbm_online_network(n_rows=1 << 15, n_steps=args.train_steps)
+        P_tr, losses_tr, _ = pipeline.train_gbm_online_network(n_rows=1 << 15, n_steps=args.train_steps,
+                                                               **TRAIN_RECIPE)
         torch.cuda.synchronize()
         params_np = P_tr.cpu().numpy()
-        weights_kind = ("trained on the GPU: em_collocation_labels (GBM, 32768 rows x 1e5 paths x 100 fine "
-                        "steps, dt in {0.125,0.25,0.5,1}) + %d Adam steps (final loss %.3g)"
-                        % (args.train_steps, float(np.mean(losses_tr[-100:]))))
+        weights_kind = ("trained on the GPU: em_collocation_labels (GBM, 32768 rows x 4e5 paths x 100 fine "
+                        "steps, dt in {0.125,0.25,0.5,1}), %d Adam steps on normalised features and labels "
+                        "(folded into the first and last layers), then 10000 Adam steps of the BF16-rounded "
+                        "network; every weight is a BF16 value and both forms run it" % args.train_steps)
     else:
         params_np = W.xavier_params(4, 7, seed=0)
         weights_kind = "Xavier-uniform seed 0 (untrained)"
@@ -381,6 +449,7 @@ def main():
                 "peak_kind": "FP32 FMA: %d SMs x 128 lanes x 2 flop x %.0f MHz" % (sms, peaks["sm_max_mhz"])}
 
     secondary = {}
+    checks = []          # FP64-oracle checks of the secondary results, run in the cpu_baseline leg
     if not args.no_secondary and rank == 0 and world == 1:
         # the other form on the same paths
         other = sl.PREC_FP32 if prec == sl.PREC_BF16 else sl.PREC_BF16
@@ -406,13 +475,41 @@ def main():
             secondary["bf16_over_fp32"] = (value / (path_steps / (o_ms * 1e-3))) if other == sl.PREC_FP32 else \
                 (path_steps / (o_ms * 1e-3)) / value
             a64, b64 = yt.double(), yt_o.double()
-            secondary["bf16_vs_fp32_max_rel_diff"] = float(((a64 - b64).abs() / (b64.abs() + 1.0)).max())
+            dd = (a64 - b64).abs() / (b64.abs() + 1.0)
+            secondary["bf16_vs_fp32_max_rel_diff"] = float(dd.max())
+            secondary["bf16_vs_fp32_p9999_rel_diff"] = float(torch.quantile(dd[::16], 0.9999))
+            secondary["bf16_vs_fp32_weights"] = "the same BF16-valued weights in both forms" if \
+                args.weights == "trained" else "the same FP32 weights (BF16-rounded in the tensor-core form)"
+            # both forms against the exact-collocation GBM chain on the same normals (the network's error)
+            yt_x = torch.empty_like(yt)
+            sl.seven_league_simulate_batched(sl.MODEL_GBM_EXACT, None, theta, Y0, off, T, n_steps, m, seed,
+                                             out_YT=yt_x, total_paths=total)
+            x64 = yt_x.double()
+            for key_f, y64 in (("bf16", a64 if prec == sl.PREC_BF16 else b64), ("fp32", b64 if prec == sl.PREC_BF16 else a64)):
+                e = (y64 - x64).abs()
+                secondary["err_vs_exact_map_" + key_f] = {"mean_abs": float(e.mean()),
+                                                           "p9999_abs": float(torch.quantile(e[::16], 0.9999)),
+                                                           "max_abs": float(e.max())}
+            secondary["err_vs_exact_map_note"] = ("|Y_T - Y_T(exact GBM collocation map)| per path, same normals, "
+                                                  "all 16e6 paths (p99.99 on every 16th): the trained network's own "
+                                                  "error, the same in both forms")
+            del yt_x
+            fp32_yt = (yt_o if other == sl.PREC_FP32 else yt)
+            ix = sample_idx(w["offsets"], 200)
+            checks.append(dict(name="fp32_form", kind="paths", P=params_np, theta=w["theta"], Y0=w["Y0"],
+                               offsets=w["offsets"], T=T, n_steps=n_steps, m=m, seed=seed, d_in=4, act=0,
+                               idx=ix, got=take(fp32_yt, ix), scale=1.0))
         except sl.SLError as e:
             secondary["other_form_error"] = str(e)
         if prec == sl.PREC_BF16:
             # the same workload with the paper's Softplus activation in the tensor-core form
             # (log(1 + e^z) on the fast exponent/logarithm unit in the epilogue)
-            net_sp = sl.make_net(P, 4, 7, act=sl.ACT_SOFTPLUS, prec=sl.PREC_BF16)
+            if args.weights == "trained":
+                P_sp, _, _ = pipeline.train_gbm_online_network(n_rows=1 << 15, n_steps=args.train_steps, act=1,
+                                                               dts=ADJ_DTS, **TRAIN_RECIPE)
+            else:
+                P_sp = P
+            net_sp = sl.make_net(P_sp, 4, 7, act=sl.ACT_SOFTPLUS, prec=sl.PREC_BF16)
             yt_sp = torch.empty_like(yt)
             step(out_yt=yt_sp, net_=net_sp)
             torch.cuda.synchronize()
@@ -423,6 +520,10 @@ def main():
             e1.record(stream)
             torch.cuda.synchronize()
             secondary["softplus_bf16_path_steps_per_s"] = path_steps / (e0.elapsed_time(e1) / 3 * 1e-3)
+            ix = sample_idx(w["offsets"], 200)
+            checks.append(dict(name="softplus_bf16", kind="paths", P=W.bf16_round(P_sp.cpu().numpy()), theta=w["theta"],
+                               Y0=w["Y0"], offsets=w["offsets"], T=T, n_steps=n_steps, m=m, seed=seed, d_in=4,
+                               act=1, idx=ix, got=take(yt_sp, ix), scale=1.0))
             del yt_sp
         # the 7L-CDC variant on the same paths (Table 6.1's second scheme): the network only at the
         # marginal collocation points of each (set, step), an interpolation in Y per path.  With a
@@ -432,8 +533,9 @@ def main():
         # unordered) and with the exact GBM map.
         if args.weights == "trained":
             P_cdc, _, _ = pipeline.train_gbm_online_network(n_rows=1 << 15, n_steps=args.train_steps,
-                                                            dts=tuple(0.125 * np.arange(1, 17)))
-            cdc_net_kind = "GBM network trained over the horizons 0.125..2 (%d Adam steps)" % args.train_steps
+                                                            dts=tuple(0.125 * np.arange(1, 17)), **TRAIN_RECIPE)
+            cdc_net_kind = ("GBM network trained over the horizons 0.125..2 (%d Adam steps, the bench's training "
+                            "recipe)" % args.train_steps)
         else:
             P_cdc = torch.as_tensor(W.near_affine_params(4, 7, seed=0), device=dev)
             cdc_net_kind = "workloads.near_affine_params (seed 0)"
@@ -461,6 +563,12 @@ def main():
                 continue
             c_rate = path_steps / (e0.elapsed_time(e1) / 5 * 1e-3)
             secondary[key + "_path_steps_per_s"] = c_rate
+            if model_c == sl.MODEL_MLP:
+                ix = sample_idx(w["offsets"], 125)
+                checks.append(dict(name=key, kind="cdcq" if space_c == sl.CDC_QUANTILE else "cdc",
+                                   P=P_cdc.cpu().numpy(), theta=w["theta"], Y0=w["Y0"], offsets=w["offsets"], T=T,
+                                   n_steps=n_steps, m=m, seed=seed, d_in=4, act=0, idx=ix, got=take(yt_c, ix),
+                                   scale=1.0))
             if key == "cdc":
                 sms = torch.cuda.get_device_properties(dev).multi_processor_count
                 fp32_peak = sms * 128 * 2 * peaks["sm_max_mhz"] * 1e6
@@ -504,6 +612,8 @@ def main():
         secondary["em_label_samples_per_s"] = 1024 * 10 ** 5 / (l_ms * 1e-3)
         secondary["em_fine_steps_per_s"] = 1024 * 10 ** 5 * 100 / (l_ms * 1e-3)
         secondary["em_labels_workload"] = "CIR 1024 rows x 1e5 paths x 100 fine steps, 7 quantiles"
+        checks.append(dict(name="em_labels", kind="labels", theta=th, Yi=yi, dt=dtr, n_paths=10 ** 5, n_fine=100,
+                           m=7, seed=1, rows=4, got=lab[:4].double().cpu().numpy()))
         del wsl
         # CIR network trained on those labels, then the batched CIR workload: 4096 theta sets with
         # log-uniform path counts in [1e3, 1e5], 32 steps, in one persistent launch replayed from a
@@ -551,6 +661,11 @@ def main():
         c_ms = e0.elapsed_time(e1) / 3
         assert sl.workspace_status(ws_c) == 0
         secondary["cir_batched_path_steps_per_s"] = tot_c * cb["n_steps"] / (c_ms * 1e-3)
+        ix = sample_idx(cb["offsets"], 2)
+        P_c_np = P_c.cpu().numpy()
+        checks.append(dict(name="cir_batched", kind="paths", P=W.bf16_round(P_c_np) if prec == sl.PREC_BF16 else P_c_np,
+                           theta=cb["theta"], Y0=cb["Y0"], offsets=cb["offsets"], T=cb["T"], n_steps=cb["n_steps"],
+                           m=7, seed=cb["seed"], d_in=5, act=0, idx=ix, got=take(yt_c, ix), scale=0.1))
         secondary["cir_batched_workload"] = ("CIR 4096 theta sets, %d paths (log-uniform 1e3..1e5 per set), "
                                              "32 steps, m=7, one persistent launch in a CUDA graph" % tot_c)
         del ws_c
@@ -572,21 +687,43 @@ def main():
         torch.cuda.synchronize()
         if sl.workspace_status(ws_cc) == 0:
             secondary["cdc_cir_batched_path_steps_per_s"] = tot_c * cb["n_steps"] / (e0.elapsed_time(e1) / 3 * 1e-3)
+            ix = sample_idx(cb["offsets"], 1)
+            checks.append(dict(name="cdc_cir_batched", kind="cdcq", P=P_cc.cpu().numpy(), theta=cb["theta"],
+                               Y0=cb["Y0"], offsets=cb["offsets"], T=cb["T"], n_steps=cb["n_steps"], m=7,
+                               seed=cb["seed"], d_in=5, act=0, idx=ix, got=take(yt_c, ix), scale=0.1))
         else:
             secondary["cdc_cir_batched_error"] = "device status %d" % sl.workspace_status(ws_cc)
         del yt_c, ws_cc
-        # adjoint: GBM network, 1e6 paths, 64 steps, checkpoint every 8 steps, K = 1, in both
-        # network forms (FP32 CUDA cores; BF16 tcgen05)
-        n_a = 10 ** 6
+        # adjoint: GBM mu = 0.1, sigma = 0.3, Y0 = 1, T = 1 in 64 steps (dt = 1/64), 1e6 paths, checkpoint
+        # every 8 steps, call K = 1.  The networks are trained down to dt = 1/64 (ReLU, FP32 and BF16
+        # forms; the Softplus network trained as such, BF16 form); the exact GBM collocation map on the
+        # same normals gives the scheme's value without a network's error; Black-Scholes (undiscounted)
+        # is the limit of both.  Each value is the FP64 mean over the paths, with its standard error.
+        if args.weights == "trained":
+            P_adj, _, _ = pipeline.train_gbm_online_network(n_rows=1 << 15, n_steps=args.train_steps, dts=ADJ_DTS,
+                                                            **TRAIN_RECIPE)
+        else:
+            P_adj = P
+        n_a, T_a, K_a, mu_a, sg_a = 10 ** 6, 1.0, 1.0, 0.1, 0.3
         off_a = torch.as_tensor(W.offsets_from_counts([n_a]), device=dev)
-        th_a = torch.tensor([[0.1, 0.3]], device=dev)
+        th_a = torch.tensor([[mu_a, sg_a]], device=dev)
         y0_a = torch.ones(1, device=dev)
         ws_a = torch.empty(sl.adjoint_workspace_size(n_a, 1, 64, 8, 2), dtype=torch.uint8, device=dev)
-        for pr, act_a, key in ((sl.PREC_FP32, sl.ACT_RELU, "adjoint_fp32"), (sl.PREC_BF16, sl.ACT_RELU, "adjoint_bf16"),
-                               (sl.PREC_BF16, sl.ACT_SOFTPLUS, "adjoint_bf16_softplus")):
-            net_a = sl.make_net(P, 4, 7, act=act_a, prec=pr)
-            run_a = lambda: sl.seven_league_adjoint(sl.MODEL_MLP, net_a, th_a, y0_a, off_a, 1.0, 64, 7, 1, 1.0,
-                                                    ckpt_k=8, ws=ws_a, total_paths=n_a)
+        paths_a = torch.empty((4, n_a), dtype=f32, device=dev)
+        ncdf = lambda x: 0.5 * math.erfc(-x / math.sqrt(2.0))
+        d1 = (math.log(1.0 / K_a) + (mu_a + 0.5 * sg_a ** 2) * T_a) / (sg_a * math.sqrt(T_a))
+        secondary["adjoint_black_scholes"] = {
+            "value": math.exp(mu_a * T_a) * ncdf(d1) - K_a * ncdf(d1 - sg_a * math.sqrt(T_a)),
+            "dY0": math.exp(mu_a * T_a) * ncdf(d1), "dmu": T_a * math.exp(mu_a * T_a) * ncdf(d1),
+            "dsigma": math.exp(mu_a * T_a) * math.exp(-0.5 * d1 * d1) / math.sqrt(2 * math.pi) * math.sqrt(T_a)}
+        for key, model_a, Pa, act_a, pr in (
+                ("adjoint_fp32", sl.MODEL_MLP, P_adj, sl.ACT_RELU, sl.PREC_FP32),
+                ("adjoint_bf16", sl.MODEL_MLP, P_adj, sl.ACT_RELU, sl.PREC_BF16),
+                ("adjoint_bf16_softplus", sl.MODEL_MLP, P_sp, sl.ACT_SOFTPLUS, sl.PREC_BF16),
+                ("adjoint_exact_map", sl.MODEL_GBM_EXACT, None, 0, sl.PREC_FP32)):
+            net_a = sl.make_net(Pa, 4, 7, act=act_a, prec=pr) if model_a == sl.MODEL_MLP else None
+            run_a = lambda: sl.seven_league_adjoint(model_a, net_a, th_a, y0_a, off_a, T_a, 64, 7, 1, K_a, ckpt_k=8,
+                                                    out_paths=paths_a, ws=ws_a, total_paths=n_a)
             run_a()
             torch.cuda.synchronize()
             e0.record(stream)
@@ -595,19 +732,33 @@ def main():
             torch.cuda.synchronize()
             assert sl.workspace_status(ws_a) == 0
             secondary[key + "_path_steps_per_s"] = n_a * 64 / (e0.elapsed_time(e1) * 1e-3)
-            secondary[key + "_result"] = ("value %.5f dY0 %.5f dtheta %s"
-                                          % (v_a.item(), d0_a.item(), [round(x, 5) for x in dth_a[0].tolist()]))
-        secondary["adjoint_workload"] = ("GBM network, 1e6 paths x 64 steps, checkpoint every 8, call K=1 "
-                                         "(adjoint_bf16_softplus: the same weights read as a Softplus network)")
+            se = (paths_a.double().std(dim=1) / math.sqrt(n_a)).tolist()
+            vals = [v_a.item(), d0_a.item()] + dth_a[0].tolist()
+            secondary[key + "_result"] = {k: [round(a, 6), round(b, 6)] for k, a, b in
+                                          zip(("value", "dY0", "dmu", "dsigma"), vals, se)}
+            if model_a == sl.MODEL_MLP:
+                ix = sample_idx(W.offsets_from_counts([n_a]), 2000)
+                Pn = Pa.cpu().numpy()
+                checks.append(dict(name=key, kind="adjoint", P=W.bf16_round(Pn) if pr == sl.PREC_BF16 else Pn,
+                                   theta=[[mu_a, sg_a]], Y0=[1.0], offsets=W.offsets_from_counts([n_a]), T=T_a,
+                                   n_steps=64, m=7, seed=1, K=K_a, d_in=4, act=act_a, idx=ix,
+                                   got=paths_a[:, torch.as_tensor(ix, device=dev)].double().cpu().numpy()))
+        secondary["adjoint_workload"] = ("GBM mu=0.1 sigma=0.3 Y0=1, 1e6 paths x 64 steps of dt=1/64, checkpoint "
+                                         "every 8, call K=1; each *_result is [FP64 mean, standard error] of the "
+                                         "value and its derivatives in Y0, mu, sigma; networks trained over dt "
+                                         "1/64..1 (adjoint_bf16_softplus: a Softplus network trained as such); "
+                                         "adjoint_exact_map: the exact GBM collocation map on the same normals")
+        del paths_a
         # CIR adjoint on the trained CIR network (BF16 tcgen05 form): kappa=1, ybar=0.1, gamma=0.3,
         # Y0=0.1, 1e6 paths x 64 steps of dt=0.25 (inside the label rows' dt range), checkpoint every 8;
         # call K=1 lies far above the CIR range (every sensitivity is 0), K=ybar is the meaningful case
         th_ca = torch.tensor([[1.0, 0.1, 0.3]], device=dev)
         y0_ca = torch.tensor([0.1], device=dev)
         ws_ca = torch.empty(sl.adjoint_workspace_size(n_a, 1, 64, 8, 3), dtype=torch.uint8, device=dev)
+        paths_ca = torch.empty((5, n_a), dtype=f32, device=dev)
         for Kc, key in ((1.0, "cir_adjoint_K1"), (0.1, "cir_adjoint_Kybar")):
             run_ca = lambda: sl.seven_league_adjoint(sl.MODEL_MLP, net_c, th_ca, y0_ca, off_a, 16.0, 64, 7, 1, Kc,
-                                                     ckpt_k=8, ws=ws_ca, total_paths=n_a)
+                                                     ckpt_k=8, out_paths=paths_ca, ws=ws_ca, total_paths=n_a)
             run_ca()
             torch.cuda.synchronize()
             e0.record(stream)
@@ -618,6 +769,13 @@ def main():
             secondary[key + "_path_steps_per_s"] = n_a * 64 / (e0.elapsed_time(e1) * 1e-3)
             secondary[key + "_result"] = ("value %.6f dY0 %.5f dtheta %s"
                                           % (v_c.item(), d0_c.item(), [round(x, 5) for x in dth_c[0].tolist()]))
+            if Kc < 1.0:
+                ix = sample_idx(W.offsets_from_counts([n_a]), 2000)
+                Pn = P_c.cpu().numpy()
+                checks.append(dict(name=key, kind="adjoint", P=W.bf16_round(Pn) if prec == sl.PREC_BF16 else Pn,
+                                   theta=[[1.0, 0.1, 0.3]], Y0=[0.1], offsets=W.offsets_from_counts([n_a]), T=16.0,
+                                   n_steps=64, m=7, seed=1, K=Kc, d_in=5, act=0, idx=ix,
+                                   got=paths_ca[:, torch.as_tensor(ix, device=dev)].double().cpu().numpy()))
         secondary["cir_adjoint_workload"] = ("CIR network (BF16 tcgen05), kappa=1 ybar=0.1 gamma=0.3 Y0=0.1, "
                                              "1e6 paths x 64 steps of dt=0.25, checkpoint every 8")
         # the paper's own experiment (Table 6.1's path counts): OU, m = 5, trained network (over the
@@ -652,6 +810,12 @@ def main():
                 e1.record(stream)
                 torch.cuda.synchronize()
                 ou_ms["%s_%d" % (key, n_ou)] = round(e0.elapsed_time(e1) / 10, 4)
+            ix = sample_idx(W.offsets_from_counts([n_ou]), 3000)
+            Pn = P_ou.cpu().numpy()
+            checks.append(dict(name="ou_" + key, kind="cdcq" if key == "cdc" else ("cdc" if key == "cdc_y" else "paths"),
+                               P=W.bf16_round(Pn) if pr == sl.PREC_BF16 and key == "bf16" else Pn,
+                               theta=[[0.5, 0.3, 1.0]], Y0=[1.5], offsets=W.offsets_from_counts([n_ou]), T=2.0,
+                               n_steps=16, m=5, seed=3, d_in=5, act=0, idx=ix, got=take(yt_ou, ix), scale=1.5))
             yt_ex = torch.empty(200000, dtype=f32, device=dev)
             sl.seven_league_simulate_batched(sl.MODEL_OU_EXACT, None, th_ou, y0_ou, off_ou, 2.0, 16, 5, 3,
                                              out_YT=yt_ex, total_paths=200000)
@@ -730,6 +894,13 @@ def main():
         err = np.abs(g - yo) / (np.abs(yo) + 1.0)
         accuracy = {"max_rel_err": float(err.max()), "p9999_rel_err": float(np.percentile(err, 99.99)),
                     "n_paths_checked": int(len(idx)), "metric": "|a-b|/(|b|+Y0) vs FP64 oracle"}
+        if checks:
+            t_chk = time.perf_counter()
+            secondary["oracle_err"] = run_oracle_checks(checks)
+            secondary["oracle_err_note"] = ("every secondary result against the FP64 oracle on a bounded sample of "
+                                            "its paths (same weights, normals and inputs): max / p99.99 / mean of "
+                                            "|a-b|/(|b|+s); adjoints per component with s = mean |b| (%.1f s)"
+                                            % (time.perf_counter() - t_chk))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -459,7 +459,10 @@ int sl_mlp_forward(const sl_net* net, const float* feats, int64_t n_rows, float*
  * Gradient of L = 1/(n_rows*m) sum_r sum_j (H_j(f_r) - y_rj)^2 over the rows
  * rows[0..n_rows) (device int32, NULL = 0..n_rows-1) of feats [N][d_in] and
  * labels [N][m]: grad device FP32 [sl_n_params], *loss device FP32 (may be
- * NULL).  Deterministic (fixed reduction order).
+ * NULL).  Deterministic (fixed reduction order).  net->prec = SL_PREC_BF16:
+ * H is the network with every weight and bias rounded to BF16 (nearest, ties
+ * to even), the one the tensor-core sampler evaluates, and grad is its
+ * gradient (applied to the FP32 parameters, a straight-through update).
  */
 int sl_mse_grad(const sl_net* net, const float* feats, const float* labels, const int32_t* rows,
                 int n_rows, float* grad, float* loss, void* ws, size_t ws_bytes, void* stream);
@@ -477,9 +480,11 @@ int sl_adam_step(float* params, float* adam_m, float* adam_v, const float* grad,
  * minibatches batch_rows[b*batch .. (b+1)*batch) (device int32): params,
  * adam_m, adam_v device FP32 [sl_n_params(d_in, m)] updated in place;
  * losses device FP32 [n_batches] (loss of each minibatch before its update,
- * may be NULL).  Only kernel launches on `stream`: capturable in a CUDA graph.
+ * may be NULL).  prec = SL_PREC_BF16 trains the BF16-rounded network (as
+ * sl_mse_grad), SL_PREC_FP32 the FP32 one; SL_ERR_ARG otherwise.  Only kernel
+ * launches on `stream`: capturable in a CUDA graph.
  */
-int sl_train(float* params, int d_in, int m, int act, float* adam_m, float* adam_v, int64_t t0,
+int sl_train(float* params, int d_in, int m, int act, int prec, float* adam_m, float* adam_v, int64_t t0,
              const float* feats, const float* labels, const int32_t* batch_rows, int n_batches,
              int batch, float lr, float b1, float b2, float eps, float* losses, void* ws,
              size_t ws_bytes, void* stream);

@@ -116,7 +116,7 @@ def load(path: str = LIB_PATH):
     L.sl_mlp_forward.argtypes = [ctypes.POINTER(sl_net), _vp, _i64, _vp, _vp]
     L.sl_mse_grad.argtypes = [ctypes.POINTER(sl_net), _vp, _vp, _vp, _i, _vp, _vp, _vp, _sz, _vp]
     L.sl_adam_step.argtypes = [_vp, _vp, _vp, _vp, _i64, _i64, _f, _f, _f, _f, _vp]
-    L.sl_train.argtypes = [_vp, _i, _i, _i, _vp, _vp, _i64, _vp, _vp, _vp, _i, _i, _f, _f, _f, _f,
+    L.sl_train.argtypes = [_vp, _i, _i, _i, _i, _vp, _vp, _i64, _vp, _vp, _vp, _i, _i, _f, _f, _f, _f,
                            _vp, _vp, _sz, _vp]
     L.sl_adjoint_workspace_size.argtypes = [_i64, _i, _i, _i, _i]
     L.sl_adjoint_workspace_size.restype = _sz
@@ -551,8 +551,9 @@ def adam_step(params, adam_m, adam_v, grad, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e
 
 
 def train(params, d_in, m, adam_m, adam_v, t0, feats, labels, batch_rows, batch, lr=1e-3, b1=0.9,
-          b2=0.999, eps=1e-8, act=ACT_RELU, losses=None, ws=None, stream=None):
-    """len(batch_rows)//batch Adam steps in place; returns the per-step losses (device)."""
+          b2=0.999, eps=1e-8, act=ACT_RELU, losses=None, ws=None, stream=None, prec=PREC_FP32):
+    """len(batch_rows)//batch Adam steps in place; returns the per-step losses (device).
+    prec=PREC_BF16 trains the BF16-rounded network (see include/sevenleague.h)."""
     torch = _torch()
     L = load()
     nb = batch_rows.numel() // batch
@@ -560,7 +561,7 @@ def train(params, d_in, m, adam_m, adam_v, t0, feats, labels, batch_rows, batch,
         losses = torch.empty(nb, dtype=torch.float32, device=params.device)
     if ws is None:
         ws = _workspace(L.sl_train_workspace_size(d_in, m, batch), params.device)
-    _check(L.sl_train(_ptr(params, torch.float32, "params"), d_in, m, act, _ptr(adam_m, torch.float32),
+    _check(L.sl_train(_ptr(params, torch.float32, "params"), d_in, m, act, prec, _ptr(adam_m, torch.float32),
                       _ptr(adam_v, torch.float32), int(t0), _ptr(feats, torch.float32, "feats"),
                       _ptr(labels, torch.float32, "labels"), _ptr(batch_rows, torch.int32, "batch_rows"),
                       nb, batch, lr, b1, b2, eps, _ptr(losses, torch.float32), _ptr(ws), ws.numel(),

@@ -3,12 +3,19 @@
 // Adam (the optimiser, batch size 1024 and learning rate 1e-3 named in the
 // experiments section), all in the library's kernels.
 //
+// BF16-aware training (prec = SL_PREC_BF16): the forward and backward passes
+// use the weights and biases rounded to BF16 (nearest, ties to even), as the
+// tensor-core sampler evaluates them, and the gradient so obtained updates the
+// FP32 parameters (a straight-through step), so the BF16 network is the one
+// trained.
+//
 // Gradient: CTA c takes kRows rows of the minibatch, runs the forward pass
 // with every layer's pre-activations kept in shared memory, back-propagates
 // the loss 1/(B m) sum (H(f) - y)^2, and writes its partial gradient (one
 // value per parameter) and partial loss to the workspace.  A second kernel
 // adds the partials of each parameter in CTA order (deterministic), and, for
 // training, applies the Adam update in the same pass.
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include "sl_internal.cuh"
@@ -57,7 +64,7 @@ struct GradSmem {
 
 // Partial MSE gradient of CTA blockIdx.x over rows rows[c*kRows ...] of the batch.
 __global__ void __launch_bounds__(kThreads)
-grad_partial_kernel(const float* __restrict__ P, int d_in, int m, int act,
+grad_partial_kernel(const float* __restrict__ P, int d_in, int m, int act, int bf16,
                     const float* __restrict__ feats, const float* __restrict__ labels,
                     const int32_t* __restrict__ rows, int n_rows, float inv_bm,
                     float* __restrict__ part, float* __restrict__ loss_part) {
@@ -67,7 +74,8 @@ grad_partial_kernel(const float* __restrict__ P, int d_in, int m, int act,
     Layer L[5];
     layer_table(d_in, m, L);
     const int n_params = L[4].b_off + m;
-    for (int i = tid; i < n_params; i += kThreads) s.P[i] = P[i];
+    for (int i = tid; i < n_params; i += kThreads)
+        s.P[i] = bf16 ? __bfloat162float(__float2bfloat16_rn(P[i])) : P[i];
     const int r0 = blockIdx.x * kRows;
     const int nr = min(kRows, n_rows - r0);
     for (int i = tid; i < kRows * d_in; i += kThreads) {
@@ -233,7 +241,7 @@ size_t part_bytes(int d_in, int m, int batch) {
     return align256(static_cast<size_t>(nc * np) * 4) + align256(static_cast<size_t>(nc) * 4);
 }
 
-int launch_grad(const float* P, int d_in, int m, int act, const float* feats, const float* labels,
+int launch_grad(const float* P, int d_in, int m, int act, int bf16, const float* feats, const float* labels,
                 const int32_t* rows, int n_rows, void* ws, cudaStream_t st, float** part_out,
                 float** loss_part_out, int* n_parts) {
     const int64_t np = sl_n_params(d_in, m);
@@ -245,7 +253,7 @@ int launch_grad(const float* P, int d_in, int m, int act, const float* feats, co
     int rc = cuda_error(cudaFuncSetAttribute(grad_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(smem)), "grad attribute");
     if (rc) return rc;
-    grad_partial_kernel<<<nc, kThreads, smem, st>>>(P, d_in, m, act, feats, labels, rows, n_rows,
+    grad_partial_kernel<<<nc, kThreads, smem, st>>>(P, d_in, m, act, bf16, feats, labels, rows, n_rows,
                                                      1.0f / (static_cast<float>(n_rows) * m), part, loss_part);
     rc = cuda_error(cudaGetLastError(), "grad_partial launch");
     *part_out = part;
@@ -295,8 +303,9 @@ int sl_mse_grad(const sl_net* net, const float* feats, const float* labels, cons
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     float *part, *lp;
     int nc;
-    rc = launch_grad(net->params, net->d_in, net->m, net->act, feats, labels, rows, n_rows, ws, st,
-                     &part, &lp, &nc);
+    if (net->prec != SL_PREC_FP32 && net->prec != SL_PREC_BF16) return set_error(SL_ERR_ARG, "prec=%d", net->prec);
+    rc = launch_grad(net->params, net->d_in, net->m, net->act, net->prec == SL_PREC_BF16, feats, labels, rows,
+                     n_rows, ws, st, &part, &lp, &nc);
     if (rc) return rc;
     const int np = static_cast<int>(sl_n_params(net->d_in, net->m));
     reduce_adam_kernel<<<reduce_blocks(np), kRedThreads, 0, st>>>(part, lp, nc, np, grad, loss, nullptr, nullptr,
@@ -317,7 +326,7 @@ int sl_adam_step(float* params, float* adam_m, float* adam_v, const float* grad,
     return cuda_error(cudaGetLastError(), "adam launch");
 }
 
-int sl_train(float* params, int d_in, int m, int act, float* adam_m, float* adam_v, int64_t t0,
+int sl_train(float* params, int d_in, int m, int act, int prec, float* adam_m, float* adam_v, int64_t t0,
              const float* feats, const float* labels, const int32_t* batch_rows, int n_batches,
              int batch, float lr, float b1, float b2, float eps, float* losses, void* ws,
              size_t ws_bytes, void* stream) {
@@ -325,6 +334,7 @@ int sl_train(float* params, int d_in, int m, int act, float* adam_m, float* adam
         return set_error(SL_ERR_ARG, "NULL argument");
     int rc = check_net_shape(d_in, m, act);
     if (rc) return rc;
+    if (prec != SL_PREC_FP32 && prec != SL_PREC_BF16) return set_error(SL_ERR_ARG, "prec=%d", prec);
     if (n_batches < 0 || batch < 1 || t0 < 0) return set_error(SL_ERR_ARG, "n_batches/batch/t0 out of range");
     if (!ws || ws_bytes < part_bytes(d_in, m, batch)) return set_error(SL_ERR_WORKSPACE, "workspace too small");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -332,8 +342,8 @@ int sl_train(float* params, int d_in, int m, int act, float* adam_m, float* adam
     for (int b = 0; b < n_batches; ++b) {
         float *part, *lp;
         int nc;
-        rc = launch_grad(params, d_in, m, act, feats, labels, batch_rows + static_cast<int64_t>(b) * batch,
-                         batch, ws, st, &part, &lp, &nc);
+        rc = launch_grad(params, d_in, m, act, prec == SL_PREC_BF16, feats, labels,
+                         batch_rows + static_cast<int64_t>(b) * batch, batch, ws, st, &part, &lp, &nc);
         if (rc) return rc;
         const double t = static_cast<double>(t0 + b + 1);
         const float c1 = static_cast<float>(1.0 / (1.0 - pow(static_cast<double>(b1), t)));

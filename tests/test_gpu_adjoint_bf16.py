@@ -295,3 +295,36 @@ def test_full_size_sampled(sl, orc):
     for c in range(3):
         assert np.mean(rel_err(paths[1 + c][idx], g[:, c], 1.0)[far] <= TOL) >= MIN_AGREE, c
     assert np.all(np.isfinite(paths))
+
+
+@pytest.mark.parametrize("act,seed", [(1, 0), (1, 5), (0, 0), (0, 5), (0, 9)])
+def test_set_means_vs_central_differences(sl, orc, act, seed):
+    """The tensor-core adjoint's set means (FP64) against central differences of the oracle's FP64
+    mean payoff on the same BF16-valued weights and the same normals, h = 1e-5: within 1e-3 relative.
+    Softplus networks are smooth; for ReLU networks a path whose pre-activation sits within the BF16
+    activations' rounding (~1e-5 of its scale) of zero may follow the neighbouring linear piece, which
+    moves a mean by that path's jump over the path count -- within the same 1e-3 here."""
+    d_in, m, n, T, n_steps = 4, 7, 20000, 2.0, 8
+    P = W.near_affine_params(d_in, m, eps=0.05, seed=seed)      # paths that move like a diffusion
+    Pb = W.bf16_round(P).astype(np.float64)
+    th = np.array([[0.1, 0.3]], np.float32)
+    off = W.offsets_from_counts([n])
+    K = _strike(orc, Pb, d_in, m, th, [1.0], off, T, n_steps, 4, act=act)
+    v, d0, dth, _ = _adj(sl, P, d_in, m, th, [1.0], off, T, n_steps, 4, K, 8, sl.PREC_BF16, act=act)
+
+    def mean_payoff(y0, t):
+        yt = orc.seven_league_paths(0, Pb, [t], [y0], off, T, n_steps, m, 4, d_in=d_in, act=act)
+        return np.maximum(yt - K, 0).mean()
+    h = 1e-5
+    fd = [(mean_payoff(1.0 + h, th[0].astype(np.float64)) - mean_payoff(1.0 - h, th[0].astype(np.float64))) / (2 * h)]
+    for c in range(2):
+        tp, tm = th[0].astype(np.float64).copy(), th[0].astype(np.float64).copy()
+        tp[c] += h
+        tm[c] -= h
+        fd.append((mean_payoff(1.0, tp) - mean_payoff(1.0, tm)) / (2 * h))
+    got = [d0[0], dth[0, 0], dth[0, 1]]
+    rel = [abs(g - f) / max(abs(f), 1e-3) for g, f in zip(got, fd)]
+    print("adjoint set means", got, "central differences", fd, "relative gaps", rel)
+    assert min(abs(f) for f in fd) > 1e-3                       # every sensitivity is a real one
+    for g, f in zip(got, fd):
+        assert g == pytest.approx(f, rel=1e-3, abs=1e-6)
