@@ -106,6 +106,33 @@ def test_select_large_segment(sl, orc):
     assert np.array_equal(got[1], want[1].astype(np.float32))
 
 
+@pytest.mark.parametrize("kind", ["atom", "narrow", "spread", "mixed"])
+def test_select_value_distributions(sl, orc, kind):
+    """Value distributions that stress a radix select's digit histograms.  atom: half of each
+    segment exactly 0 (CIR's full truncation makes such atoms), ranks inside and outside it;
+    narrow: every value in [1, 1 + 2^-10), so the keys share their top 11 bits; spread: lognormal
+    values; mixed: segments of each kind in one call.  Bit for bit against the oracle's sort."""
+    rng = np.random.default_rng({"atom": 1, "narrow": 2, "spread": 3, "mixed": 4}[kind])
+    n, n_seg = 100_000, 6
+    segs = []
+    for k in range(n_seg):
+        sk = kind if kind != "mixed" else ("atom", "narrow", "spread")[k % 3]
+        if sk == "atom":
+            v = rng.lognormal(-2, 1, n)
+            v[rng.random(n) < 0.5] = 0.0
+        elif sk == "narrow":
+            v = 1.0 + rng.random(n) * 2.0 ** -10
+        else:
+            v = rng.lognormal(0, 0.5, n)
+        segs.append(v.astype(np.float32))
+    v = np.concatenate(segs)
+    off = W.offsets_from_counts([n] * n_seg)
+    ranks = np.concatenate([orc.quantile_ranks(7, n), [0, n - 1, n // 2 - 1, n // 2]])
+    got = sl.segmented_select(_dev(v), _dev(off, torch.int64), ranks).cpu().numpy()
+    want = orc.order_statistics(v, off, ranks)
+    assert np.array_equal(got, want.astype(np.float32))
+
+
 def test_labels_small(sl, orc):
     th, yi, dt = W.cir_label_rows(6)
     n, nf, m = 4000, 100, 7
