@@ -133,6 +133,29 @@ def test_select_value_distributions(sl, orc, kind):
     assert np.array_equal(got, want.astype(np.float32))
 
 
+@pytest.mark.parametrize("c", [22527, 22528, 22529, 40000])
+def test_select_candidate_capacity(sl, orc, c):
+    """A segment whose requested ranks sit in one narrow cluster of c values (1 + k 2^-22, many of
+    them repeated) among values spread over many binades: the cluster's first-digit bin holds c
+    values.  The select copies the ranks' bins to shared memory when they hold at most 22,528
+    values together, so c = 22527 and 22528 take its shared-memory finish and 22529, 40000 its
+    refining passes (with ranks outside the cluster too, every c refines).  Bit for bit against
+    the oracle's sort, ranks at both ends of the cluster."""
+    rng = np.random.default_rng(c)
+    far = np.concatenate([rng.uniform(2.0 ** -40, 2.0 ** -20, 30_000), rng.uniform(4.0, 2.0 ** 40, 30_000)])
+    cl = 1.0 + rng.integers(0, 300, c) * 2.0 ** -22
+    v = rng.permutation(np.concatenate([far, cl])).astype(np.float32)
+    n = v.size
+    lo = 30_000
+    off = np.array([0, n, 2 * n], np.int64)
+    v2 = np.concatenate([v, v[::-1]])
+    inside = [lo, lo + 1, lo + c // 3, lo + c // 2, lo + c - 2, lo + c - 1]   # the cluster's bin alone
+    for ranks in (np.array(inside), np.array(inside + [lo - 1, lo + c, 0, n - 1])):
+        got = sl.segmented_select(_dev(v2), _dev(off, torch.int64), ranks).cpu().numpy()
+        want = orc.order_statistics(v2, off, ranks)
+        assert np.array_equal(got, want.astype(np.float32))
+
+
 def test_labels_small(sl, orc):
     th, yi, dt = W.cir_label_rows(6)
     n, nf, m = 4000, 100, 7
