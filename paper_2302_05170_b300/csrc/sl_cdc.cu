@@ -940,22 +940,22 @@ __device__ __forceinline__ void cdc_paths(const SimArgs& a, const float* __restr
     }
 }
 
-// Phase 2: the paths.  Each thread takes kPair neighbouring flat paths; when they
-// belong to one set (all but the pairs that straddle a set boundary) they share the
+// Phase 2: the paths.  Each thread takes kPathsPerThread neighbouring flat paths; when they
+// belong to one set (all but the groups that straddle a set boundary) they share the
 // table loads of every step.
-constexpr int kPair = 2;
+constexpr int kPathsPerThread = 4;
 
 template <int M, int SPACE>
-__global__ void __launch_bounds__(kPathThreads, 4) cdc_path_kernel(const SimArgs a, const float* __restrict__ tab) {
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x * kPair;
-    for (int64_t g0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) * kPair; g0 < a.total;
+__global__ void __launch_bounds__(kPathThreads, 3) cdc_path_kernel(const SimArgs a, const float* __restrict__ tab) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x * kPathsPerThread;
+    for (int64_t g0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) * kPathsPerThread; g0 < a.total;
          g0 += stride) {
-        int s[kPair];
-        int64_t q[kPair], g[kPair];
-        bool write[kPair];
+        int s[kPathsPerThread];
+        int64_t q[kPathsPerThread], g[kPathsPerThread];
+        bool write[kPathsPerThread];
         bool same = true;
 #pragma unroll
-        for (int p = 0; p < kPair; ++p) {
+        for (int p = 0; p < kPathsPerThread; ++p) {
             write[p] = g0 + p < a.total;
             g[p] = write[p] ? g0 + p : g0;
             s[p] = a.offsets ? owning_set(a.offsets, a.n_sets, g[p]) : 0;
@@ -964,10 +964,10 @@ __global__ void __launch_bounds__(kPathThreads, 4) cdc_path_kernel(const SimArgs
             same = same && s[p] == s[0];
         }
         if (same) {
-            cdc_paths<M, kPair, SPACE>(a, tab + static_cast<int64_t>(s[0]) * a.n_steps * kTabFloats, s[0], q, g, write);
+            cdc_paths<M, kPathsPerThread, SPACE>(a, tab + static_cast<int64_t>(s[0]) * a.n_steps * kTabFloats, s[0], q, g, write);
         } else {
 #pragma unroll
-            for (int p = 0; p < kPair; ++p) {
+            for (int p = 0; p < kPathsPerThread; ++p) {
                 const int64_t q1[1] = {q[p]}, g1[1] = {g[p]};
                 const bool w1[1] = {write[p]};
                 cdc_paths<M, 1, SPACE>(a, tab + static_cast<int64_t>(s[p]) * a.n_steps * kTabFloats, s[p], q1, g1, w1);
@@ -1036,7 +1036,7 @@ int launch_paths_m(const SimArgs& a, const float* tab, cudaStream_t st) {
     int per_sm = 1;
     int rc = blocks_per_sm(kern, kPathThreads, 0, cache, &per_sm);
     if (rc) return rc;
-    const int64_t per_block = static_cast<int64_t>(kPathThreads) * kPair;
+    const int64_t per_block = static_cast<int64_t>(kPathThreads) * kPathsPerThread;
     const int64_t need = (a.total + per_block - 1) / per_block;
     int64_t blocks = static_cast<int64_t>(sm_count()) * per_sm;
     if (blocks > need) blocks = need;
