@@ -13,7 +13,9 @@ Prints one JSON line (rank 0).  Under torchrun (N ranks) the job is one batch
 of 16 N parameter sets (10^6 paths each) split across the ranks by path count
 (paper_2302_05170_b300.sharding): every rank runs its contiguous range of the
 flat path list, and the per-set FP64 partial moments are combined with one
-all-gather per step.  Per-GPU work is fixed as N grows: weak scaling.
+all-gather per step.  Per-GPU work is fixed as N grows: weak scaling.  The
+process group is NCCL; SL_DIST_BACKEND=gloo selects gloo (host collectives),
+and ranks beyond the visible GPUs share them (LOCAL_RANK modulo the count).
 """
 from __future__ import annotations
 
@@ -167,6 +169,8 @@ def max_over_ranks(value, device="cpu"):
     """Largest `value` over all ranks (the job's time is its slowest rank's)."""
     import torch
     import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_backend() != "nccl":
+        device = "cpu"                 # gloo: host tensors
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -316,12 +320,13 @@ def main():
     from paper_2302_05170_b300 import workloads as W
 
     world, rank, local = _dist()
+    local = local % max(torch.cuda.device_count(), 1)
     torch.cuda.set_device(local)
     if args.only_labels:
         return run_labels_only(args, torch, sl, W, local)
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        dist.init_process_group(os.environ.get("SL_DIST_BACKEND", "nccl"))
     sl.load()
     dev = torch.device("cuda", local)
     f32, i64 = torch.float32, torch.int64

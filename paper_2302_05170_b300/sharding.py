@@ -70,6 +70,8 @@ def gather_partials(count, mean, var, group=None):
     import torch.distributed as dist
     part = torch.stack([count.to(torch.float64), mean.to(torch.float64), var.to(torch.float64)])
     world, _ = _world(group)
+    if world > 1 and part.is_cuda and dist.get_backend(group) != "nccl":
+        part = part.cpu()              # gloo gathers host tensors
     if world == 1:
         parts = [part]
     else:
