@@ -1,12 +1,12 @@
 // sl_simt.cu -- FP32 CUDA-core form of the 7L online sampler (Algorithm I,
 // steps 2-8) and the deterministic FP64 per-set moments.
 //
-// One thread owns one path for the whole time loop; the state, the network's
-// activations, the normals and the collocation vector stay in registers.  The
-// network (Eq. 6.4) is evaluated with FP32 FMAs against weights staged once per
-// CTA in shared memory (every lane of a warp reads the same weight, a
-// broadcast).  The exact-collocation models (GBM lognormal map, OU map of
-// Eq. 6.6) replace the network by their closed form.
+// A thread owns its paths for the whole time loop: two per thread for the network
+// (Eq. 6.4, FP32 FMAs against weights staged once per CTA in shared memory, every
+// lane of a warp reading the same weight: a broadcast), one per thread for the
+// exact-collocation models (GBM lognormal map, OU map of Eq. 6.6), which replace
+// the network by their closed form.  The state, the normals and the collocation
+// vector stay in registers.
 #include <math.h>
 
 #include "sl_internal.cuh"
@@ -17,17 +17,10 @@ namespace {
 
 using namespace simt;
 
-// MODEL: SL_MODEL_MLP / GBM_EXACT / OU_EXACT.
-template <int MODEL, int ACT>
+// The exact-collocation models, MODEL: SL_MODEL_GBM_EXACT / SL_MODEL_OU_EXACT.
+template <int MODEL>
 __global__ void __launch_bounds__(256) simt_7l_kernel(const SimArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SmemNet& net = *reinterpret_cast<SmemNet*>(smem_raw);
-    float* act = reinterpret_cast<float*>(smem_raw + sizeof(SmemNet)) + threadIdx.x;
     const int m = a.m;
-    if (MODEL == SL_MODEL_MLP) {
-        stage_net(net, a.params, a.d_in, m);
-        __syncthreads();
-    }
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < a.total;
          g += stride) {
@@ -46,24 +39,18 @@ __global__ void __launch_bounds__(256) simt_7l_kernel(const SimArgs a) {
         // Per-path constants of the exact maps (theta is fixed along the path).
         float ex[SL_MAX_M];   // GBM: y_j = Y * ex[j];  OU: y_j = c1 * Y + ex[j]
         float c1 = 0.0f;
-        float f[DS];
-#pragma unroll
-        for (int k = 0; k < DS; ++k) f[k] = 0.0f;
         if (MODEL == SL_MODEL_GBM_EXACT) {
             const float mu = __ldg(th), sg = __ldg(th + 1);
             const float am = (mu - 0.5f * sg * sg) * a.dt, bm = sg * sqrtf(a.dt);
 #pragma unroll
             for (int j = 0; j < SL_MAX_M; ++j) ex[j] = (j < m) ? expf(fmaf(bm, a.gh.x[j], am)) : 0.0f;
-        } else if (MODEL == SL_MODEL_OU_EXACT) {
+        } else {
             const float yb = __ldg(th), sg = __ldg(th + 1), lam = __ldg(th + 2);
             c1 = expf(-lam * a.dt);
             const float sd = sg * sqrtf(-expm1f(-2.0f * lam * a.dt) / (2.0f * lam));
             const float c0 = yb * (-expm1f(-lam * a.dt));
 #pragma unroll
             for (int j = 0; j < SL_MAX_M; ++j) ex[j] = fmaf(sd, a.gh.x[j], c0);
-        } else {
-            f[1] = a.dt;
-            for (int k = 0; k < a.p && k < DS - 2; ++k) f[2 + k] = __ldg(th + k);
         }
 
         float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -73,10 +60,7 @@ __global__ void __launch_bounds__(256) simt_7l_kernel(const SimArgs a) {
                              static_cast<uint32_t>(i >> 2));
             const float X = pick4(z4, i & 3);
             float y[SL_MAX_M];
-            if (MODEL == SL_MODEL_MLP) {
-                f[0] = Y;
-                mlp_forward<ACT>(net, act, blockDim.x, f, y);
-            } else if (MODEL == SL_MODEL_GBM_EXACT) {
+            if (MODEL == SL_MODEL_GBM_EXACT) {
 #pragma unroll
                 for (int j = 0; j < SL_MAX_M; ++j) y[j] = Y * ex[j];
             } else {
@@ -91,27 +75,109 @@ __global__ void __launch_bounds__(256) simt_7l_kernel(const SimArgs a) {
     }
 }
 
-constexpr int kSimtThreads = 256;
+// The network form: two neighbouring paths per thread, every weight load feeding one packed
+// FP32x2 FMA for both (mlp_forward_x2: per path the arithmetic of mlp_forward, so the same
+// results as one path per thread, 1.47x faster on the 16 x 1e6 x 16 workload).  The parameters
+// (42 KB) and each thread's two activation columns sit in shared memory.
+constexpr int kMlpThreads = 128;
+template <int ACT>
+__global__ void __launch_bounds__(kMlpThreads) simt_7l_mlp_kernel(const SimArgs a) {
+    constexpr int NP = 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemNet& net = *reinterpret_cast<SmemNet*>(smem_raw);
+    float* act = reinterpret_cast<float*>(smem_raw + sizeof(SmemNet)) + threadIdx.x;
+    const int m = a.m;
+    stage_net(net, a.params, a.d_in, m);
+    __syncthreads();
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x * NP;
+    for (int64_t g0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) * NP; g0 < a.total;
+         g0 += stride) {
+        int s[NP];
+        int64_t q[NP], g[NP];
+        bool live[NP];
+        float Y[NP], f[NP][DS];
+        float4 z4[NP];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            live[p] = g0 + p < a.total;           // a path past the end runs and is not stored
+            g[p] = live[p] ? g0 + p : g0;
+            const int64_t gg = a.first + g[p];    // index in the whole batch (g: in this call)
+            s[p] = 0;
+            q[p] = gg;
+            if (a.offsets) {
+                s[p] = owning_set(a.offsets, a.n_sets, gg);
+                q[p] = gg - __ldg(a.offsets + s[p]);
+                if (live[p]) live[p] = path_in_set(a.offsets, s[p], gg, a.status);
+            }
+            const float* th = a.theta + static_cast<int64_t>(s[p]) * a.p;
+            Y[p] = a.Y0 ? __ldg(a.Y0 + s[p]) : a.y0_scalar;
+            if (a.out_grid && live[p]) a.out_grid[g[p]] = Y[p];
+#pragma unroll
+            for (int k = 0; k < DS; ++k) f[p][k] = 0.0f;
+            f[p][1] = a.dt;
+            for (int k = 0; k < a.p && k < DS - 2; ++k) f[p][2 + k] = __ldg(th + k);
+            z4[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        for (int i = 0; i < a.n_steps; ++i) {
+            float X[NP], y[NP][SL_MAX_M];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                if ((i & 3) == 0)
+                    z4[p] = normal4(a.seed, 0u, static_cast<uint32_t>(s[p]), static_cast<uint32_t>(q[p]),
+                                    static_cast<uint32_t>(i >> 2));
+                X[p] = pick4(z4[p], i & 3);
+                f[p][0] = Y[p];
+            }
+            mlp_forward_x2<ACT>(net, act, blockDim.x, f, y);
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                Y[p] = lagrange_eval_m(y[p], X[p], a.gh, m);
+                if (a.out_grid && live[p]) a.out_grid[static_cast<int64_t>(i + 1) * a.total + g[p]] = Y[p];
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            if (!live[p]) continue;
+            if (a.out_YT) a.out_YT[g[p]] = Y[p];
+            if (!isfinite(Y[p])) raise_status(a.status, SL_DEV_NONFINITE);
+        }
+    }
+}
 
-template <int MODEL, int ACT>
-int launch_one(const SimArgs& a, cudaStream_t st) {
-    auto kern = simt_7l_kernel<MODEL, ACT>;
-    const size_t smem = (MODEL == SL_MODEL_MLP)
-                            ? sizeof(SmemNet) + static_cast<size_t>(W) * kSimtThreads * sizeof(float)
-                            : 0;
+template <int ACT>
+int launch_mlp(const SimArgs& a, cudaStream_t st) {
+    auto kern = simt_7l_mlp_kernel<ACT>;
+    const size_t smem = sizeof(SmemNet) + static_cast<size_t>(W) * 2 * kMlpThreads * sizeof(float);
     int rc = cuda_error(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(smem)),
-                        "simt_7l attribute");
+                        "simt_7l_mlp attribute");
     if (rc) return rc;
     int per_sm = 0;
-    rc = cuda_error(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSimtThreads, smem),
-                    "simt_7l occupancy");
+    rc = cuda_error(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMlpThreads, smem),
+                    "simt_7l_mlp occupancy");
+    if (rc) return rc;
+    const int64_t per_block = static_cast<int64_t>(kMlpThreads) * 2;
+    const int64_t need = (a.total + per_block - 1) / per_block;
+    int64_t blocks = static_cast<int64_t>(sm_count()) * (per_sm > 0 ? per_sm : 1);
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    kern<<<static_cast<unsigned>(blocks), kMlpThreads, smem, st>>>(a);
+    return cuda_error(cudaGetLastError(), "simt_7l_mlp launch");
+}
+constexpr int kSimtThreads = 256;
+
+template <int MODEL>
+int launch_one(const SimArgs& a, cudaStream_t st) {
+    auto kern = simt_7l_kernel<MODEL>;
+    int per_sm = 0;
+    int rc = cuda_error(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSimtThreads, 0),
+                        "simt_7l occupancy");
     if (rc) return rc;
     const int64_t need = (a.total + kSimtThreads - 1) / kSimtThreads;
     int64_t blocks = static_cast<int64_t>(sm_count()) * (per_sm > 0 ? per_sm : 1);
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    kern<<<static_cast<unsigned>(blocks), kSimtThreads, smem, st>>>(a);
+    kern<<<static_cast<unsigned>(blocks), kSimtThreads, 0, st>>>(a);
     return cuda_error(cudaGetLastError(), "simt_7l launch");
 }
 
@@ -193,10 +259,10 @@ int moments_chunks(int n_sets) {
 
 int launch_simt_7l(int model, int m, const SimArgs& a, cudaStream_t st) {
     if (m < SL_MIN_M || m > SL_MAX_M) return set_error(SL_ERR_UNSUPPORTED, "m=%d", m);
-    if (model == SL_MODEL_GBM_EXACT) return launch_one<SL_MODEL_GBM_EXACT, 0>(a, st);
-    if (model == SL_MODEL_OU_EXACT) return launch_one<SL_MODEL_OU_EXACT, 0>(a, st);
-    if (a.act == SL_ACT_SOFTPLUS) return launch_one<SL_MODEL_MLP, SL_ACT_SOFTPLUS>(a, st);
-    return launch_one<SL_MODEL_MLP, SL_ACT_RELU>(a, st);
+    if (model == SL_MODEL_GBM_EXACT) return launch_one<SL_MODEL_GBM_EXACT>(a, st);
+    if (model == SL_MODEL_OU_EXACT) return launch_one<SL_MODEL_OU_EXACT>(a, st);
+    if (a.act == SL_ACT_SOFTPLUS) return launch_mlp<SL_ACT_SOFTPLUS>(a, st);
+    return launch_mlp<SL_ACT_RELU>(a, st);
 }
 
 int launch_range_offsets(const int64_t* offsets, int n_sets, int64_t first, int64_t n, int64_t* local,

@@ -119,5 +119,85 @@ __device__ __forceinline__ void mlp_forward(const SmemNet& s, float* act, int nt
     for (int o = 0; o < SL_MAX_M; ++o) y[o] = dot50(s.W5 + o * WS, h, s.b5[o]);
 }
 
+// acc = (w, w) * (h0, h1) + acc for two paths in one packed FP32x2 FMA (each half rounds like
+// fmaf: the same results as two scalar FMAs).
+__device__ __forceinline__ void fma2w(float w, float h0, float h1, float& a0, float& a1) {
+    asm("{\n.reg .b64 ww, hh, aa;\nmov.b64 ww, {%2, %2};\nmov.b64 hh, {%3, %4};\nmov.b64 aa, {%0, %1};\n"
+        "fma.rn.f32x2 aa, ww, hh, aa;\nmov.b64 {%0, %1}, aa;\n}"
+        : "+f"(a0), "+f"(a1)
+        : "f"(w), "f"(h0), "f"(h1));
+}
+
+// Two paths per thread with packed FMAs (the same arithmetic per path as mlp_forward).
+template <int ACT>
+__device__ __forceinline__ void mlp_forward_x2(const SmemNet& s, float* act, int nt,
+                                               const float (&f)[2][DS], float (&y)[2][SL_MAX_M]) {
+#pragma unroll 2
+    for (int o = 0; o < W; ++o) {
+        const float4 a = *reinterpret_cast<const float4*>(s.W1 + o * DS);
+        const float4 b = *reinterpret_cast<const float4*>(s.W1 + o * DS + 4);
+        float a0 = s.b1[o], a1 = a0;
+        fma2w(a.x, f[0][0], f[1][0], a0, a1);
+        fma2w(a.y, f[0][1], f[1][1], a0, a1);
+        fma2w(a.z, f[0][2], f[1][2], a0, a1);
+        fma2w(a.w, f[0][3], f[1][3], a0, a1);
+        fma2w(b.x, f[0][4], f[1][4], a0, a1);
+        fma2w(b.y, f[0][5], f[1][5], a0, a1);
+        fma2w(b.z, f[0][6], f[1][6], a0, a1);
+        fma2w(b.w, f[0][7], f[1][7], a0, a1);
+        act[o * nt] = activation<ACT>(a0);
+        act[(W + o) * nt] = activation<ACT>(a1);
+    }
+    float h0[W], h1[W];
+    for (int l = 0; l < 3; ++l) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            h0[k] = act[k * nt];
+            h1[k] = act[(W + k) * nt];
+        }
+#pragma unroll 2
+        for (int o = 0; o < W; ++o) {
+            const float* row = s.Wh[l] + o * WS;
+            float a0 = s.bh[l][o], a1 = a0;
+#pragma unroll
+            for (int k = 0; k < 48; k += 4) {
+                const float4 w4 = *reinterpret_cast<const float4*>(row + k);
+                fma2w(w4.x, h0[k], h1[k], a0, a1);
+                fma2w(w4.y, h0[k + 1], h1[k + 1], a0, a1);
+                fma2w(w4.z, h0[k + 2], h1[k + 2], a0, a1);
+                fma2w(w4.w, h0[k + 3], h1[k + 3], a0, a1);
+            }
+            const float2 w2 = *reinterpret_cast<const float2*>(row + 48);
+            fma2w(w2.x, h0[48], h1[48], a0, a1);
+            fma2w(w2.y, h0[49], h1[49], a0, a1);
+            act[o * nt] = activation<ACT>(a0);
+            act[(W + o) * nt] = activation<ACT>(a1);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        h0[k] = act[k * nt];
+        h1[k] = act[(W + k) * nt];
+    }
+#pragma unroll
+    for (int o = 0; o < SL_MAX_M; ++o) {
+        const float* row = s.W5 + o * WS;
+        float a0 = s.b5[o], a1 = a0;
+#pragma unroll
+        for (int k = 0; k < 48; k += 4) {
+            const float4 w4 = *reinterpret_cast<const float4*>(row + k);
+            fma2w(w4.x, h0[k], h1[k], a0, a1);
+            fma2w(w4.y, h0[k + 1], h1[k + 1], a0, a1);
+            fma2w(w4.z, h0[k + 2], h1[k + 2], a0, a1);
+            fma2w(w4.w, h0[k + 3], h1[k + 3], a0, a1);
+        }
+        const float2 w2 = *reinterpret_cast<const float2*>(row + 48);
+        fma2w(w2.x, h0[48], h1[48], a0, a1);
+        fma2w(w2.y, h0[49], h1[49], a0, a1);
+        y[0][o] = a0;
+        y[1][o] = a1;
+    }
+}
+
 }  // namespace simt
 }  // namespace sl
