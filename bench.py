@@ -715,6 +715,7 @@ def main():
         y0_a = torch.ones(1, device=dev)
         ws_a = torch.empty(sl.adjoint_workspace_size(n_a, 1, 64, 8, 2), dtype=torch.uint8, device=dev)
         paths_a = torch.empty((4, n_a), dtype=f32, device=dev)
+        per_path_a = {}
         ncdf = lambda x: 0.5 * math.erfc(-x / math.sqrt(2.0))
         d1 = (math.log(1.0 / K_a) + (mu_a + 0.5 * sg_a ** 2) * T_a) / (sg_a * math.sqrt(T_a))
         secondary["adjoint_black_scholes"] = {
@@ -741,6 +742,7 @@ def main():
             vals = [v_a.item(), d0_a.item()] + dth_a[0].tolist()
             secondary[key + "_result"] = {k: [round(a, 6), round(b, 6)] for k, a, b in
                                           zip(("value", "dY0", "dmu", "dsigma"), vals, se)}
+            per_path_a[key] = paths_a.double().clone()
             if model_a == sl.MODEL_MLP:
                 ix = sample_idx(W.offsets_from_counts([n_a]), 2000)
                 Pn = Pa.cpu().numpy()
@@ -753,7 +755,18 @@ def main():
                                          "value and its derivatives in Y0, mu, sigma; networks trained over dt "
                                          "1/64..1 (adjoint_bf16_softplus: a Softplus network trained as such); "
                                          "adjoint_exact_map: the exact GBM collocation map on the same normals")
-        del paths_a
+        # each network's own error, stated per result: per path, the network chain's payoff and its
+        # derivatives minus the exact map's on the same normals (paired, so the Monte Carlo noise
+        # they share cancels); [mean, standard error].  A network result = the exact map's (itself
+        # within its standard error of Black-Scholes) + this error.
+        ex_a = per_path_a.pop("adjoint_exact_map")
+        for key, pp in per_path_a.items():
+            dd = pp - ex_a
+            secondary[key + "_network_error"] = {
+                k: [round(a, 6), round(b, 6)] for k, a, b in
+                zip(("value", "dY0", "dmu", "dsigma"), dd.mean(dim=1).tolist(),
+                    (dd.std(dim=1) / math.sqrt(n_a)).tolist())}
+        del paths_a, per_path_a, ex_a
         # CIR adjoint on the trained CIR network (BF16 tcgen05 form): kappa=1, ybar=0.1, gamma=0.3,
         # Y0=0.1, 1e6 paths x 64 steps of dt=0.25 (inside the label rows' dt range), checkpoint every 8;
         # call K=1 lies far above the CIR range (every sensitivity is 0), K=ybar is the meaningful case

@@ -7,7 +7,7 @@
 //   layer 5:   [128 paths x K=112] x [K x N=16]      (m <= 8 outputs used)
 // A persistent CTA (one per SM) holds S independent path tiles ("slots") of
 // 128 paths.  Warpgroup t (warps 4t..4t+3, TMEM lanes 32*(warp%4)..) owns
-// slot t: its warp 0 issues the slot's tcgen05.mma (one elected lane), with B
+// slot t: its warp t % 4 issues the slot's tcgen05.mma (one elected lane), with B
 // (weights) in shared memory through 128-byte-swizzled K-major descriptors, A
 // (activations) and FP32 accumulators in tensor memory; all four warps are the
 // slot's epilogue: each thread reads the accumulator row of its path with
@@ -29,8 +29,12 @@
 //
 // Synchronisation: the four warps of a slot meet at a named barrier (an AND
 // reduction, so a failed wait stops all four together) once the next A operand
-// is written; warp 0 then issues the layer's MMAs and commits them to the
-// slot's mbarrier d_ready, on which all four warps wait.  Every wait is bounded
+// is written; the issuing warp then issues the layer's MMAs and commits them to
+// the slot's mbarrier d_ready, on which all four warps wait.  Warp w runs on SM
+// sub-partition w % 4, so warpgroup t issuing from its warp t % 4 spreads the
+// slots' issue work over the four sub-partitions (with every slot issuing from
+// its warp 0, sub-partition 0 carried all of it, and its warps arrived last at
+// every hand-off: 11.5 ms against 11.0 ms on the 16 x 1e6 x 16 workload).  Every wait is bounded
 // (about one second of global time); on expiry the kernel sets SL_DEV_TIMEOUT
 // in the status word, the slot stops, every issuer drains its own MMAs
 // (bounded) and the tensor memory is released.
@@ -43,7 +47,7 @@ using namespace tc;
 
 // WG warpgroups per CTA, TPW path tiles per warpgroup (S = WG * TPW tiles in
 // flight).  Warp w of a warpgroup reads and writes TMEM lanes 32(w%4).., i.e.
-// paths 32(w%4).. of each of its tiles; warp 0 of the warpgroup also issues the
+// paths 32(w%4).. of each of its tiles; warp wg % 4 of the warpgroup also issues the
 // tiles' MMAs.  With TPW = 2 the warpgroup alternates between its two tiles
 // layer by layer, so one tile's epilogue runs while the other tile's MMAs run
 // ("ping-pong"); with TPW = 1 the overlap comes only from other warpgroups.
@@ -63,7 +67,7 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_7l_kernel(const SimArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wg = warp >> 2, wq = warp & 3;
     const int r = wq * 32 + lane;                                          // row = TMEM lane = path in tile
-    const bool issuer = (wq == 0);
+    const bool issuer = (wq == (wg & 3));                                 // sub-partition wg % 4
 
     if (threadIdx.x == 0) {
         for (int k = 0; k < S; ++k) mbar_init(smem_u32(&bars[k]), 1);   // d_ready: tcgen05.commit

@@ -8,7 +8,7 @@
 //  2. itm_compact_kernel: f(Y_T) for every path, zero sensitivities for the
 //     out-of-the-money paths (Y_T <= K), and the list of in-the-money paths;
 //  3. tc_adjoint_reverse_kernel over that list only, 128 listed paths per tile
-//     (one warpgroup, warp 0 issues the MMAs), lambda = 1 at Y_T; per segment
+//     (one warpgroup, one of its warps issues the MMAs), lambda = 1 at Y_T; per segment
 //     (last first), in blocks of at most 8 steps (last first):
 //     a. a forward pass over the block from its first state (the checkpoint,
 //        or for a segment longer than 8 steps a state recomputed first) that
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wg = warp >> 2, wq = warp & 3;
     const int r = wq * 32 + lane;
-    const bool issuer = (wq == 0);
+    const bool issuer = (wq == (wg & 3));   // one issuing warp per SM sub-partition (as the sampler)
 
     if (threadIdx.x == 0) {
         for (int q = 0; q < S; ++q) mbar_init(smem_u32(&bars[q]), 1);

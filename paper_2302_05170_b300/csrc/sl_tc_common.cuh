@@ -421,7 +421,7 @@ __device__ __forceinline__ void tile_features(Tile& T, const SimArgs& a) {
     tc_fence_before();
 }
 
-// All four warps agree (named-barrier AND) that the next A is written; warp 0
+// All four warps agree (named-barrier AND) that the next A is written; the issuing warp
 // then issues layer l's MMAs and commits them to the tile's d_ready.
 __device__ __forceinline__ bool tile_sync_issue(const Tile& T, const IssueConst& C, int l, bool ok, bool issuer) {
     ok = bar_and(T.bar_id, ok);

@@ -106,17 +106,28 @@ def test_select_large_segment(sl, orc):
     assert np.array_equal(got[1], want[1].astype(np.float32))
 
 
-@pytest.mark.parametrize("kind", ["atom", "narrow", "spread", "mixed"])
+@pytest.mark.parametrize("kind", ["atom", "atom_denormal", "narrow", "spread", "mixed"])
 def test_select_value_distributions(sl, orc, kind):
     """Value distributions that stress a radix select's digit histograms.  atom: half of each
     segment exactly 0 (CIR's full truncation makes such atoms), ranks inside and outside it;
-    narrow: every value in [1, 1 + 2^-10), so the keys share their top 11 bits; spread: lognormal
-    values; mixed: segments of each kind in one call.  Bit for bit against the oracle's sort."""
-    rng = np.random.default_rng({"atom": 1, "narrow": 2, "spread": 3, "mixed": 4}[kind])
+    atom_denormal: the atom (+0 and -0) shares its first-digit bin with positive denormals, and
+    ranks fall on both sides of the zeros' count inside that bin; narrow: every value in
+    [1, 1 + 2^-10), so the keys share their top 11 bits; spread: lognormal values; mixed: segments
+    of each kind in one call.  Bit for bit against the oracle's sort."""
+    rng = np.random.default_rng({"atom": 1, "narrow": 2, "spread": 3, "mixed": 4, "atom_denormal": 5}[kind])
     n, n_seg = 100_000, 6
     segs = []
     for k in range(n_seg):
         sk = kind if kind != "mixed" else ("atom", "narrow", "spread")[k % 3]
+        if sk == "atom_denormal":
+            v = rng.lognormal(-2, 1, n).astype(np.float32)
+            z = rng.random(n)
+            v[z < 0.3] = 0.0
+            v[(z >= 0.3) & (z < 0.35)] = -0.0
+            den = (z >= 0.35) & (z < 0.36)            # ~1000 positive denormals in the +0 bin
+            v[den] = (rng.integers(1, 1 << 18, int(den.sum())).astype(np.uint32)).view(np.float32)
+            segs.append(v)
+            continue
         if sk == "atom":
             v = rng.lognormal(-2, 1, n)
             v[rng.random(n) < 0.5] = 0.0
@@ -128,9 +139,14 @@ def test_select_value_distributions(sl, orc, kind):
     v = np.concatenate(segs)
     off = W.offsets_from_counts([n] * n_seg)
     ranks = np.concatenate([orc.quantile_ranks(7, n), [0, n - 1, n // 2 - 1, n // 2]])
+    if kind == "atom_denormal":   # around the end of the zeros, inside the denormals, just above them
+        nz = int(np.sum(v[:n] == 0.0))
+        ranks = np.concatenate([ranks, [nz - 1, nz, nz + 1, nz + 500, 36_500]])
     got = sl.segmented_select(_dev(v), _dev(off, torch.int64), ranks).cpu().numpy()
     want = orc.order_statistics(v, off, ranks)
     assert np.array_equal(got, want.astype(np.float32))
+    if kind == "atom_denormal":
+        assert np.any((want > 0) & (want < 1.2e-38))          # some ranks landed on denormals
 
 
 @pytest.mark.parametrize("c", [22527, 22528, 22529, 40000])
