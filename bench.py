@@ -310,6 +310,8 @@ def main():
     ap.add_argument("--only-labels", action="store_true",
                     help="time only the offline label stage (CIR, 1024 rows x 1e5 paths x 100 fine steps)")
     ap.add_argument("--train-steps", type=int, default=40000)
+    ap.add_argument("--tc-config", default=None,
+                    help="tensor-core launch shape 'slots/tiles-per-warpgroup' (e.g. 4/1) instead of autotuning")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -386,7 +388,13 @@ def main():
         return r
 
     tuning = None
-    if prec == sl.PREC_BF16:
+    if prec == sl.PREC_BF16 and args.tc_config:   # a fixed launch shape (profiling), no autotuning
+        slots, tpw = (int(x) for x in args.tc_config.split("/"))
+        sl.tc_set_pipeline(1)
+        sl.tc_set_slots(slots)
+        sl.tc_set_pipeline(tpw)
+        tuning = {"tc_slots": slots, "tc_tiles_per_warpgroup": tpw, "ms_by_config": None}
+    elif prec == sl.PREC_BF16:
         from paper_2302_05170_b300 import autotune
         best, tms = autotune.tune_slots(lambda: step(out_mean=None, out_var=None),
                                         "gbm-online d4 m7 s16 n%d" % total, use_cache=False)
