@@ -210,11 +210,12 @@ __device__ __forceinline__ void tile_cotangent(const Tile& T, float lam) {
 }
 
 // Normal of step i and the Lagrange basis at it, for any order of steps: the
-// block of four normals is redrawn whenever step i falls in another block.
+// block of four normals is redrawn whenever step i falls in another block, with
+// the forward sweep's generator (normal4_fast, as the sampler's tile_rng).
 __device__ __forceinline__ void tile_rng_any(Tile& T, const SimArgs& a, int i, int& blk) {
     if ((i >> 2) != blk) {
         blk = i >> 2;
-        T.z4 = normal4(a.seed, 0u, static_cast<uint32_t>(T.s), T.q, static_cast<uint32_t>(blk));
+        T.z4 = normal4_fast(a.seed, 0u, static_cast<uint32_t>(T.s), T.q, static_cast<uint32_t>(blk));
     }
     lagrange_basis_m(pick4(T.z4, i & 3), a.gh, a.m, T.lb);
 }

@@ -9,6 +9,7 @@
 #include <math.h>
 
 #include "sl_internal.cuh"
+#include "sl_fastnormal.cuh"
 
 namespace sl {
 namespace tc {
@@ -439,10 +440,13 @@ __device__ __forceinline__ bool tile_sync_issue(const Tile& T, const IssueConst&
     return ok;
 }
 
-// Normal of step i and the Lagrange basis at it (independent of the network).
+// Normal of step i and the Lagrange basis at it (independent of the network).  The normals
+// are normal4's Philox words and Box-Muller pairs on the special-function unit (normal4_fast:
+// a few 1e-7 of the normal's scale from normal4; 1.3 % of the sampler's time, which follows
+// its instruction count); the tensor-core adjoint redraws them the same way.
 __device__ __forceinline__ void tile_rng(Tile& T, const SimArgs& a, int i) {
     if ((i & 3) == 0)
-        T.z4 = normal4(a.seed, 0u, static_cast<uint32_t>(T.s), T.q, static_cast<uint32_t>(i >> 2));
+        T.z4 = normal4_fast(a.seed, 0u, static_cast<uint32_t>(T.s), T.q, static_cast<uint32_t>(i >> 2));
     lagrange_basis_m(pick4(T.z4, i & 3), a.gh, a.m, T.lb);
 }
 
