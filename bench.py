@@ -72,7 +72,7 @@ def sample_idx(offsets, per_set, seed=12):
 # DRAM traffic of the sampler kernel on the default workload, from the committed ncu summary;
 # used only while the kernel's sources are those the counters were taken on.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "tc_7l_kernel_gbm_online.md")
-KERNEL_SOURCES = ("sl_tc.cu", "sl_tc_common.cuh", "sl_internal.cuh")
+KERNEL_SOURCES = ("sl_tc.cu", "sl_tc_common.cuh", "sl_internal.cuh", "sl_fastnormal.cuh")
 
 
 def kernel_source_hash() -> str:
