@@ -811,7 +811,7 @@ def main():
         P_ou, _, _ = pipeline.train_ou_network(n_rows=1 << 14, n_steps=20000, dts=tuple(0.125 * np.arange(1, 17)),
                                                device=dev)
         th_ou, y0_ou = torch.tensor([[0.5, 0.3, 1.0]], device=dev), torch.tensor([1.5], device=dev)
-        ou_ms = {}
+        ou_ms, ou_graph_ms = {}, {}
         for pr, key in ((sl.PREC_BF16, "bf16"), (sl.PREC_FP32, "fp32"), (sl.PREC_FP32, "cdc"), (sl.PREC_FP32, "cdc_y")):
             net_ou = sl.make_net(P_ou, 5, 5, prec=pr)
             for n_ou in (1000, 50000, 100000, 200000):
@@ -836,6 +836,23 @@ def main():
                 e1.record(stream)
                 torch.cuda.synchronize()
                 ou_ms["%s_%d" % (key, n_ou)] = round(e0.elapsed_time(e1) / 10, 4)
+                # the same run replayed from a CUDA graph: device time without the Python binding's
+                # per-call host work
+                try:
+                    g_ou = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(g_ou):
+                        run_ou()
+                    g_ou.replay()
+                    torch.cuda.synchronize()
+                    e0.record(stream)
+                    for _ in range(10):
+                        g_ou.replay()
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ou_graph_ms["%s_%d" % (key, n_ou)] = round(e0.elapsed_time(e1) / 10, 4)
+                    del g_ou
+                except RuntimeError as e:
+                    ou_graph_ms["%s_%d" % (key, n_ou)] = "not captured: %s" % str(e)[:80]
             ix = sample_idx(W.offsets_from_counts([n_ou]), 3000)
             Pn = P_ou.cpu().numpy()
             checks.append(dict(name="ou_" + key, kind="cdcq" if key == "cdc" else ("cdc" if key == "cdc_y" else "paths"),
@@ -847,9 +864,12 @@ def main():
                                              out_YT=yt_ex, total_paths=200000)
             secondary["ou_pathwise_err_" + key] = float((yt_ou - yt_ex).abs().mean().item())
         secondary["ou_table61_ms_per_run"] = ou_ms
+        secondary["ou_table61_graph_ms_per_run"] = ou_graph_ms
         secondary["ou_table61_workload"] = ("OU (Ybar 0.5, sigma 0.3, lambda 1, Y0 1.5), m=5, trained 5->50x4->5 ReLU "
                                             "network (horizons 0.125..2), T=2 in 16 steps; paths 1e3/5e4/1e5/2e5 as "
-                                            "in Table 6.1; keys bf16/fp32 = 7L scheme, cdc / cdc_y = 7L-CDC scheme (quantile coordinate / Y)")
+                                            "in Table 6.1; keys bf16/fp32 = 7L scheme, cdc / cdc_y = 7L-CDC scheme (quantile coordinate / Y); "
+                                            "ms_per_run: ten calls through the Python binding, graph_ms_per_run: "
+                                            "ten replays of a CUDA graph of one call")
 
     # --- end to end through the C ABI with host buffers (pinned), copies timed.  Every step copies
     # its inputs host -> device, runs the sampler and copies Y_T and the set moments back; the steps
