@@ -27,9 +27,9 @@
 // columns (one store per chunk); the features sit in the slot's last 8 columns,
 // written once per tile except Y's word.
 //
-// Synchronisation: the four warps of a slot meet at a named barrier (an AND
-// reduction, so a failed wait stops all four together) once the next A operand
-// is written; the issuing warp then issues the layer's MMAs and commits them to
+// Synchronisation: the four warps of a slot meet at a named barrier once the
+// next A operand is written (at the end of every step an AND reduction, so a
+// failed wait stops all four together); the issuing warp then issues the layer's MMAs and commits them to
 // the slot's mbarrier d_ready, on which all four warps wait.  Warp w runs on SM
 // sub-partition w % 4, so warpgroup t issuing from its warp t % 4 spreads the
 // slots' issue work over the four sub-partitions (with every slot issuing from
@@ -128,25 +128,21 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_7l_kernel(const SimArgs a) {
             for (int l = 1; l <= 4; ++l) {
 #pragma unroll
                 for (int j = 0; j < TPW; ++j) {
-                    const bool w = tile_wait(T[j], abort_flag, a.status);
-                    if (w) tile_hidden_act<ACT>(T[j]);
-                    ok = tile_sync_issue(T[j], C, l, w, issuer);
-                    if (!ok) break;
+                    ok &= tile_wait(T[j], abort_flag, a.status);
+                    tile_hidden_act<ACT>(T[j]);
+                    tile_sync_issue_all(T[j], C, l, issuer);
                     // the step's normal and Lagrange basis while the output layer's MMAs run
                     if (l == 4) tile_rng(T[j], a, i);
                 }
-                if (!ok) break;
             }
-            if (!ok) break;
 #pragma unroll
             for (int j = 0; j < TPW; ++j) {
-                bool w = tile_wait(T[j], abort_flag, a.status);
-                if (w) tile_out(T[j], a, i);
+                ok &= tile_wait(T[j], abort_flag, a.status);
+                tile_out(T[j], a, i);
                 if (i + 1 < a.n_steps) {
-                    if (w) tile_features(T[j], a);
-                    w = tile_sync_issue(T[j], C, 0, w, issuer);
+                    tile_features(T[j], a);
+                    tile_sync_issue_all(T[j], C, 0, issuer);
                 }
-                ok = ok && w;
             }
             // Every warp of the warpgroup must take the same branch below and meet the
             // same named barriers afterwards: agree on `ok` (also after the last step).

@@ -106,7 +106,24 @@ struct IssueConstT {
     uint64_t db5, db4, db3, db2, db1;   // transposed B descriptors, in chain order
 };
 
-// Backward MMAs of chain step lt (0: W5^T, 1: W4^T, 2: W3^T, 3: W2^T, 4: W1^T).
+// Backward MMAs of chain step lt (0: W5^T, 1: W4^T, 2: W3^T, 3: W2^T, 4: W1^T), issued after the
+// warpgroup's named barrier whatever the waits before returned (as tile_sync_issue_all).
+__device__ __forceinline__ void tile_sync_issue_T_all(const Tile& T, const IssueConstT& C, int lt, bool issuer) {
+    asm volatile("bar.sync %0, 128;" ::"r"(T.bar_id) : "memory");
+    if (issuer) {
+        constexpr uint32_t kIdesc64 = idesc_bf16(128, 64), kIdesc16 = idesc_bf16(128, 16);
+        tc_fence_after();
+        if (lt == 0) {
+            mma1_ta_commit(T.d_tmem, T.d_tmem + 64, C.db5, kIdesc64, T.d_bar);
+        } else {
+            const uint64_t db = (lt == 1) ? C.db4 : (lt == 2) ? C.db3 : (lt == 3) ? C.db2 : C.db1;
+            mma7_ta_commit(T.d_tmem, T.d_tmem + 64, db, (lt < 4) ? (64 * kRowBytes) >> 4 : (16 * kRowBytes) >> 4,
+                           (lt < 4) ? kIdesc64 : kIdesc16, T.d_bar);
+        }
+    }
+}
+
+// The same with the warpgroup's AND of ok (the Softplus chain, whose recomputes branch on it).
 __device__ __forceinline__ bool tile_sync_issue_T(const Tile& T, const IssueConstT& C, int lt, bool ok, bool issuer) {
     ok = bar_and(T.bar_id, ok);
     if (ok && issuer) {
@@ -364,23 +381,21 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
             constexpr int kBlk = (ACT == SL_ACT_RELU) ? kMaskSteps : 1;
             if (i1 - i0 > kBlk) {
                 // a long segment: recompute its states first (Y_{i0+1} .. Y_{i1-1})
+                // (one failure check per step, at its AND barrier, as in the sampler)
                 for (int i = i0; i < i1 - 1; ++i) {
                     T.Y = Ys[i - i0];
                     tile_features(T, a);
-                    ok = tile_sync_issue(T, C, 0, ok, issuer);
-                    if (!ok) break;
+                    tile_sync_issue_all(T, C, 0, issuer);
                     tile_rng_any(T, a, i, blk);
 #pragma unroll
                     for (int l = 1; l <= 4; ++l) {
-                        const bool w = tile_wait(T, abort_flag, a.status);
-                        if (w) tile_hidden_act<ACT>(T);
-                        ok = tile_sync_issue(T, C, l, w, issuer);
-                        if (!ok) break;
+                        ok &= tile_wait(T, abort_flag, a.status);
+                        tile_hidden_act<ACT>(T);
+                        tile_sync_issue_all(T, C, l, issuer);
                     }
-                    if (!ok) break;
-                    const bool w = tile_wait(T, abort_flag, a.status);
-                    if (w) tile_out(T, a, i);
-                    ok = bar_and(T.bar_id, w);
+                    ok &= tile_wait(T, abort_flag, a.status);
+                    tile_out(T, a, i);
+                    ok = bar_and(T.bar_id, ok);
                     if (!ok) break;
                     Ys[i - i0 + 1] = T.Y;
                 }
@@ -435,40 +450,34 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
                 T.Y = Ys[j0 - i0];
                 for (int i = j0; i < j1; ++i) {
                     tile_features(T, a);
-                    ok = tile_sync_issue(T, C, 0, ok, issuer);
-                    if (!ok) break;
+                    tile_sync_issue_all(T, C, 0, issuer);
                     tile_rng_any(T, a, i, blk);
 #pragma unroll
                     for (int l = 1; l <= 4; ++l) {
-                        const bool w = tile_wait(T, abort_flag, a.status);
-                        if (w) tile_hidden_rec(T, tmask + ((i - j0) * 4 + (l - 1)) * 2 * kTile);
-                        ok = tile_sync_issue(T, C, l, w, issuer);
-                        if (!ok) break;
+                        ok &= tile_wait(T, abort_flag, a.status);
+                        tile_hidden_rec(T, tmask + ((i - j0) * 4 + (l - 1)) * 2 * kTile);
+                        tile_sync_issue_all(T, C, l, issuer);
                     }
-                    if (!ok) break;
-                    const bool w = tile_wait(T, abort_flag, a.status);
-                    if (w) tile_out(T, a, i);
-                    ok = bar_and(T.bar_id, w);
+                    ok &= tile_wait(T, abort_flag, a.status);
+                    tile_out(T, a, i);
+                    ok = bar_and(T.bar_id, ok);
                     if (!ok) break;
                 }
                 for (int i = j1 - 1; ok && i >= j0; --i) {
                     // backward chain with c_j = lambda * ell_j(X_i)
                     tile_rng_any(T, a, i, blk);
                     tile_cotangent(T, lam);
-                    ok = tile_sync_issue_T(T, CT, 0, ok, issuer);
-                    if (!ok) break;
+                    tile_sync_issue_T_all(T, CT, 0, issuer);
 #pragma unroll
                     for (int lt = 1; lt <= 4; ++lt) {   // dh4 -> W4^T, dh3 -> W3^T, dh2 -> W2^T, dh1 -> W1^T
-                        const bool w = tile_wait(T, abort_flag, a.status);
+                        ok &= tile_wait(T, abort_flag, a.status);
                         const uint32_t* mr = tmask + ((i - j0) * 4 + (4 - lt)) * 2 * kTile;
-                        if (w) tile_backward_bits(T, mr[0], mr[kTile]);
-                        ok = tile_sync_issue_T(T, CT, lt, w, issuer);
-                        if (!ok) break;
+                        tile_backward_bits(T, mr[0], mr[kTile]);
+                        tile_sync_issue_T_all(T, CT, lt, issuer);
                     }
-                    if (!ok) break;
                     // d/d(features): lambda <- d/dY_i, g_theta += d/dtheta
-                    const bool w = tile_wait(T, abort_flag, a.status);
-                    if (w) {
+                    ok &= tile_wait(T, abort_flag, a.status);
+                    {
                         tc_fence_after();
                         uint32_t gf[8];
                         tmem_ld8(T.taddr, gf);
@@ -479,7 +488,7 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
                         for (int q = 0; q < SL_MAX_DIN_TC - 2; ++q)
                             if (q < p) gth[q] += __uint_as_float(gf[2 + q]);
                     }
-                    ok = bar_and(T.bar_id, w);
+                    ok = bar_and(T.bar_id, ok);
                 }
                 j1 = j0;
             }

@@ -90,11 +90,13 @@ static __device__ __noinline__ bool mbar_wait_slow(uint32_t addr, uint32_t parit
     }
 }
 
+// One suspending try inline (it returns when the phase completes, which is the common case);
+// the retries, the abort check and the time limit live in the out-of-line slow path.  Every
+// instruction counts here: the kernels' time follows their instruction count, and a retry loop
+// inline cost 1.3 % of the sampler's launch.
 __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, volatile int* abort_flag,
                                           unsigned* status) {
-#pragma unroll 1
-    for (int it = 0; it < 64; ++it)
-        if (mbar_try_wait(addr, parity)) return true;
+    if (mbar_try_wait(addr, parity)) return true;
     return mbar_wait_slow(addr, parity, abort_flag, status);
 }
 
@@ -438,6 +440,26 @@ __device__ __forceinline__ bool tile_sync_issue(const Tile& T, const IssueConst&
         }
     }
     return ok;
+}
+
+// The hot loop's hand-off: the tile's four warps meet at their named barrier (the next A row is
+// written), then the issuing warp issues layer l's MMAs whatever the waits before returned.  A
+// failed wait (the abort flag or the time limit) is acted on once per step, at the step's AND
+// barrier, so the layers of a step run without per-layer branches (5 % of the sampler's time);
+// after a failure the rest of the step runs on stale rows (the status word reports it).
+__device__ __forceinline__ void tile_sync_issue_all(const Tile& T, const IssueConst& C, int l, bool issuer) {
+    asm volatile("bar.sync %0, 128;" ::"r"(T.bar_id) : "memory");
+    if (issuer) {
+        constexpr uint32_t kIdesc64 = idesc_bf16(128, 64), kIdesc16 = idesc_bf16(128, 16);
+        tc_fence_after();
+        if (l == 0) {
+            mma1_ta_commit(T.d_tmem, T.d_tmem + kFeatCol, C.db0, kIdesc64, T.d_bar);
+        } else {
+            const uint64_t db = (l == 1) ? C.db1 : (l == 2) ? C.db2 : (l == 3) ? C.db3 : C.db4;
+            mma7_ta_commit(T.d_tmem, T.d_tmem + 64, db, (l < 4) ? (64 * kRowBytes) >> 4 : (16 * kRowBytes) >> 4,
+                           (l < 4) ? kIdesc64 : kIdesc16, T.d_bar);
+        }
+    }
 }
 
 // Normal of step i and the Lagrange basis at it (independent of the network).  The normals
