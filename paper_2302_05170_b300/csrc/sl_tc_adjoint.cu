@@ -123,23 +123,6 @@ __device__ __forceinline__ void tile_sync_issue_T_all(const Tile& T, const Issue
     }
 }
 
-// The same with the warpgroup's AND of ok (the Softplus chain, whose recomputes branch on it).
-__device__ __forceinline__ bool tile_sync_issue_T(const Tile& T, const IssueConstT& C, int lt, bool ok, bool issuer) {
-    ok = bar_and(T.bar_id, ok);
-    if (ok && issuer) {
-        constexpr uint32_t kIdesc64 = idesc_bf16(128, 64), kIdesc16 = idesc_bf16(128, 16);
-        tc_fence_after();
-        if (lt == 0) {
-            mma1_ta_commit(T.d_tmem, T.d_tmem + 64, C.db5, kIdesc64, T.d_bar);
-        } else {
-            const uint64_t db = (lt == 1) ? C.db4 : (lt == 2) ? C.db3 : (lt == 3) ? C.db2 : C.db1;
-            mma7_ta_commit(T.d_tmem, T.d_tmem + 64, db, (lt < 4) ? (64 * kRowBytes) >> 4 : (16 * kRowBytes) >> 4,
-                           (lt < 4) ? kIdesc64 : kIdesc16, T.d_bar);
-        }
-    }
-    return ok;
-}
-
 // Steps of a segment whose ReLU patterns are recorded at once (per tile: 8 steps x 4
 // hidden layers x 2 words x 128 rows in shared memory).
 constexpr int kMaskSteps = 8;
@@ -402,34 +385,31 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
             }
             if constexpr (ACT == SL_ACT_SOFTPLUS) {
                 for (int i = i1 - 1; ok && i >= i0; --i) {
-                    // backward chain with c_j = lambda * ell_j(X_i); dh4 = W5^T c
+                    // backward chain with c_j = lambda * ell_j(X_i); dh4 = W5^T c (one failure
+                    // check per step, at its AND barrier)
                     tile_rng_any(T, a, i, blk);
                     tile_cotangent(T, lam);
-                    ok = tile_sync_issue_T(T, CT, 0, ok, issuer);
-                    if (!ok) break;
+                    tile_sync_issue_T_all(T, CT, 0, issuer);
                     for (int lt = 1; lt <= 4; ++lt) {
                         const int l = 5 - lt;               // dh_l is in the accumulator
-                        bool w = tile_wait(T, abort_flag, a.status);
+                        ok &= tile_wait(T, abort_flag, a.status);
                         float dh[SL_WIDTH];
-                        if (w) tile_acc50(T, dh);
+                        tile_acc50(T, dh);
                         // the step's forward again, up to z_l (issues 0 .. l-1)
                         T.Y = Ys[i - i0];
                         tile_features(T, a);
-                        ok = tile_sync_issue(T, C, 0, w, issuer);
-                        for (int ll = 1; ok && ll < l; ++ll) {
-                            const bool w2 = tile_wait(T, abort_flag, a.status);
-                            if (w2) tile_hidden_act<ACT>(T);
-                            ok = tile_sync_issue(T, C, ll, w2, issuer);
+                        tile_sync_issue_all(T, C, 0, issuer);
+                        for (int ll = 1; ll < l; ++ll) {
+                            ok &= tile_wait(T, abort_flag, a.status);
+                            tile_hidden_act<ACT>(T);
+                            tile_sync_issue_all(T, C, ll, issuer);
                         }
-                        if (!ok) break;
-                        w = tile_wait(T, abort_flag, a.status);
-                        if (w) tile_backward_sp(T, dh);
-                        ok = tile_sync_issue_T(T, CT, lt, w, issuer);   // dh_{l-1} = W_l^T dz_l
-                        if (!ok) break;
+                        ok &= tile_wait(T, abort_flag, a.status);
+                        tile_backward_sp(T, dh);
+                        tile_sync_issue_T_all(T, CT, lt, issuer);   // dh_{l-1} = W_l^T dz_l
                     }
-                    if (!ok) break;
-                    const bool w = tile_wait(T, abort_flag, a.status);
-                    if (w) {
+                    ok &= tile_wait(T, abort_flag, a.status);
+                    {
                         tc_fence_after();
                         uint32_t gf[8];
                         tmem_ld8(T.taddr, gf);
@@ -440,7 +420,7 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
                         for (int q = 0; q < SL_MAX_DIN_TC - 2; ++q)
                             if (q < p) gth[q] += __uint_as_float(gf[2 + q]);
                     }
-                    ok = bar_and(T.bar_id, w);
+                    ok = bar_and(T.bar_id, ok);
                 }
             } else {
             // blocks of at most kMaskSteps steps, last first: a forward pass over the block that
