@@ -18,19 +18,20 @@ namespace sl {
 namespace {
 
 constexpr int kEmThreads = 256;
-constexpr int kSelThreads = 512;
+constexpr int kSelThreads = 1024;                 // one CTA per SM (see the kernel)
 constexpr int kSelWarps = kSelThreads / 32;
 constexpr int kMaxK = 16;
 constexpr int kD1 = 14;                       // select: first digit, the keys' top 14 bits
 constexpr int kBins1 = 1 << kD1;
 constexpr int kD2 = 9;                        // refine digits (9 + 9 bits)
 constexpr int kBins2 = 1 << kD2;
-constexpr int kCandCap = kBins1 + 6144;        // keys the collect step holds in shared memory
+constexpr int kCandCap = 40960;                // keys the collect step holds in shared memory
 // byte table of the ranks' bins, then the histogram, whose space (and 28 KB more) holds the keys
 constexpr size_t kSelSmem = static_cast<size_t>(kBins1) + static_cast<size_t>(kCandCap) * 4;
 static_assert(kMaxK * kBins2 <= kBins1, "refine histograms reuse the first digit's");
 static_assert(kD1 + 2 * kD2 == 32 && (32 - kD1) % 6 == 0, "digits cover the key");
-static_assert(kSelThreads * 32 == kBins1 && kMaxK <= kSelWarps, "one thread per 32 first-digit bins, one warp per rank");
+constexpr int kBPT = kBins1 / kSelThreads;     // first-digit bins per thread in the scan
+static_assert(kBPT * kSelThreads == kBins1 && kMaxK <= kSelWarps, "first-digit bins per thread, one warp per rank");
 
 // Two paths per thread (q and q + kEmThreads of the CTA's 2 kEmThreads): their independent
 // step chains interleave, which keeps the issue slots busier than one chain per thread.
@@ -270,9 +271,12 @@ __device__ __forceinline__ void collect_keys(const float* __restrict__ values, c
 //   refine:  otherwise (a value repeated very often, or very narrow data) two more passes over the
 //            segment with 9-bit digits, one histogram per distinct prefix.
 // A byte table marks the bins of the ranks, so the later passes skip every other value after one
-// shared-memory load.  They re-read the segment mostly from L2: the CTAs resident at a time hold
-// less than its 126 MB.
-__global__ void __launch_bounds__(kSelThreads, 2)
+// shared-memory load.  One CTA of 1024 threads per SM (176 KB of shared memory): the 148
+// segments in flight (59 MB for 1e5-value segments) stay in the 126 MB L2 between the two
+// reads, and the candidate buffer holds 40,960 keys, so narrow rows rarely refine (CIR labels,
+// 1024 x 1e5: 0.250 ms against 0.332 ms with two CTAs of 512 threads per SM and 22,528
+// candidates; lognormal values: 0.240 against 0.221 ms).
+__global__ void __launch_bounds__(kSelThreads, 1)
 segmented_select_kernel(const float* __restrict__ values, const int64_t* __restrict__ seg_off,
                         int64_t uniform_len, RankList ranks, float* __restrict__ out,
                         unsigned* status) {
@@ -311,20 +315,20 @@ segmented_select_kernel(const float* __restrict__ values, const int64_t* __restr
         if (in) atomicAdd(&hist[key >> (32 - kD1)], 1u);
     });
     __syncthreads();
-    {   // thread t owns bins 32t .. 32t+31 (read rotated by lane: no bank conflicts)
+    {   // thread t owns bins kBPT t .. kBPT t + kBPT - 1 (read rotated by lane)
         uint32_t loc = 0;
 #pragma unroll 8
-        for (int i = 0; i < 32; ++i) loc += hist[32 * tid + ((i + lane) & 31)];
+        for (int i = 0; i < kBPT; ++i) loc += hist[kBPT * tid + ((i + lane) & (kBPT - 1))];
         uint32_t total;
         const uint32_t excl = block_exclusive_scan(loc, part, total);
         for (int j = 0; j < nk; ++j) {
             const int64_t r = ranks.r[j];
             if (r >= n || r < static_cast<int64_t>(excl) || r >= static_cast<int64_t>(excl) + loc) continue;
             int64_t cum = excl;
-            for (int i = 0; i < 32; ++i) {
-                const uint32_t c = hist[32 * tid + i];
+            for (int i = 0; i < kBPT; ++i) {
+                const uint32_t c = hist[kBPT * tid + i];
                 if (r < cum + c) {
-                    prefix[j] = static_cast<uint32_t>(32 * tid + i) << (32 - kD1);
+                    prefix[j] = static_cast<uint32_t>(kBPT * tid + i) << (32 - kD1);
                     rem[j] = r - cum;
                     break;
                 }

@@ -149,14 +149,14 @@ def test_select_value_distributions(sl, orc, kind):
         assert np.any((want > 0) & (want < 1.2e-38))          # some ranks landed on denormals
 
 
-@pytest.mark.parametrize("c", [22527, 22528, 22529, 40000])
+@pytest.mark.parametrize("c", [22528, 40959, 40960, 40961, 60000])
 def test_select_candidate_capacity(sl, orc, c):
     """A segment whose requested ranks sit in one narrow cluster of c values (1 + k 2^-22, many of
     them repeated) among values spread over many binades: the cluster's first-digit bin holds c
-    values.  The select copies the ranks' bins to shared memory when they hold at most 22,528
-    values together, so c = 22527 and 22528 take its shared-memory finish and 22529, 40000 its
-    refining passes (with ranks outside the cluster too, every c refines).  Bit for bit against
-    the oracle's sort, ranks at both ends of the cluster."""
+    values.  The select copies the ranks' bins to shared memory when they hold at most 40,960
+    values together, so c up to 40960 takes its shared-memory finish and 40961, 60000 its
+    refining passes (with ranks outside the cluster too, every c from 40960 on refines).  Bit for
+    bit against the oracle's sort, ranks at both ends of the cluster."""
     rng = np.random.default_rng(c)
     far = np.concatenate([rng.uniform(2.0 ** -40, 2.0 ** -20, 30_000), rng.uniform(4.0, 2.0 ** 40, 30_000)])
     cl = 1.0 + rng.integers(0, 300, c) * 2.0 ** -22
