@@ -196,6 +196,79 @@ __device__ __forceinline__ void tile_backward_sp(const Tile& T, const float (&dh
     });
 }
 
+// Softplus layers whose sigma(z) = 1 / (1 + e^{-z}) the backward chain takes from tensor memory
+// instead of recomputing the step's forward pass: the tile's sigma columns (FP32, one column per
+// neuron) at kSig4 (layer 4) and kSig3 (layer 3) past its accumulator.  Layers 2 and 1 are still
+// recomputed (their sigma would need 100 more columns per tile).
+constexpr uint32_t kSig4 = 256, kSig3 = 256 + 64;
+
+__device__ __forceinline__ uint32_t sigma_bits(uint32_t zb) {
+    return __float_as_uint(__frcp_rn(1.0f + __expf(-__uint_as_float(zb))));
+}
+
+// The accumulator row (z of a Softplus layer): sigma(z) into the sigma columns at scol and, with
+// kAct, Softplus(z) split into BF16 hi + lo as the next A row (tile_hidden_act's output).
+template <bool kAct>
+__device__ __forceinline__ void tile_forward_sigma(const Tile& T, uint32_t scol) {
+    tc_fence_after();
+    uint32_t v0[16], v1[16], v2[16], v3[2];
+    tmem_ld16(T.taddr, v0);
+    tmem_ld16(T.taddr + 16, v1);
+    tmem_ld16(T.taddr + 32, v2);
+    tmem_ld2(T.taddr + 48, v3);
+    tmem_wait_ld();
+    uint32_t s[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) s[k] = sigma_bits(v0[k]);
+    tmem_st16(T.taddr + scol, s);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) s[k] = sigma_bits(v1[k]);
+    tmem_st16(T.taddr + scol + 16, s);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) s[k] = sigma_bits(v2[k]);
+    tmem_st16(T.taddr + scol + 32, s);
+    tmem_st1(T.taddr + scol + 48, sigma_bits(v3[0]));
+    tmem_st1(T.taddr + scol + 49, sigma_bits(v3[1]));
+    if constexpr (kAct) {
+        auto sp = [](uint32_t x) { return __float_as_uint(softplus_fast(__uint_as_float(x))); };
+        const uint32_t at = T.taddr + 64;
+        uint32_t w[16];
+#pragma unroll
+        for (int p = 0; p < 8; ++p) split_rn(sp(v0[2 * p]), sp(v0[2 * p + 1]), w[p], w[8 + p]);
+        tmem_st16(at, w);
+#pragma unroll
+        for (int p = 0; p < 8; ++p) split_rn(sp(v1[2 * p]), sp(v1[2 * p + 1]), w[p], w[8 + p]);
+        tmem_st16(at + 16, w);
+#pragma unroll
+        for (int p = 0; p < 8; ++p) split_rn(sp(v2[2 * p]), sp(v2[2 * p + 1]), w[p], w[8 + p]);
+        tmem_st16(at + 32, w);
+        uint32_t h, l;
+        split_rn(sp(v3[0]), sp(v3[1]), h, l);
+        tmem_st1(at + 48, h);
+        tmem_st1(at + 50, l);
+    }
+    tmem_wait_st();
+    tc_fence_before();
+}
+
+// Backward epilogue of a Softplus layer whose sigma(z) is in the sigma columns at scol: the
+// accumulator holds dh; dz = dh * sigma(z), split into BF16 hi + lo as the next A row (the
+// values of tile_backward_sp, without the forward recompute).
+__device__ __forceinline__ void tile_backward_sig(const Tile& T, uint32_t scol) {
+    uint32_t s0[16], s1[16], s2[16], s3[2];
+    tc_fence_after();
+    tmem_ld16(T.taddr + scol, s0);
+    tmem_ld16(T.taddr + scol + 16, s1);
+    tmem_ld16(T.taddr + scol + 32, s2);
+    tmem_ld2(T.taddr + scol + 48, s3);
+    auto dz = [&](uint32_t db, uint32_t sb) { return __float_as_uint(__uint_as_float(db) * __uint_as_float(sb)); };
+    tile_epilogue(T, [&](int n, uint32_t x0, uint32_t x1, uint32_t& hw, uint32_t& lw) {
+        const uint32_t sa = (n < 16) ? s0[n] : (n < 32) ? s1[n - 16] : (n < 48) ? s2[n - 32] : s3[n - 48];
+        const uint32_t sb = (n + 1 < 16) ? s0[n + 1] : (n + 1 < 32) ? s1[n - 15] : (n + 1 < 48) ? s2[n - 31] : s3[n - 47];
+        split_rn(dz(x0, sa), dz(x1, sb), hw, lw);
+    });
+}
+
 // Cotangent of the collocation points, c_j = lambda * ell_j(X), as the A row
 // of W5^T: words 0..3 = hi pairs (c_0, c_1) .. (c_6, c_7), words 4..7 = lo pairs.
 __device__ __forceinline__ void tile_cotangent(const Tile& T, float lam) {
@@ -266,8 +339,9 @@ constexpr int mask_words_per_tile() { return ACT == SL_ACT_RELU ? kMaskWordsPerT
 template <int WG, int ACT>
 __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const AdjTC A) {
     constexpr int S = WG;
-    constexpr uint32_t kCols = (S * 128 <= 128) ? 128 : (S * 128 <= 256) ? 256 : 512;
-    static_assert(S * 128 <= 512, "tensor memory holds 512 columns");
+    // Softplus: two tiles, and past them each tile's sigma columns (kSig4, kSig3)
+    constexpr uint32_t kCols = (ACT == SL_ACT_SOFTPLUS) ? 512 : (S * 128 <= 128) ? 128 : (S * 128 <= 256) ? 256 : 512;
+    static_assert(S * 128 <= 512 && (ACT != SL_ACT_SOFTPLUS || S <= 2), "tensor memory holds 512 columns");
     const SimArgs& a = A.s;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
@@ -385,12 +459,33 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
             }
             if constexpr (ACT == SL_ACT_SOFTPLUS) {
                 for (int i = i1 - 1; ok && i >= i0; --i) {
-                    // backward chain with c_j = lambda * ell_j(X_i); dh4 = W5^T c (one failure
-                    // check per step, at its AND barrier)
                     tile_rng_any(T, a, i, blk);
+                    // the step's forward once, keeping sigma(z_3) and sigma(z_4) in tensor memory
+                    // (one failure check per step, at its AND barrier)
+                    T.Y = Ys[i - i0];
+                    tile_features(T, a);
+                    tile_sync_issue_all(T, C, 0, issuer);
+                    ok &= tile_wait(T, abort_flag, a.status);
+                    tile_hidden_act<ACT>(T);
+                    tile_sync_issue_all(T, C, 1, issuer);
+                    ok &= tile_wait(T, abort_flag, a.status);
+                    tile_hidden_act<ACT>(T);
+                    tile_sync_issue_all(T, C, 2, issuer);
+                    ok &= tile_wait(T, abort_flag, a.status);
+                    tile_forward_sigma<true>(T, kSig3);
+                    tile_sync_issue_all(T, C, 3, issuer);
+                    ok &= tile_wait(T, abort_flag, a.status);
+                    tile_forward_sigma<false>(T, kSig4);
+                    // backward chain with c_j = lambda * ell_j(X_i): dh4 = W5^T c, then dh3, dh2
                     tile_cotangent(T, lam);
                     tile_sync_issue_T_all(T, CT, 0, issuer);
-                    for (int lt = 1; lt <= 4; ++lt) {
+                    ok &= tile_wait(T, abort_flag, a.status);
+                    tile_backward_sig(T, kSig4);
+                    tile_sync_issue_T_all(T, CT, 1, issuer);
+                    ok &= tile_wait(T, abort_flag, a.status);
+                    tile_backward_sig(T, kSig3);
+                    tile_sync_issue_T_all(T, CT, 2, issuer);
+                    for (int lt = 3; lt <= 4; ++lt) {
                         const int l = 5 - lt;               // dh_l is in the accumulator
                         ok &= tile_wait(T, abort_flag, a.status);
                         float dh[SL_WIDTH];
