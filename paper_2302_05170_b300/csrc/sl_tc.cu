@@ -28,16 +28,17 @@
 // written once per tile except Y's word.
 //
 // Synchronisation: the four warps of a slot meet at a named barrier once the
-// next A operand is written (at the end of every step an AND reduction, so a
-// failed wait stops all four together); the issuing warp then issues the layer's MMAs and commits them to
-// the slot's mbarrier d_ready, on which all four warps wait.  Warp w runs on SM
-// sub-partition w % 4, so warpgroup t issuing from its warp t % 4 spreads the
-// slots' issue work over the four sub-partitions (with every slot issuing from
-// its warp 0, sub-partition 0 carried all of it, and its warps arrived last at
-// every hand-off: 11.5 ms against 11.0 ms on the 16 x 1e6 x 16 workload).  Every wait is bounded
-// (about one second of global time); on expiry the kernel sets SL_DEV_TIMEOUT
-// in the status word, the slot stops, every issuer drains its own MMAs
-// (bounded) and the tensor memory is released.
+// next A operand is written, and the issuing warp then issues the layer's MMAs
+// and commits them to the slot's mbarrier d_ready, on which all four warps
+// wait.  Warp w runs on SM sub-partition w % 4, so warpgroup t issuing from its
+// warp t % 4 spreads the slots' issue work over the four sub-partitions (with
+// every slot issuing from its warp 0, sub-partition 0 carried all of it and its
+// warps arrived last at every hand-off: 11.5 ms against 11.0 ms on the
+// 16 x 1e6 x 16 workload).  Every wait is bounded (about one second of global
+// time); on expiry the kernel sets SL_DEV_TIMEOUT in the status word.  The
+// waits' results are ANDed over the slot's warps once per step (a bar.red at
+// the step's end), where a failure stops the slot; every issuer then drains its
+// own MMAs (bounded) and the tensor memory is released.
 #include "sl_tc_common.cuh"
 
 namespace sl {
