@@ -25,7 +25,8 @@ constexpr uint64_t kTimeoutNs = 1000000000ull;           // bounded waits: 1 s
 // Hidden A row: 112 BF16 values (K) in 56 tensor-memory columns, two per column, the even K
 // index in the low half.  Chunk c = 0, 1, 2 covers neurons 16c .. 16c+15: columns 16c .. 16c+7
 // hold the hi pairs (neurons 16c+2p, 16c+2p+1 in column 16c+p), columns 16c+8 .. 16c+15 the lo
-// pairs.  Column 48 holds the hi pair of neurons 48, 49, column 49 = {1, 0} (the bias unit),
+// pairs.  Column 48 holds the hi pair of neurons 48, 49, column 49 = {1, 0} (the bias unit;
+// log2(e) as a hi, lo pair in the base-2 Softplus form),
 // column 50 the lo pair of neurons 48, 49, columns 51..55 = 0.  So an epilogue stores each chunk
 // with one 16-column store straight from the split's outputs, and columns 49, 51..55 never
 // change (tile_init_row writes them once).  The B tiles of the hidden and output layers (and the
@@ -36,6 +37,12 @@ enum KRole { kKNone = 0, kKHi = 1, kKLo = 2, kKBias = 3 };
 // its constant words (dt, theta, the bias unit) are written once per tile, Y's word per step.
 constexpr uint32_t kFeatCol = 120;
 constexpr uint32_t kBiasWord = 0x00003F80u;              // {1.0, 0} as BF16x2
+// The base-2 Softplus form of the sampler (softplus2_fast) carries every pre-activation scaled by
+// log2(e): its bias unit is log2(e) as the BF16 pair (hi, lo), both rounded to nearest (their sum
+// is log2(e) within 5e-6 of it, relative), against B rows holding the bias at both K indices.
+constexpr uint32_t kBiasWordL2 = 0xBB2C3FB9u;
+constexpr float kLog2e = 1.44269504088896341f;
+constexpr float kLn2 = 0.693147180559945309f;
 __host__ __device__ constexpr int hid_k_role(int k, int& n) {
     if (k < 96) {
         n = 16 * (k >> 5) + (k & 15);
@@ -276,6 +283,16 @@ __device__ __forceinline__ void split_relu(uint32_t a, uint32_t b, uint32_t& hw,
 __device__ __forceinline__ float softplus_fast(float x) {
     return fmaxf(x, 0.0f) + __logf(1.0f + __expf(-fabsf(x)));
 }
+// The same in base 2, for y = x log2(e): log2(1 + 2^y) = Softplus(x) log2(e), with the exponent
+// and logarithm units' own base (no scaling on either side of them).  A hidden layer whose input
+// and output are both kept in these units needs no change of weights (ln 2 log2(e) = 1), only a
+// bias unit of log2(e) (kBiasWordL2): one instruction per activation fewer than softplus_fast.
+__device__ __forceinline__ float softplus2_fast(float y) {
+    float e, l;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-fabsf(y)));
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(1.0f + e));
+    return fmaxf(y, 0.0f) + l;
+}
 __device__ __forceinline__ uint32_t pack_rn(float lo_elem, float hi_elem) {
     uint32_t d;
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi_elem), "f"(lo_elem));
@@ -302,9 +319,11 @@ __device__ __forceinline__ uint32_t b_elem_off(int rows, int n, int k) {
 }
 
 // Stage the network's weights as BF16 B tiles.
-//   B1[n][2i] = B1[n][2i+1] = W1[n][i] (i < d_in), B1[n][2 d_in] = b1[n]
+//   B1[n][2i] = B1[n][2i+1] = W1[n][i] (i < d_in), B1[n][2 d_in] = B1[n][2 d_in + 1] = b1[n]
 //   Bl[n][k] = Wl[n][j] where K index k holds neuron j's hi or lo part, bl[n] at the bias
-//   unit's k, 0 elsewhere (the hidden A row's K order, hid_k_role)
+//   unit's k and at k = 99, 0 elsewhere (the hidden A row's K order, hid_k_role)
+// The second bias entries meet the high half of the bias word: 0 in {1.0, 0}, the lo part of
+// log2(e) in the base-2 Softplus form's kBiasWordL2.
 __device__ inline void stage_weights(unsigned char* sB, const float* __restrict__ P, int d_in, int m) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int W = SL_WIDTH;
@@ -317,7 +336,7 @@ __device__ inline void stage_weights(unsigned char* sB, const float* __restrict_
         const int n = i / 16, k = i % 16;
         float v = 0.0f;
         if (k < 2 * d_in) v = W1[n * d_in + (k >> 1)];
-        else if (k == 2 * d_in) v = b1[n];
+        else if (k == 2 * d_in || k == 2 * d_in + 1) v = b1[n];
         else continue;
         *reinterpret_cast<__nv_bfloat16*>(sB + b_elem_off(64, n, k)) = __float2bfloat16_rn(v);
     }
@@ -332,8 +351,9 @@ __device__ inline void stage_weights(unsigned char* sB, const float* __restrict_
             const int n = i / 112, k = i % 112;
             int j = 0;
             const int role = hid_k_role(k, j);
-            if (role == kKNone) continue;
-            const float v = (role == kKBias) ? bl[n] : Wl[n * W + j];
+            const bool bias = role == kKBias || k == 99;
+            if (role == kKNone && !bias) continue;
+            const float v = bias ? bl[n] : Wl[n * W + j];
             *reinterpret_cast<__nv_bfloat16*>(dst + b_elem_off(rows, n, k)) = __float2bfloat16_rn(v);
         }
         p = bl + n_out;
@@ -403,23 +423,28 @@ __device__ __forceinline__ uint32_t feature_word(float x) {
 }
 
 // Layer-1 A row of a new tile: features [Y, dt, theta] as (hi, lo) BF16 pairs, then the
-// constant 1 (columns kFeatCol..kFeatCol+7).
+// constant 1 (columns kFeatCol..kFeatCol+7).  L2: the base-2 Softplus form, features and bias
+// unit scaled by log2(e).
+template <bool L2 = false>
 __device__ __forceinline__ void tile_features_init(Tile& T, const SimArgs& a) {
     T.feat[0] = T.Y;
+    constexpr uint32_t bw = L2 ? kBiasWordL2 : kBiasWord;
     uint32_t fw[8];
 #pragma unroll
     for (int k = 0; k < SL_MAX_DIN_TC; ++k)
-        fw[k] = (k < a.d_in) ? feature_word(T.feat[k]) : ((k == a.d_in) ? kBiasWord : 0u);   // 1.0 after the features
-    fw[7] = (a.d_in == SL_MAX_DIN_TC) ? kBiasWord : 0u;
+        fw[k] = (k < a.d_in) ? feature_word(L2 ? T.feat[k] * kLog2e : T.feat[k])
+                             : ((k == a.d_in) ? bw : 0u);   // the bias unit after the features
+    fw[7] = (a.d_in == SL_MAX_DIN_TC) ? bw : 0u;
     tmem_st8(T.taddr + kFeatCol, fw);
     tmem_wait_st();
     tc_fence_before();
 }
 
 // Layer-1 A row of the next step: only Y's word changes.
+template <bool L2 = false>
 __device__ __forceinline__ void tile_features(Tile& T, const SimArgs& a) {
     (void)a;
-    tmem_st1(T.taddr + kFeatCol, feature_word(T.Y));
+    tmem_st1(T.taddr + kFeatCol, feature_word(L2 ? T.Y * kLog2e : T.Y));
     tmem_wait_st();
     tc_fence_before();
 }
@@ -480,8 +505,9 @@ __device__ __forceinline__ bool tile_wait(Tile& T, volatile int* abort_flag, uns
 
 // The constant columns of the tile's hidden A row (49 = bias unit, 51..55 = 0), once per
 // kernel before the first MMA (the features' wait::st orders it before the issue).
+template <bool L2 = false>
 __device__ __forceinline__ void tile_init_row(const Tile& T) {
-    const uint32_t c[8] = {0u, kBiasWord, 0u, 0u, 0u, 0u, 0u, 0u};
+    const uint32_t c[8] = {0u, L2 ? kBiasWordL2 : kBiasWord, 0u, 0u, 0u, 0u, 0u, 0u};
     tmem_st8(T.taddr + 64 + 48, c);
 }
 
@@ -531,10 +557,15 @@ __device__ __forceinline__ void tile_epilogue(const Tile& T, F&& f) {
 }
 
 // Hidden-layer epilogue: accumulator row -> activation -> BF16 hi + lo -> next A row.
-// ReLU is fused into the split's conversions; Softplus is applied to the whole row first.
-template <int ACT>
+// ReLU is fused into the split's conversions; Softplus is applied to the whole row first (L2:
+// in base 2, the accumulator and the activations scaled by log2(e)).
+template <int ACT, bool L2 = false>
 __device__ __forceinline__ void tile_hidden_act(const Tile& T) {
-    if constexpr (ACT == SL_ACT_SOFTPLUS) {
+    if constexpr (ACT == SL_ACT_SOFTPLUS && L2) {
+        tile_epilogue(
+            T, [](uint32_t x) { return __float_as_uint(softplus2_fast(__uint_as_float(x))); },
+            [](int, uint32_t x0, uint32_t x1, uint32_t& hw, uint32_t& lw) { split_rn(x0, x1, hw, lw); });
+    } else if constexpr (ACT == SL_ACT_SOFTPLUS) {
         tile_epilogue(
             T, [](uint32_t x) { return __float_as_uint(softplus_fast(__uint_as_float(x))); },
             [](int, uint32_t x0, uint32_t x1, uint32_t& hw, uint32_t& lw) { split_rn(x0, x1, hw, lw); });
@@ -548,7 +579,8 @@ __device__ __forceinline__ void tile_hidden_act(const Tile& T) {
 __device__ __forceinline__ void tile_hidden(const Tile& T) { tile_hidden_act<SL_ACT_RELU>(T); }
 
 // Output layer: collocation points y_j, then Y_{i+1} = g_m(X) = sum_j y_j ell_j(X)
-// (Algorithm I steps 5-6).
+// (Algorithm I steps 5-6).  L2: the accumulator holds y_j log2(e).
+template <bool L2 = false>
 __device__ __forceinline__ void tile_out(Tile& T, const SimArgs& a, int i) {
     tc_fence_after();
     uint32_t yv[8];
@@ -558,7 +590,7 @@ __device__ __forceinline__ void tile_out(Tile& T, const SimArgs& a, int i) {
     float acc = 0.0f;
 #pragma unroll
     for (int j = SL_MAX_M - 1; j >= 0; --j) acc = fmaf(__uint_as_float(yv[j]), T.lb[j], acc);
-    T.Y = acc;
+    T.Y = L2 ? acc * kLn2 : acc;
     if (a.out_grid && T.valid) {
         const int next = i + 1;
         if (a.grid_k <= 1) a.out_grid[static_cast<int64_t>(next) * a.total + T.g] = T.Y;
