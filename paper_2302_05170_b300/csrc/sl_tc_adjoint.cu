@@ -183,14 +183,13 @@ __device__ __forceinline__ void tile_acc50(const Tile& T, float (&d)[SL_WIDTH]) 
     tc_fence_before();
 }
 
-// Backward epilogue of a Softplus layer: the accumulator holds the layer's pre-activation
-// z (just recomputed); dz = dh * sigma(z), sigma(z) = 1 / (1 + e^{-z}) (0 when e^{-z}
-// overflows), split into BF16 hi + lo and written as the next A row (layout of
-// tile_backward_bits).
+// Backward epilogue of a Softplus layer: the accumulator holds the layer's pre-activation in
+// the sampler's base-2 units, y = z log2(e) (just recomputed); dz = dh * sigma(z),
+// sigma(z) = 1 / (1 + 2^{-y}) (sigma2_fast), split into BF16 hi + lo and written as the next A
+// row (layout of tile_backward_bits).  The cotangents themselves are in natural units: the
+// backward chain runs through the unscaled transposed weights.
 __device__ __forceinline__ void tile_backward_sp(const Tile& T, const float (&dh)[SL_WIDTH]) {
-    auto dz = [&](int j, uint32_t zb) {
-        return __float_as_uint(dh[j] * __frcp_rn(1.0f + __expf(-__uint_as_float(zb))));
-    };
+    auto dz = [&](int j, uint32_t yb) { return __float_as_uint(dh[j] * sigma2_fast(__uint_as_float(yb))); };
     tile_epilogue(T, [&](int n, uint32_t x0, uint32_t x1, uint32_t& hw, uint32_t& lw) {
         split_rn(dz(n, x0), dz(n + 1, x1), hw, lw);
     });
@@ -202,12 +201,13 @@ __device__ __forceinline__ void tile_backward_sp(const Tile& T, const float (&dh
 // recomputed (their sigma would need 100 more columns per tile).
 constexpr uint32_t kSig4 = 256, kSig3 = 256 + 64;
 
-__device__ __forceinline__ uint32_t sigma_bits(uint32_t zb) {
-    return __float_as_uint(__frcp_rn(1.0f + __expf(-__uint_as_float(zb))));
+__device__ __forceinline__ uint32_t sigma_bits(uint32_t yb) {
+    return __float_as_uint(sigma2_fast(__uint_as_float(yb)));
 }
 
-// The accumulator row (z of a Softplus layer): sigma(z) into the sigma columns at scol and, with
-// kAct, Softplus(z) split into BF16 hi + lo as the next A row (tile_hidden_act's output).
+// The accumulator row (y = z log2(e) of a Softplus layer): sigma(z) into the sigma columns at
+// scol and, with kAct, Softplus(z) log2(e) split into BF16 hi + lo as the next A row
+// (tile_hidden_act's output in base 2).
 template <bool kAct>
 __device__ __forceinline__ void tile_forward_sigma(const Tile& T, uint32_t scol) {
     tc_fence_after();
@@ -230,7 +230,7 @@ __device__ __forceinline__ void tile_forward_sigma(const Tile& T, uint32_t scol)
     tmem_st1(T.taddr + scol + 48, sigma_bits(v3[0]));
     tmem_st1(T.taddr + scol + 49, sigma_bits(v3[1]));
     if constexpr (kAct) {
-        auto sp = [](uint32_t x) { return __float_as_uint(softplus_fast(__uint_as_float(x))); };
+        auto sp = [](uint32_t x) { return __float_as_uint(softplus2_fast(__uint_as_float(x))); };
         const uint32_t at = T.taddr + 64;
         uint32_t w[16];
 #pragma unroll
@@ -342,6 +342,7 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
     // Softplus: two tiles, and past them each tile's sigma columns (kSig4, kSig3)
     constexpr uint32_t kCols = (ACT == SL_ACT_SOFTPLUS) ? 512 : (S * 128 <= 128) ? 128 : (S * 128 <= 256) ? 256 : 512;
     static_assert(S * 128 <= 512 && (ACT != SL_ACT_SOFTPLUS || S <= 2), "tensor memory holds 512 columns");
+    constexpr bool L2 = (ACT == SL_ACT_SOFTPLUS);   // the forward recompute in base 2, as the sampler
     const SimArgs& a = A.s;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
@@ -400,7 +401,7 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
     T.d_bar = smem_u32(&bars[wg]);
     T.bar_id = 1 + wg;
     T.dph = 0;
-    tile_init_row(T);
+    tile_init_row<L2>(T);
     uint32_t* tmask = masks + wg * mask_words_per_tile<ACT>() + r;   // word (step, layer l, half h) at ((step*4 + l-1)*2 + h)*128
 
     int64_t n_list = static_cast<int64_t>(*A.count);
@@ -422,7 +423,7 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
             valid = false;
         }
         tile_begin_listed(T, a, g, valid);
-        tile_features_init(T, a);
+        tile_features_init<L2>(T, a);
         if (T.valid) T.valid = path_in_set(a.offsets, T.s, g, a.status);
         int blk = -1;
         float lam = valid ? 1.0f : 0.0f;
@@ -441,17 +442,17 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
                 // (one failure check per step, at its AND barrier, as in the sampler)
                 for (int i = i0; i < i1 - 1; ++i) {
                     T.Y = Ys[i - i0];
-                    tile_features(T, a);
+                    tile_features<L2>(T, a);
                     tile_sync_issue_all(T, C, 0, issuer);
                     tile_rng_any(T, a, i, blk);
 #pragma unroll
                     for (int l = 1; l <= 4; ++l) {
                         ok &= tile_wait(T, abort_flag, a.status);
-                        tile_hidden_act<ACT>(T);
+                        tile_hidden_act<ACT, L2>(T);
                         tile_sync_issue_all(T, C, l, issuer);
                     }
                     ok &= tile_wait(T, abort_flag, a.status);
-                    tile_out(T, a, i);
+                    tile_out<L2>(T, a, i);
                     ok = bar_and(T.bar_id, ok);
                     if (!ok) break;
                     Ys[i - i0 + 1] = T.Y;
@@ -463,13 +464,13 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
                     // the step's forward once, keeping sigma(z_3) and sigma(z_4) in tensor memory
                     // (one failure check per step, at its AND barrier)
                     T.Y = Ys[i - i0];
-                    tile_features(T, a);
+                    tile_features<L2>(T, a);
                     tile_sync_issue_all(T, C, 0, issuer);
                     ok &= tile_wait(T, abort_flag, a.status);
-                    tile_hidden_act<ACT>(T);
+                    tile_hidden_act<ACT, L2>(T);
                     tile_sync_issue_all(T, C, 1, issuer);
                     ok &= tile_wait(T, abort_flag, a.status);
-                    tile_hidden_act<ACT>(T);
+                    tile_hidden_act<ACT, L2>(T);
                     tile_sync_issue_all(T, C, 2, issuer);
                     ok &= tile_wait(T, abort_flag, a.status);
                     tile_forward_sigma<true>(T, kSig3);
@@ -492,11 +493,11 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
                         tile_acc50(T, dh);
                         // the step's forward again, up to z_l (issues 0 .. l-1)
                         T.Y = Ys[i - i0];
-                        tile_features(T, a);
+                        tile_features<L2>(T, a);
                         tile_sync_issue_all(T, C, 0, issuer);
                         for (int ll = 1; ll < l; ++ll) {
                             ok &= tile_wait(T, abort_flag, a.status);
-                            tile_hidden_act<ACT>(T);
+                            tile_hidden_act<ACT, L2>(T);
                             tile_sync_issue_all(T, C, ll, issuer);
                         }
                         ok &= tile_wait(T, abort_flag, a.status);
@@ -524,7 +525,7 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
                 const int j0 = max(i0, j1 - kMaskSteps);
                 T.Y = Ys[j0 - i0];
                 for (int i = j0; i < j1; ++i) {
-                    tile_features(T, a);
+                    tile_features<L2>(T, a);
                     tile_sync_issue_all(T, C, 0, issuer);
                     tile_rng_any(T, a, i, blk);
 #pragma unroll
@@ -534,7 +535,7 @@ __global__ void __launch_bounds__(128 * WG, 1) tc_adjoint_reverse_kernel(const A
                         tile_sync_issue_all(T, C, l, issuer);
                     }
                     ok &= tile_wait(T, abort_flag, a.status);
-                    tile_out(T, a, i);
+                    tile_out<L2>(T, a, i);
                     ok = bar_and(T.bar_id, ok);
                     if (!ok) break;
                 }

@@ -277,22 +277,29 @@ __device__ __forceinline__ void split_relu(uint32_t a, uint32_t b, uint32_t& hw,
     sub_f32x2(a, b, hw << 16, hw & 0xFFFF0000u, la, lb);
     lw = pack_relu(la, lb);
 }
-// Softplus log(1 + e^x) = max(x, 0) + log(1 + e^{-|x|}) on the fast exponent/logarithm
-// unit.  e^{-|x|} lies in (0, 1], so the logarithm's argument lies in (1, 2]; its absolute
-// error stays near 1e-7, far below what the BF16 hi + lo split keeps of the result.
-__device__ __forceinline__ float softplus_fast(float x) {
-    return fmaxf(x, 0.0f) + __logf(1.0f + __expf(-fabsf(x)));
+// Softplus in base 2.  The tensor-core kernels carry every Softplus pre-activation as
+// y = x log2(e) (the features and the bias unit scaled, kBiasWordL2): then
+// log2(1 + 2^y) = Softplus(x) log2(e) = max(y, 0) + log2(1 + 2^{-|y|}) takes the exponent and
+// logarithm units' own base with no scaling on either side, and a hidden layer whose input and
+// output are both in these units needs no change of weights (ln 2 log2(e) = 1).  2^{-|y|} lies in
+// (0, 1], so the logarithm's argument lies in (1, 2]; its absolute error stays near 1e-7, far
+// below what the BF16 hi + lo split keeps of the result.
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
-// The same in base 2, for y = x log2(e): log2(1 + 2^y) = Softplus(x) log2(e), with the exponent
-// and logarithm units' own base (no scaling on either side of them).  A hidden layer whose input
-// and output are both kept in these units needs no change of weights (ln 2 log2(e) = 1), only a
-// bias unit of log2(e) (kBiasWordL2): one instruction per activation fewer than softplus_fast.
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ float softplus2_fast(float y) {
-    float e, l;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-fabsf(y)));
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(1.0f + e));
-    return fmaxf(y, 0.0f) + l;
+    return fmaxf(y, 0.0f) + lg2_approx(1.0f + ex2_approx(-fabsf(y)));
 }
+// The logistic function of the same pre-activation: sigma(x) = 1 / (1 + 2^-y) (0 where 2^-y
+// overflows), the derivative of Softplus at x.
+__device__ __forceinline__ float sigma2_fast(float y) { return __frcp_rn(1.0f + ex2_approx(-y)); }
 __device__ __forceinline__ uint32_t pack_rn(float lo_elem, float hi_elem) {
     uint32_t d;
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi_elem), "f"(lo_elem));
@@ -557,17 +564,14 @@ __device__ __forceinline__ void tile_epilogue(const Tile& T, F&& f) {
 }
 
 // Hidden-layer epilogue: accumulator row -> activation -> BF16 hi + lo -> next A row.
-// ReLU is fused into the split's conversions; Softplus is applied to the whole row first (L2:
-// in base 2, the accumulator and the activations scaled by log2(e)).
+// ReLU is fused into the split's conversions; Softplus is applied to the whole row first, in
+// base 2 (L2: the accumulator and the activations scaled by log2(e)).
 template <int ACT, bool L2 = false>
 __device__ __forceinline__ void tile_hidden_act(const Tile& T) {
-    if constexpr (ACT == SL_ACT_SOFTPLUS && L2) {
+    static_assert(ACT != SL_ACT_SOFTPLUS || L2, "the Softplus layers run in base 2");
+    if constexpr (ACT == SL_ACT_SOFTPLUS) {
         tile_epilogue(
             T, [](uint32_t x) { return __float_as_uint(softplus2_fast(__uint_as_float(x))); },
-            [](int, uint32_t x0, uint32_t x1, uint32_t& hw, uint32_t& lw) { split_rn(x0, x1, hw, lw); });
-    } else if constexpr (ACT == SL_ACT_SOFTPLUS) {
-        tile_epilogue(
-            T, [](uint32_t x) { return __float_as_uint(softplus_fast(__uint_as_float(x))); },
             [](int, uint32_t x0, uint32_t x1, uint32_t& hw, uint32_t& lw) { split_rn(x0, x1, hw, lw); });
     } else {
         tile_epilogue(T, [](int, uint32_t x0, uint32_t x1, uint32_t& hw, uint32_t& lw) {
