@@ -164,3 +164,70 @@ def test_softplus(sl, orc, slots):
     want = orc.seven_league_paths(0, W.bf16_round(P).astype(np.float64), th, y0, off, 2.0, 16, 7, 4, d_in=5,
                                   act=orc.ACT_SOFTPLUS)
     _check(orc, yt.cpu().numpy(), want, off, 4, 16)
+
+
+def _with_biases(P, d_in, m, scale, seed):
+    """P with every bias drawn from U(-scale, scale) (Xavier parameters have zero biases)."""
+    P = P.copy()
+    rng = np.random.default_rng(seed)
+    o = 0
+    for fo, fi in W.layer_shapes(d_in, m):
+        o += fo * fi
+        P[o:o + fo] = rng.uniform(-scale, scale, fo)
+        o += fo
+    assert o == len(P)
+    return P
+
+
+@pytest.mark.parametrize("act", ["relu", "softplus"])
+@pytest.mark.parametrize("m,d_in", [(2, 3), (5, 4), (8, 7), (3, 2), (6, 6)])
+def test_biases_every_shape(sl, orc, act, m, d_in):
+    """Nonzero biases (up to 4 in magnitude) in every layer, for every feature count: the
+    layer-1 bias unit sits in feature column d_in (the last one for d_in = 7) and the hidden and
+    output biases on the hidden A row's bias unit.  (The Softplus form's bias unit is log2(e) as
+    a BF16 hi + lo pair; without the lo entry every bias would be scaled by 1.0018, which the
+    gate catches for three of these five shapes, checked with the oracle:
+    test_bias_chain_constant_features catches it for every network.)"""
+    P = _with_biases(W.xavier_params(d_in, m, seed=40 + m + d_in), d_in, m, 4.0, seed=m * 10 + d_in)
+    rng = np.random.default_rng(m + d_in)
+    n_sets = 3
+    th = rng.uniform(0.05, 0.4, size=(n_sets, d_in - 2)).astype(np.float32)
+    off = W.offsets_from_counts([1500, 131, 2200])
+    y0 = np.array([1.0, 0.6, 1.4], np.float32)
+    a = sl.ACT_SOFTPLUS if act == "softplus" else sl.ACT_RELU
+    net = sl.make_net(_dev(P), d_in, m, act=a, prec=sl.PREC_BF16)
+    total = int(off[-1])
+    yt = torch.full((total,), float("nan"), dtype=torch.float32, device="cuda")
+    ws = sl.seven_league_simulate_batched(sl.MODEL_MLP, net, _dev(th), _dev(y0), _dev(off, torch.int64), 1.5, 8,
+                                          m, 5, out_YT=yt)
+    assert sl.workspace_status(ws) == 0
+    want = orc.seven_league_paths(0, W.bf16_round(P).astype(np.float64), th, y0, off, 1.5, 8, m, 5, d_in=d_in,
+                                  act=orc.ACT_SOFTPLUS if act == "softplus" else orc.ACT_RELU)
+    got = yt.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    _check(orc, got, want, off, 5, 8)
+
+
+@pytest.mark.parametrize("act", ["relu", "softplus"])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_bias_chain_constant_features(sl, orc, act, seed):
+    """W1 = 0 and biases up to 4 in every layer: every path gets the same collocation points (the
+    chain of biases and hidden weights), so the per-path error is the hi + lo split's rounding of
+    constant activations and the gate can be 1e-4.  Checked with the oracle: scaling every bias
+    by hi / log2(e) (a Softplus bias unit that lost its lo entry) moves the paths by ~2e-3."""
+    d_in, m = 4, 7
+    P = _with_biases(W.xavier_params(d_in, m, seed=60 + seed), d_in, m, 4.0, seed=70 + seed)
+    P[:50 * d_in] = 0.0
+    th = W.gbm_online_thetas(2)
+    off = W.offsets_from_counts([2000, 777])
+    y0 = np.array([1.0, 0.7], np.float32)
+    a = sl.ACT_SOFTPLUS if act == "softplus" else sl.ACT_RELU
+    net = sl.make_net(_dev(P), d_in, m, act=a, prec=sl.PREC_BF16)
+    total = int(off[-1])
+    yt = torch.full((total,), float("nan"), dtype=torch.float32, device="cuda")
+    ws = sl.seven_league_simulate_batched(sl.MODEL_MLP, net, _dev(th), _dev(y0), _dev(off, torch.int64), 1.0, 4,
+                                          m, 9, out_YT=yt)
+    assert sl.workspace_status(ws) == 0
+    want = orc.seven_league_paths(0, W.bf16_round(P).astype(np.float64), th, y0, off, 1.0, 4, m, 9, d_in=d_in,
+                                  act=orc.ACT_SOFTPLUS if act == "softplus" else orc.ACT_RELU)
+    _check(orc, yt.cpu().numpy(), want, off, 9, 4, tol=1e-4)
