@@ -33,3 +33,17 @@ def flat_sets(offsets, idx):
     offsets = np.asarray(offsets)
     s = np.searchsorted(offsets, idx, side="right") - 1
     return s, idx - offsets[s]
+
+
+def with_biases(P, shapes, scale, seed):
+    """Flat parameters P (per layer W [out][in], then b; `shapes` the layers' (out, in)) with every
+    bias drawn from U(-scale, scale): Xavier parameters have zero biases."""
+    P = P.copy()
+    rng = np.random.default_rng(seed)
+    o = 0
+    for fo, fi in shapes:
+        o += fo * fi
+        P[o:o + fo] = rng.uniform(-scale, scale, fo)
+        o += fo
+    assert o == len(P)
+    return P

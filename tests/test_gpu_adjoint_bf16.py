@@ -28,7 +28,7 @@ import pytest
 import torch
 
 from paper_2302_05170_b300 import workloads as W
-from tests.helpers import flat_sets, gate, max_abs_normals, rel_err
+from tests.helpers import flat_sets, gate, max_abs_normals, rel_err, with_biases
 
 pytestmark = pytest.mark.gpu
 TOL = 2e-3
@@ -144,6 +144,26 @@ def test_softplus_paths_vs_oracle(sl, orc, d_in, m, counts, n_steps, k):
     K = _strike(orc, P, d_in, m, th, y0, off, 2.0, n_steps, 5, act=1)
     got = _adj(sl, P, d_in, m, th, y0, off, 2.0, n_steps, 5, K, k, sl.PREC_BF16, act=1)
     assert _check(orc, P, d_in, m, th, y0, off, 2.0, n_steps, 5, K, got, act=1) > 0.9
+
+
+@pytest.mark.parametrize("act", [0, 1])
+@pytest.mark.parametrize("d_in,m,counts,n_steps,k", [
+    (4, 7, [3000, 129, 2500], 12, 4),
+    (7, 5, [2000, 700], 6, 3),
+])
+def test_biases_paths_vs_oracle(sl, orc, act, d_in, m, counts, n_steps, k):
+    """Nonzero biases (up to 1.5 in magnitude) in every layer, both activations: the forward
+    sweep and the reverse sweep's recomputes carry them on the bias units (the Softplus form's in
+    base 2, log2(e) as a BF16 hi + lo pair), the backward chain meets them as zero rows."""
+    P = with_biases(W.xavier_params(d_in, m, seed=50 + d_in + m), W.layer_shapes(d_in, m), 1.5, seed=d_in * m)
+    th = _thetas(len(counts), d_in - 2, m)
+    off = W.offsets_from_counts(counts)
+    y0 = np.linspace(0.9, 1.1, len(counts)).astype(np.float32)
+    K = _strike(orc, P, d_in, m, th, y0, off, 2.0, n_steps, 5, act=act)
+    got = _adj(sl, P, d_in, m, th, y0, off, 2.0, n_steps, 5, K, k, sl.PREC_BF16, act=act)
+    sure = _check(orc, P, d_in, m, th, y0, off, 2.0, n_steps, 5, K, got, act=act)
+    if act == 1:
+        assert sure > 0.9
 
 
 def test_softplus_bf16_vs_fp32_forms(sl, orc):

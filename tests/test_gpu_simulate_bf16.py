@@ -11,7 +11,7 @@ import pytest
 import torch
 
 from paper_2302_05170_b300 import workloads as W
-from tests.helpers import flat_sets, gate, max_abs_normals, rel_err
+from tests.helpers import flat_sets, gate, max_abs_normals, rel_err, with_biases
 
 pytestmark = pytest.mark.gpu
 TOL = 2e-3
@@ -167,16 +167,7 @@ def test_softplus(sl, orc, slots):
 
 
 def _with_biases(P, d_in, m, scale, seed):
-    """P with every bias drawn from U(-scale, scale) (Xavier parameters have zero biases)."""
-    P = P.copy()
-    rng = np.random.default_rng(seed)
-    o = 0
-    for fo, fi in W.layer_shapes(d_in, m):
-        o += fo * fi
-        P[o:o + fo] = rng.uniform(-scale, scale, fo)
-        o += fo
-    assert o == len(P)
-    return P
+    return with_biases(P, W.layer_shapes(d_in, m), scale, seed)
 
 
 @pytest.mark.parametrize("act", ["relu", "softplus"])
